@@ -1,0 +1,228 @@
+/*
+ * phc.h -- C ABI of the GB300 path-tracking library.
+ *
+ * The library tracks the solution paths of polynomial homotopies on one
+ * NVIDIA GB300 (sm_103a): the total-degree homotopy of a square system, the
+ * top-dimensional embedded system of a numerical irreducible decomposition
+ * and the cascade of homotopies down to dimension zero (Verschelde, "A
+ * Blackbox Polynomial System Solver on Parallel Shared Memory Computers",
+ * Sections 2 and 3).  Paths are independent (Section 1), so every path is
+ * tracked by one GPU thread; all compute runs in the library's CUDA kernels.
+ *
+ * Conventions
+ *  - Every function returns PHC_OK (0) or a negative PHC_E* code; the message
+ *    of the last failure on the calling thread is phc_last_error().
+ *  - Complex numbers are phc_cd {re, im} (16 bytes, the layout of CUDA's
+ *    double2 and of numpy/torch complex128).
+ *  - "device" arrays live in the memory of the current CUDA device and are
+ *    owned by the caller; the library reads and writes them on the stream
+ *    passed as `cuda_stream` (a cudaStream_t; NULL is the legacy default
+ *    stream).  Calls return after enqueueing work, except where noted.
+ *  - "host" arrays are owned by the caller and read during the call only.
+ *  - Endpoint arrays are structs of arrays: x[j * n_paths + p] is unknown j
+ *    of path p ("SoA [n_var][n_paths]").
+ *  - A per-path numerical failure is not an error: it is class PHC_FAILED.
+ *  - The library never exits, aborts or traps on the device.
+ */
+#ifndef PHC_H
+#define PHC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } phc_cd;
+
+/* Opaque, library-owned homotopy handle; free with phc_destroy_homotopy. */
+typedef struct phc_homotopy phc_homotopy;
+
+enum {
+    PHC_OK = 0,
+    PHC_EINVAL = -1,        /* invalid argument or system                 */
+    PHC_ENOMEM = -2,        /* host or device allocation failed           */
+    PHC_ECUDA = -3,         /* a CUDA call failed (message names it)      */
+    PHC_ETIMEOUT = -4,      /* a bounded device wait ran out              */
+    PHC_EUNSUPPORTED = -5   /* size or option outside what is built       */
+};
+
+/* Endpoint classes (int8 codes).  The paper counts paths that diverge "at
+ * infinity" and separates regular from singular solutions (Sections 3.1 and
+ * 4); the thresholds are in phc_opts. */
+enum { PHC_REGULAR = 0, PHC_SINGULAR = 1, PHC_AT_INFINITY = 2, PHC_FAILED = 3 };
+
+/* Why tracking stopped (phc_path_stats.stop). */
+enum { PHC_STOP_REACHED = 0, PHC_STOP_DIVERGED = 1, PHC_STOP_STEP_MIN = 2, PHC_STOP_BUDGET = 3,
+       PHC_STOP_NONFINITE = 4 };
+
+/* Arithmetic of the tracker.  FP32_INTERIOR evaluates the Jacobian and
+ * factors it in single precision while t < fp32_t_max (the residual of every
+ * Newton correction stays double); a rejected single precision step is
+ * retried in double. */
+enum { PHC_PREC_FP64 = 0, PHC_PREC_FP32_INTERIOR = 1 };
+
+#define PHC_MAX_VARS 12    /* largest number of unknowns of a tracked system */
+
+/* Tracking options.  The paper fixes none of these; the defaults
+ * (phc_default_opts) are the readings the CPU oracle uses too.
+ *   predictor   classical 4th-order Runge-Kutta on dx/dt = -H_x^{-1} H_t
+ *   corrector   <= max_corr_iters Newton steps at t + h; converged when
+ *               ||dx|| <= corr_tol (1 + ||x||); rejected when a correction
+ *               fails to shrink by corr_contract or none converges
+ *   step        clamped to land on t = 1; times `expand` (<= h_max) after
+ *               expand_after accepted steps in a row; times `shrink` after
+ *               a rejection; h < h_min or max_steps steps stall the path
+ *   end         a path that reaches t = 1 gets <= end_iters Newton steps at
+ *               t = 1 (stop at ||dx|| <= end_tol (1 + ||x||))
+ *   classes     norms are max_j max(|Re x_j|, |Im x_j|).
+ *               AT_INFINITY: ||x|| > diverge_norm after an accepted step; or
+ *                 stalled with ||x|| > stall_inf_norm; or stalled at
+ *                 t >= end_zone with ||x|| grown by more than growth_inf per
+ *                 decade of 1-t over its last (<= 4) decade checkpoints.
+ *               FAILED: non-finite values, or stalled before end_zone.
+ *               REGULAR: reached t = 1, cond <= cond_regular and relative
+ *                 residual <= res_regular.
+ *               SINGULAR: everything else (stalled near t = 1 or reached
+ *                 t = 1 with a large condition number).
+ *               cond is the root condition number
+ *                 max_j sum_i |(J^-1)_ji|_1 (1 + scale_i) / (1 + ||x||),
+ *                 J = H_x(x,1), scale_i = sum over the terms of equation i
+ *                 of |c|_1 |x^a|_1, |z|_1 = |Re z| + |Im z|;
+ *               relative residual = max_i |H_i(x,1)|_1 / (1 + scale_i).
+ *   slack_tol   z is zero when |z| <= slack_tol (1 + ||x||). */
+typedef struct {
+    double h_init, h_max, h_min;
+    int32_t expand_after;
+    double expand, shrink;
+    int32_t max_corr_iters;
+    double corr_tol, corr_contract;
+    int32_t max_steps;
+    double diverge_norm, stall_inf_norm, end_zone, growth_inf;
+    int32_t end_iters;
+    double end_tol;
+    double cond_regular, res_regular, slack_tol;
+    int32_t precision;       /* PHC_PREC_*                                  */
+    double fp32_t_max;       /* FP32_INTERIOR: single precision for t < this */
+    int32_t block_threads;   /* threads per block; 0 = chosen by the library */
+    int32_t max_blocks;      /* grid size cap; 0 = one wave of resident blocks */
+} phc_opts;
+
+/* Per-path statistics (device array of these, optional). */
+typedef struct {
+    double t;        /* last t reached                                     */
+    double h;        /* last step size                                     */
+    double cond;     /* root condition number at the endpoint (see opts)   */
+    double relres;   /* relative residual at t = 1                         */
+    double norm_x;   /* max-norm of the endpoint                           */
+    double growth;   /* log10 growth of ||x|| per decade of 1-t, last checkpoints */
+    int32_t n_accept, n_reject;   /* accepted / rejected steps            */
+    int32_t n_newton;             /* Newton corrections (tracking + end)  */
+    int32_t n_solve;              /* evaluate + factor + solve units      */
+    int32_t stop;                 /* PHC_STOP_*                           */
+    int32_t n_fp32;               /* evaluate + solve units in single precision */
+    int32_t grew;                 /* 1 when the growth test flagged the path */
+    int32_t reserved;
+} phc_path_stats;
+
+/* Host-side system lists, library-allocated (phc_embed); free with
+ * phc_free_lists.  Equation i owns terms_per_eq[i] consecutive terms; term t
+ * is coefs[t] * prod_j x_j^exps[t * n_var + j]. */
+typedef struct {
+    int32_t n_eq, n_var, n_terms;
+    int32_t *terms_per_eq;   /* [n_eq]            */
+    uint8_t *exps;           /* [n_terms][n_var]  */
+    phc_cd *coefs;           /* [n_terms]         */
+} phc_system_lists;
+
+/* Fill *opts with the defaults described above.  Never fails for non-NULL. */
+int phc_default_opts(phc_opts *opts);
+
+/* Build the total-degree homotopy H(x,t) = (1-t) gamma g(x) + t f(x) of a
+ * square system f (n_eq == n_var), g_i(x) = x_i^{d_i} - 1 with d_i the
+ * total degree of equation i (the Bezout start system; Section 5 quotes the
+ * Bezout bound).  The lists are host arrays: terms_per_eq [n_eq] (>= 1
+ * each), exps [T][n_var] row-major (T = sum terms_per_eq), coefs [T].
+ * The library copies them, compiles the evaluation tables and uploads them
+ * to the current device; the handle owns that memory.
+ * Errors: PHC_EINVAL for a non-square system, n_var outside
+ * 1..PHC_MAX_VARS, an equation without terms or of degree 0, a non-finite
+ * coefficient, or gamma of zero modulus; PHC_ENOMEM / PHC_ECUDA. */
+int phc_make_homotopy(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps,
+                      const phc_cd *coefs, phc_cd gamma, phc_homotopy **out);
+
+/* Number of paths of the total-degree homotopy, prod d_i (host call). */
+int phc_num_paths(const phc_homotopy *h, int64_t *out);
+
+/* Track paths first_path .. first_path + n_paths - 1 of the total-degree
+ * homotopy (path p starts at the roots of unity selected by the digits of p
+ * in the mixed radix (d_1, ..., d_n), x_1 fastest) from t = 0 to t = 1 and
+ * classify the endpoints.  opts may be NULL (defaults).
+ * Outputs (device, caller-owned): x_out SoA [n_var][n_paths] phc_cd,
+ * cls_out [n_paths] int8 (PHC_REGULAR ...), stats_out [n_paths] or NULL.
+ * Errors: PHC_EINVAL for a NULL handle or output, a range outside
+ * [0, num_paths), or invalid options; PHC_ECUDA. */
+int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_out,
+                    int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
+
+/* The embedded system E_D of Section 2.1 (eq. (2) for D = 1): unknowns
+ * x_1..x_n, z_1..z_D; equation i is f_i(x) + sum_k gammas[i][k] z_k; equation
+ * n_eq + k is hyper[k][0] + sum_j hyper[k][j+1] x_j + z_k.  A square f only
+ * (the squaring of Section 2.1 is left to the caller).  gammas [n_eq][D] and
+ * hyper [D][n_var + 1] are host arrays; when NULL they are drawn from
+ * `seed` (standard complex Gaussian from a 64-bit PCG: state advance
+ * s = s * 6364136223846793005 + 1442695040888963407, output the top 53 bits
+ * of s ^ (s >> 29) as a uniform in [0,1), Box-Muller for the normal).  Host
+ * call; *out is library-allocated (phc_free_lists).
+ * Errors: PHC_EINVAL for a non-square f, top_dim < 0, or n_var + top_dim
+ * above PHC_MAX_VARS; PHC_ENOMEM. */
+int phc_embed(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps, const phc_cd *coefs,
+              int top_dim, const phc_cd *gammas, const phc_cd *hyper, uint64_t seed, phc_system_lists **out);
+
+/* One stage of the cascade of homotopies (Section 3.1, Figure 3): embedded_k
+ * is a handle made from E_k (k >= 1 slacks, as phc_embed lays it out: z_k is
+ * the last unknown and hyperplane k the last equation).  The homotopy keeps
+ * every equation of E_k except hyperplane k, which becomes
+ * (1-t) (hyper[k][0] + sum_j hyper[k][j+1] x_j) + z_k; at t = 1, z_k = 0 and
+ * the remaining equations are E_{k-1}.  starts: device SoA
+ * [n_var(E_k)][n_starts], solutions of E_k with z_k != 0.
+ * Outputs (device): x_out SoA [n_var(E_k) - 1][n_starts] (z_k dropped),
+ * cls_out [n_starts], slack_zero_out [n_starts] (1 when k > 1 and z_{k-1}
+ * is zero, i.e. a candidate generic point of a (k-1)-dimensional set),
+ * stats_out [n_starts] or NULL.
+ * Errors: PHC_EINVAL (k < 1, k >= n_var, NULL arrays), PHC_ECUDA. */
+int phc_cascade_stage(const phc_homotopy *embedded_k, int k, const phc_cd *starts, int64_t n_starts,
+                      const phc_opts *opts, phc_cd *x_out, int8_t *cls_out, uint8_t *slack_zero_out,
+                      phc_path_stats *stats_out, void *cuda_stream);
+
+/* Refine endpoints of h (evaluated at t = 1) by Newton's method in complex
+ * double double arithmetic (the paper's double double path, Section 5,
+ * after Hida, Li and Bailey): every endpoint that reached t = 1
+ * (stats[p].stop == PHC_STOP_REACHED), has class PHC_SINGULAR or
+ * PHC_REGULAR and cond > cond_threshold gets <= max_iters iterations; it
+ * becomes PHC_REGULAR when a correction falls to 1e-20 (1 + ||x||) and the
+ * condition number at the refined point is <= cond_max, else PHC_SINGULAR.
+ * Device arrays: x_hi_io SoA [n_var][n] (in/out, the double part),
+ * x_lo_out SoA [n_var][n] (the low part; zero where untouched), cls_io [n],
+ * stats_io [n] (cond updated).  For a cascade stage pass the handle of
+ * E_{k-1} and the stage's outputs.
+ * Errors: PHC_EINVAL, PHC_ECUDA. */
+int phc_refine_endpoints(const phc_homotopy *h, phc_cd *x_hi_io, phc_cd *x_lo_out, int64_t n,
+                         double cond_threshold, double cond_max, int max_iters, int8_t *cls_io,
+                         phc_path_stats *stats_io, void *cuda_stream);
+
+/* Message of the last non-OK return on the calling thread ("" if none). */
+const char *phc_last_error(void);
+
+void phc_destroy_homotopy(phc_homotopy *h);
+void phc_free_lists(phc_system_lists *lists);
+
+/* Sizes of the structs, for bindings that mirror them. */
+int phc_sizeof_opts(void);
+int phc_sizeof_stats(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHC_H */

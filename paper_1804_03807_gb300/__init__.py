@@ -1,0 +1,79 @@
+"""GB300 path tracker for polynomial homotopies (total-degree homotopy,
+embedding and cascade of a numerical irreducible decomposition).
+
+The compute path is libphc.so (CUDA for sm_103a, C ABI in include/phc.h);
+this package only marshals arguments (``_lib``) and allocates the output
+tensors for the convenience helpers below.  Nothing here computes on the CPU.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from ._lib import (PHC_AT_INFINITY, PHC_FAILED, PHC_MAX_VARS, PHC_PREC_FP32_INTERIOR, PHC_PREC_FP64,
+                   PHC_REGULAR, PHC_SINGULAR, PHC_STOP_REACHED, STATS_DTYPE, Homotopy, PhcError, SystemLists,
+                   load, phc_cascade_stage, phc_default_opts, phc_embed, phc_last_error, phc_make_homotopy,
+                   phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths)
+
+__all__ = [
+    "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
+    "PHC_SINGULAR", "PHC_STOP_REACHED", "STATS_DTYPE", "Homotopy", "PhcError", "SystemLists", "load",
+    "phc_cascade_stage", "phc_default_opts", "phc_embed", "phc_last_error", "phc_make_homotopy", "phc_num_paths",
+    "phc_opts", "phc_refine_endpoints", "phc_track_paths", "Tracked", "track", "cascade", "refine",
+    "stats_numpy",
+]
+
+
+@dataclass
+class Tracked:
+    """Device outputs of one call: x [n_var, P] complex128 (SoA), cls [P]
+    int8, stats [P, 80] uint8 (phc_path_stats records), slack_zero [P] uint8
+    for cascade stages."""
+    x: object
+    cls: object
+    stats: object
+    slack_zero: object = None
+
+
+def stats_numpy(stats) -> np.ndarray:
+    """Copy a stats tensor to the host as a numpy structured array."""
+    return stats.cpu().numpy().view(STATS_DTYPE).reshape(-1)
+
+
+def _alloc(n_var: int, n: int, device):
+    import torch
+    x = torch.empty((n_var, n), dtype=torch.complex128, device=device)
+    cls = torch.empty(n, dtype=torch.int8, device=device)
+    st = torch.empty((n, STATS_DTYPE.itemsize), dtype=torch.uint8, device=device)
+    return x, cls, st
+
+
+def track(h: Homotopy, first: int = 0, n_paths: int | None = None, opts=None, stream=None,
+          device="cuda") -> Tracked:
+    """Track total-degree paths first..first+n_paths-1 into new tensors."""
+    if n_paths is None:
+        n_paths = phc_num_paths(h) - first
+    x, cls, st = _alloc(h.n, n_paths, device)
+    phc_track_paths(h, first, n_paths, opts, x, cls, st, stream)
+    return Tracked(x, cls, st)
+
+
+def cascade(h_k: Homotopy, k: int, starts, opts=None, stream=None) -> Tracked:
+    """One cascade stage from E_k (handle h_k) on starts [n_var(E_k), n]."""
+    import torch
+    n = int(starts.shape[1])
+    x, cls, st = _alloc(h_k.n - 1, n, starts.device)
+    sz = torch.empty(n, dtype=torch.uint8, device=starts.device)
+    phc_cascade_stage(h_k, k, starts.contiguous(), n, opts, x, cls, sz, st, stream)
+    return Tracked(x, cls, st, sz)
+
+
+def refine(h: Homotopy, r: Tracked, cond_threshold: float = 1e6, cond_max: float = 1e12, max_iters: int = 8,
+           stream=None):
+    """Double double refinement in place on r.x / r.cls / r.stats; returns x_lo."""
+    import torch
+    x_lo = torch.empty_like(r.x)
+    phc_refine_endpoints(h, r.x, x_lo, int(r.x.shape[1]), cond_threshold, cond_max, max_iters, r.cls, r.stats,
+                         stream)
+    return x_lo

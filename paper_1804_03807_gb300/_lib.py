@@ -1,0 +1,221 @@
+"""ctypes binding of libphc.so (include/phc.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device
+arrays are torch CUDA tensors (their ``data_ptr()`` is passed); the stream is
+torch's current CUDA stream unless one is given.  There is no fallback: if
+the shared library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphc.so")
+
+PHC_OK, PHC_EINVAL, PHC_ENOMEM, PHC_ECUDA, PHC_ETIMEOUT, PHC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+PHC_REGULAR, PHC_SINGULAR, PHC_AT_INFINITY, PHC_FAILED = 0, 1, 2, 3
+PHC_STOP_REACHED, PHC_STOP_DIVERGED, PHC_STOP_STEP_MIN, PHC_STOP_BUDGET, PHC_STOP_NONFINITE = 0, 1, 2, 3, 4
+PHC_PREC_FP64, PHC_PREC_FP32_INTERIOR = 0, 1
+PHC_MAX_VARS = 12
+
+EXPORTED = [
+    "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
+    "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
+    "phc_sizeof_stats",
+]
+
+
+class PhcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"phc error {code}: {msg}")
+        self.code = code
+
+
+class phc_cd(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class phc_opts(ctypes.Structure):
+    _fields_ = [
+        ("h_init", ctypes.c_double), ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
+        ("expand_after", ctypes.c_int32), ("expand", ctypes.c_double), ("shrink", ctypes.c_double),
+        ("max_corr_iters", ctypes.c_int32), ("corr_tol", ctypes.c_double), ("corr_contract", ctypes.c_double),
+        ("max_steps", ctypes.c_int32),
+        ("diverge_norm", ctypes.c_double), ("stall_inf_norm", ctypes.c_double), ("end_zone", ctypes.c_double),
+        ("growth_inf", ctypes.c_double),
+        ("end_iters", ctypes.c_int32), ("end_tol", ctypes.c_double),
+        ("cond_regular", ctypes.c_double), ("res_regular", ctypes.c_double), ("slack_tol", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("fp32_t_max", ctypes.c_double),
+        ("block_threads", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
+    ]
+
+
+STATS_DTYPE = np.dtype([
+    ("t", "f8"), ("h", "f8"), ("cond", "f8"), ("relres", "f8"), ("norm_x", "f8"), ("growth", "f8"),
+    ("n_accept", "i4"), ("n_reject", "i4"), ("n_newton", "i4"), ("n_solve", "i4"), ("stop", "i4"),
+    ("n_fp32", "i4"), ("grew", "i4"), ("reserved", "i4"),
+])
+
+
+class phc_system_lists(ctypes.Structure):
+    _fields_ = [
+        ("n_eq", ctypes.c_int32), ("n_var", ctypes.c_int32), ("n_terms", ctypes.c_int32),
+        ("terms_per_eq", ctypes.POINTER(ctypes.c_int32)), ("exps", ctypes.POINTER(ctypes.c_uint8)),
+        ("coefs", ctypes.POINTER(phc_cd)),
+    ]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libphc.so (built in-tree by paper_1804_03807_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libphc.so is not built ({LIB_PATH}); run paper_1804_03807_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.phc_default_opts.argtypes = [ctypes.POINTER(phc_opts)]
+    L.phc_make_homotopy.argtypes = [i32, i32, vp, vp, vp, phc_cd, ctypes.POINTER(vp)]
+    L.phc_num_paths.argtypes = [vp, ctypes.POINTER(i64)]
+    L.phc_track_paths.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
+    L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
+                            ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
+    L.phc_cascade_stage.argtypes = [vp, i32, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
+    L.phc_refine_endpoints.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]
+    L.phc_last_error.restype = ctypes.c_char_p
+    L.phc_destroy_homotopy.argtypes = [vp]
+    L.phc_destroy_homotopy.restype = None
+    L.phc_free_lists.argtypes = [ctypes.POINTER(phc_system_lists)]
+    L.phc_free_lists.restype = None
+    for name in ("phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed",
+                 "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats"):
+        getattr(L, name).restype = ctypes.c_int
+    if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
+        raise ImportError("phc_opts layout mismatch between phc.h and the binding")
+    if L.phc_sizeof_stats() != STATS_DTYPE.itemsize:
+        raise ImportError("phc_path_stats layout mismatch between phc.h and the binding")
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != PHC_OK:
+        raise PhcError(rc, load().phc_last_error().decode())
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(getattr(stream, "cuda_stream", stream) or 0)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _lists(sys):
+    tpe = np.ascontiguousarray(sys.terms_per_eq, dtype=np.int32)
+    exps = np.ascontiguousarray(sys.exps, dtype=np.uint8)
+    coefs = np.ascontiguousarray(sys.coefs, dtype=np.complex128)
+    return tpe, exps, coefs
+
+
+class Homotopy:
+    """Owning wrapper of a phc_homotopy* (destroyed with the object)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.ptr = ptr
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.phc_destroy_homotopy(ctypes.c_void_p(self.ptr))
+            self.ptr = None
+
+
+def phc_default_opts(**overrides) -> phc_opts:
+    o = phc_opts()
+    _check(load().phc_default_opts(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def phc_make_homotopy(sys, gamma: complex) -> Homotopy:
+    """Total-degree homotopy of the square system ``sys`` (an object with
+    n_eq, n_var, terms_per_eq, exps, coefs)."""
+    L = load()
+    tpe, exps, coefs = _lists(sys)
+    out = ctypes.c_void_p()
+    _check(L.phc_make_homotopy(int(sys.n_eq), int(sys.n_var), tpe.ctypes.data, exps.ctypes.data, coefs.ctypes.data,
+                               phc_cd(float(np.real(gamma)), float(np.imag(gamma))), ctypes.byref(out)))
+    return Homotopy(out.value, int(sys.n_var))
+
+
+def phc_num_paths(h: Homotopy) -> int:
+    v = ctypes.c_int64()
+    _check(load().phc_num_paths(ctypes.c_void_p(h.ptr), ctypes.byref(v)))
+    return int(v.value)
+
+
+def phc_track_paths(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls_out, stats_out=None, stream=None):
+    """x_out: complex128 CUDA tensor [n_var, n_paths]; cls_out: int8 [n_paths];
+    stats_out: uint8 [n_paths, 80] or None."""
+    _check(load().phc_track_paths(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
+                                  ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
+                                  _ptr(stats_out), _stream_ptr(stream)))
+
+
+class SystemLists:
+    """Host copy of a phc_system_lists (the output of phc_embed)."""
+
+    def __init__(self, n_eq, n_var, terms_per_eq, exps, coefs):
+        self.n_eq, self.n_var = int(n_eq), int(n_var)
+        self.terms_per_eq, self.exps, self.coefs = terms_per_eq, exps, coefs
+
+
+def phc_embed(sys, top_dim: int, gammas=None, hyper=None, seed: int = 0) -> SystemLists:
+    L = load()
+    tpe, exps, coefs = _lists(sys)
+    g = None if gammas is None else np.ascontiguousarray(gammas, dtype=np.complex128)
+    hy = None if hyper is None else np.ascontiguousarray(hyper, dtype=np.complex128)
+    out = ctypes.POINTER(phc_system_lists)()
+    _check(L.phc_embed(int(sys.n_eq), int(sys.n_var), tpe.ctypes.data, exps.ctypes.data, coefs.ctypes.data,
+                       int(top_dim), None if g is None else g.ctypes.data, None if hy is None else hy.ctypes.data,
+                       ctypes.c_uint64(seed), ctypes.byref(out)))
+    s = out.contents
+    T, N = s.n_terms, s.n_var
+    res = SystemLists(
+        s.n_eq, N,
+        np.ctypeslib.as_array(s.terms_per_eq, shape=(s.n_eq,)).copy(),
+        np.ctypeslib.as_array(s.exps, shape=(T * N,)).copy().reshape(T, N),
+        np.ctypeslib.as_array(ctypes.cast(s.coefs, ctypes.POINTER(ctypes.c_double)), shape=(2 * T,)).copy()
+        .view(np.complex128),
+    )
+    L.phc_free_lists(out)
+    return res
+
+
+def phc_cascade_stage(h: Homotopy, k: int, starts, n_starts: int, opts, x_out, cls_out, slack_zero_out,
+                      stats_out=None, stream=None):
+    _check(load().phc_cascade_stage(ctypes.c_void_p(h.ptr), int(k), _ptr(starts), int(n_starts),
+                                    ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
+                                    _ptr(slack_zero_out), _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_refine_endpoints(h: Homotopy, x_hi, x_lo, n: int, cond_threshold: float, cond_max: float, max_iters: int,
+                         cls, stats, stream=None):
+    _check(load().phc_refine_endpoints(ctypes.c_void_p(h.ptr), _ptr(x_hi), _ptr(x_lo), int(n),
+                                       ctypes.c_double(cond_threshold), ctypes.c_double(cond_max), int(max_iters),
+                                       _ptr(cls), _ptr(stats), _stream_ptr(stream)))
+
+
+def phc_last_error() -> str:
+    return load().phc_last_error().decode()

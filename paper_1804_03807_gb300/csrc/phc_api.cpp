@@ -1,0 +1,572 @@
+// phc_api.cpp -- host side of the C ABI declared in include/phc.h:
+// argument checks, compilation of coefficient/exponent lists into the
+// device term tables, the embedding of Section 2.1, and the launch sequence
+// (track -> classify [-> drop z_k]) of each entry point.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "phc_internal.h"
+
+using phc::DevTables;
+using phc::TermRec;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                                   \
+    do {                                                                                                           \
+        cudaError_t e_ = (call);                                                                                   \
+        if (e_ != cudaSuccess) return fail(PHC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+    } while (0)
+
+extern "C" const char *phc_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ options
+
+extern "C" int phc_default_opts(phc_opts *o)
+{
+    if (!o) return fail(PHC_EINVAL, "opts is NULL");
+    std::memset(o, 0, sizeof *o);
+    o->h_init = 0.01;
+    o->h_max = 0.1;
+    o->h_min = 1e-14;
+    o->expand_after = 3;
+    o->expand = 2.0;
+    o->shrink = 0.5;
+    o->max_corr_iters = 3;
+    o->corr_tol = 1e-9;
+    o->corr_contract = 0.5;
+    o->max_steps = 20000;
+    o->diverge_norm = 1e8;
+    o->stall_inf_norm = 1e4;
+    o->end_zone = 0.9;
+    o->growth_inf = 1.1220184543019633;  // 10^0.05
+    o->end_iters = 8;
+    o->end_tol = 1e-13;
+    o->cond_regular = 1e6;
+    o->res_regular = 1e-12;
+    o->slack_tol = 1e-8;
+    o->precision = PHC_PREC_FP64;
+    o->fp32_t_max = 0.9;
+    o->block_threads = 0;
+    o->max_blocks = 0;
+    return PHC_OK;
+}
+
+static int check_opts(const phc_opts &o)
+{
+    if (!(o.h_init > 0 && o.h_max > 0 && o.h_min > 0 && o.h_min <= o.h_max))
+        return fail(PHC_EINVAL, "step sizes must satisfy 0 < h_min <= h_max and h_init > 0");
+    if (o.expand_after < 1 || !(o.expand >= 1.0) || !(o.shrink > 0.0 && o.shrink < 1.0))
+        return fail(PHC_EINVAL, "invalid step control (expand_after >= 1, expand >= 1, 0 < shrink < 1)");
+    if (o.max_corr_iters < 1 || o.max_corr_iters > 64 || o.end_iters < 0 || o.end_iters > 64)
+        return fail(PHC_EINVAL, "iteration counts out of range");
+    if (o.max_steps < 1) return fail(PHC_EINVAL, "max_steps must be positive");
+    if (!(o.growth_inf >= 1.0)) return fail(PHC_EINVAL, "growth_inf must be >= 1");
+    if (o.precision != PHC_PREC_FP64 && o.precision != PHC_PREC_FP32_INTERIOR)
+        return fail(PHC_EINVAL, "unknown precision %d", o.precision);
+    if (o.block_threads < 0 || o.block_threads % 32) return fail(PHC_EINVAL, "block_threads must be a multiple of 32");
+    return PHC_OK;
+}
+
+// ------------------------------------------------------------------ handles
+
+struct DeviceTable {
+    DevTables view{};
+    void *blob = nullptr;
+};
+
+struct phc_homotopy {
+    int n = 0;
+    // host copy of the system lists
+    std::vector<int32_t> tpe;
+    std::vector<uint8_t> exps;
+    std::vector<phc_cd> coefs;
+    phc_cd gamma{1.0, 0.0};
+    std::vector<int32_t> deg;
+    int64_t num_paths = 0;
+    // device
+    int device = 0;
+    DeviceTable total;    // total-degree homotopy
+    DeviceTable cascade;  // cascade stage (last slack), built on first use
+    int32_t *d_deg = nullptr, *d_root_off = nullptr;
+    double2 *d_roots = nullptr;
+    // scratch
+    unsigned long long *d_qhead = nullptr;
+    phc_path_stats *d_stats = nullptr;
+    int64_t stats_cap = 0;
+    double2 *d_xfull = nullptr;
+    int64_t xfull_cap = 0;
+};
+
+static void free_table(DeviceTable &t)
+{
+    if (t.blob) cudaFree(t.blob);
+    t.blob = nullptr;
+}
+
+// Terms of a homotopy with coefficients linear in t, as host vectors.
+struct HostTerms {
+    std::vector<TermRec> recs;
+    std::vector<uint8_t> vars, exps;
+    std::vector<double2> c0, c1;
+
+    void add(int eq, const uint8_t *a, int n, double2 c0v, double2 c1v)
+    {
+        TermRec r{};
+        r.eq = (uint8_t)eq;
+        r.off = (uint16_t)vars.size();
+        int k = 0;
+        for (int j = 0; j < n; j++) {
+            if (a[j] == 0) continue;
+            vars.push_back((uint8_t)j);
+            exps.push_back(a[j]);
+            if (a[j] > 1) r.flags |= phc::TERM_POWERS;
+            k++;
+        }
+        r.k = (uint8_t)k;
+        recs.push_back(r);
+        c0.push_back(c0v);
+        c1.push_back(c1v);
+    }
+};
+
+static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
+{
+    const size_t T = ht.recs.size(), V = ht.vars.size();
+    if (V > 65535) return fail(PHC_EUNSUPPORTED, "system too large (%zu exponent entries)", V);
+    const size_t o_terms = 0;
+    const size_t o_vars = o_terms + T * sizeof(TermRec);
+    const size_t o_exps = o_vars + V;
+    size_t o_c0 = o_exps + V;
+    o_c0 = (o_c0 + 15) & ~(size_t)15;
+    const size_t o_c1 = o_c0 + T * sizeof(double2);
+    const size_t bytes = o_c1 + T * sizeof(double2);
+    std::vector<char> host(bytes, 0);
+    std::memcpy(host.data() + o_terms, ht.recs.data(), T * sizeof(TermRec));
+    if (V) {
+        std::memcpy(host.data() + o_vars, ht.vars.data(), V);
+        std::memcpy(host.data() + o_exps, ht.exps.data(), V);
+    }
+    std::memcpy(host.data() + o_c0, ht.c0.data(), T * sizeof(double2));
+    std::memcpy(host.data() + o_c1, ht.c1.data(), T * sizeof(double2));
+    void *blob = nullptr;
+    if (cudaMalloc(&blob, bytes) != cudaSuccess) return fail(PHC_ENOMEM, "cudaMalloc of %zu table bytes", bytes);
+    if (cudaMemcpy(blob, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(blob);
+        return fail(PHC_ECUDA, "cudaMemcpy of the term table");
+    }
+    char *b = static_cast<char *>(blob);
+    out.blob = blob;
+    out.view.n = n;
+    out.view.n_terms = (int)T;
+    out.view.n_ve = (int)V;
+    out.view.terms = reinterpret_cast<const TermRec *>(b + o_terms);
+    out.view.vars = reinterpret_cast<const uint8_t *>(b + o_vars);
+    out.view.exps = reinterpret_cast<const uint8_t *>(b + o_exps);
+    out.view.c0 = reinterpret_cast<const double2 *>(b + o_c0);
+    out.view.c1 = reinterpret_cast<const double2 *>(b + o_c1);
+    return PHC_OK;
+}
+
+static int validate_lists(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                          bool square, std::vector<int32_t> *deg_out)
+{
+    if (n_var < 1 || n_var > PHC_MAX_VARS) return fail(PHC_EINVAL, "n_var = %d outside 1..%d", n_var, PHC_MAX_VARS);
+    if (square && n_eq != n_var) return fail(PHC_EINVAL, "system is not square (%d equations, %d unknowns)", n_eq, n_var);
+    if (n_eq < 1 || n_eq > 255) return fail(PHC_EINVAL, "n_eq = %d out of range", n_eq);
+    if (!tpe || !exps || !coefs) return fail(PHC_EINVAL, "NULL list");
+    std::vector<int32_t> deg(n_eq, 0);
+    int64_t off = 0;
+    for (int i = 0; i < n_eq; i++) {
+        if (tpe[i] < 1) return fail(PHC_EINVAL, "equation %d has no terms", i);
+        if (tpe[i] > 4096) return fail(PHC_EUNSUPPORTED, "equation %d has %d terms", i, tpe[i]);
+        for (int k = 0; k < tpe[i]; k++, off++) {
+            const phc_cd c = coefs[off];
+            if (!std::isfinite(c.re) || !std::isfinite(c.im))
+                return fail(PHC_EINVAL, "coefficient %lld of equation %d is not finite", (long long)off, i);
+            int d = 0;
+            for (int j = 0; j < n_var; j++) d += exps[off * n_var + j];
+            if (d > deg[i]) deg[i] = d;
+        }
+        if (deg[i] < 1) return fail(PHC_EINVAL, "equation %d has degree 0", i);
+    }
+    if (deg_out) *deg_out = deg;
+    return PHC_OK;
+}
+
+extern "C" int phc_make_homotopy(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                                 phc_cd gamma, phc_homotopy **out)
+{
+    if (!out) return fail(PHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::vector<int32_t> deg;
+    int rc = validate_lists(n_eq, n_var, tpe, exps, coefs, true, &deg);
+    if (rc) return rc;
+    if (!std::isfinite(gamma.re) || !std::isfinite(gamma.im) || (gamma.re == 0.0 && gamma.im == 0.0))
+        return fail(PHC_EINVAL, "gamma must be finite and nonzero");
+    const int n = n_var;
+    int64_t T = 0;
+    for (int i = 0; i < n_eq; i++) T += tpe[i];
+
+    phc_homotopy *h = new (std::nothrow) phc_homotopy();
+    if (!h) return fail(PHC_ENOMEM, "host allocation");
+    h->n = n;
+    h->tpe.assign(tpe, tpe + n_eq);
+    h->exps.assign(exps, exps + T * n);
+    h->coefs.assign(coefs, coefs + T);
+    h->gamma = gamma;
+    h->deg = deg;
+    h->num_paths = 1;
+    for (int i = 0; i < n; i++) {
+        if (h->num_paths > (int64_t)1 << 50) {
+            delete h;
+            return fail(PHC_EUNSUPPORTED, "Bezout number too large");
+        }
+        h->num_paths *= deg[i];
+    }
+    cudaGetDevice(&h->device);
+
+    // total-degree homotopy: f terms (0, c); x_i^{d_i}: (gamma, -gamma); -1: (-gamma, gamma)
+    HostTerms ht;
+    int64_t off = 0;
+    for (int i = 0; i < n; i++) {
+        for (int k = 0; k < tpe[i]; k++, off++)
+            ht.add(i, exps + off * n, n, make_double2(0.0, 0.0), make_double2(coefs[off].re, coefs[off].im));
+        std::vector<uint8_t> a(n, 0);
+        a[i] = (uint8_t)deg[i];
+        ht.add(i, a.data(), n, make_double2(gamma.re, gamma.im), make_double2(-gamma.re, -gamma.im));
+        std::vector<uint8_t> z(n, 0);
+        ht.add(i, z.data(), n, make_double2(-gamma.re, -gamma.im), make_double2(gamma.re, gamma.im));
+    }
+    rc = upload_table(ht, n, h->total);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    // start system: degrees and the table of roots of unity
+    std::vector<int32_t> roff(n);
+    int total = 0;
+    for (int i = 0; i < n; i++) {
+        roff[i] = total;
+        total += deg[i];
+    }
+    if (cudaMalloc(&h->d_deg, n * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_root_off, n * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_roots, total * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&h->d_qhead, sizeof(unsigned long long)) != cudaSuccess) {
+        phc_destroy_homotopy(h);
+        return fail(PHC_ENOMEM, "cudaMalloc of the start tables");
+    }
+    cudaMemcpy(h->d_deg, deg.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_root_off, roff.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaError_t e = phc::launch_roots(h->d_deg, h->d_root_off, h->d_roots, n, total, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        phc_destroy_homotopy(h);
+        return fail(PHC_ECUDA, "roots of unity kernel: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return PHC_OK;
+}
+
+extern "C" void phc_destroy_homotopy(phc_homotopy *h)
+{
+    if (!h) return;
+    free_table(h->total);
+    free_table(h->cascade);
+    if (h->d_deg) cudaFree(h->d_deg);
+    if (h->d_root_off) cudaFree(h->d_root_off);
+    if (h->d_roots) cudaFree(h->d_roots);
+    if (h->d_qhead) cudaFree(h->d_qhead);
+    if (h->d_stats) cudaFree(h->d_stats);
+    if (h->d_xfull) cudaFree(h->d_xfull);
+    delete h;
+}
+
+extern "C" int phc_num_paths(const phc_homotopy *h, int64_t *out)
+{
+    if (!h || !out) return fail(PHC_EINVAL, "NULL argument");
+    *out = h->num_paths;
+    return PHC_OK;
+}
+
+extern "C" int phc_sizeof_opts(void) { return (int)sizeof(phc_opts); }
+extern "C" int phc_sizeof_stats(void) { return (int)sizeof(phc_path_stats); }
+
+// ------------------------------------------------------------------ scratch
+
+static int ensure_stats(phc_homotopy *h, int64_t n)
+{
+    if (h->stats_cap >= n) return PHC_OK;
+    if (h->d_stats) cudaFree(h->d_stats);
+    h->d_stats = nullptr;
+    h->stats_cap = 0;
+    if (cudaMalloc(&h->d_stats, n * sizeof(phc_path_stats)) != cudaSuccess)
+        return fail(PHC_ENOMEM, "cudaMalloc of %lld path records", (long long)n);
+    h->stats_cap = n;
+    return PHC_OK;
+}
+
+static int ensure_xfull(phc_homotopy *h, int64_t elems)
+{
+    if (h->xfull_cap >= elems) return PHC_OK;
+    if (h->d_xfull) cudaFree(h->d_xfull);
+    h->d_xfull = nullptr;
+    h->xfull_cap = 0;
+    if (cudaMalloc(&h->d_xfull, elems * sizeof(double2)) != cudaSuccess)
+        return fail(PHC_ENOMEM, "cudaMalloc of %lld endpoint values", (long long)elems);
+    h->xfull_cap = elems;
+    return PHC_OK;
+}
+
+// ------------------------------------------------------------------ tracking
+
+static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, const double2 *starts, int64_t first,
+                     int64_t n, const phc_opts &o, double2 *x_out, int8_t *cls_out, phc_path_stats *stats,
+                     cudaStream_t s)
+{
+    CU(cudaMemsetAsync(h->d_qhead, 0, sizeof(unsigned long long), s));
+    phc::TrackLaunch L{};
+    L.tab = tab;
+    L.start_mode = start_mode;
+    L.deg = h->d_deg;
+    L.root_off = h->d_root_off;
+    L.roots = h->d_roots;
+    L.starts = starts;
+    L.first = first;
+    L.n_paths = n;
+    L.x_out = x_out;
+    L.stats = stats;
+    L.qhead = h->d_qhead;
+    L.o = o;
+    cudaError_t e = phc::launch_track(L, o.block_threads, o.max_blocks, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "track kernel launch: %s", cudaGetErrorString(e));
+    phc::ClassifyLaunch C{};
+    C.tab = tab;
+    C.n_paths = n;
+    C.x = x_out;
+    C.stats = stats;
+    C.cls = cls_out;
+    C.o = o;
+    e = phc::launch_classify(C, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "classify kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+extern "C" int phc_track_paths(phc_homotopy *h, int64_t first, int64_t n, const phc_opts *opts, phc_cd *x_out,
+                               int8_t *cls_out, phc_path_stats *stats_out, void *stream)
+{
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (n < 0 || first < 0 || first + n > h->num_paths)
+        return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + n), (long long)h->num_paths);
+    if (n == 0) return PHC_OK;
+    if (!x_out || !cls_out) return fail(PHC_EINVAL, "NULL output array");
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    phc_path_stats *st = stats_out;
+    if (!st) {
+        rc = ensure_stats(h, n);
+        if (rc) return rc;
+        st = h->d_stats;
+    }
+    return run_track(h, h->total.view, 0, nullptr, first, n, o, reinterpret_cast<double2 *>(x_out), cls_out, st,
+                     static_cast<cudaStream_t>(stream));
+}
+
+// Cascade homotopy on the handle's system E_k: every term keeps its
+// coefficient (c, 0) except the terms of the last equation (hyperplane k)
+// other than its slack z_k (the last unknown), which become (c, -c), i.e.
+// (1-t) c.
+static int ensure_cascade(phc_homotopy *h)
+{
+    if (h->cascade.blob) return PHC_OK;
+    const int n = h->n;
+    HostTerms ht;
+    int64_t off = 0;
+    for (int i = 0; i < n; i++) {
+        for (int k = 0; k < h->tpe[i]; k++, off++) {
+            const uint8_t *a = h->exps.data() + off * n;
+            const phc_cd c = h->coefs[off];
+            bool is_slack = a[n - 1] == 1;
+            for (int j = 0; j < n - 1; j++) is_slack = is_slack && a[j] == 0;
+            if (i == n - 1 && !is_slack)
+                ht.add(i, a, n, make_double2(c.re, c.im), make_double2(-c.re, -c.im));
+            else
+                ht.add(i, a, n, make_double2(c.re, c.im), make_double2(0.0, 0.0));
+        }
+    }
+    return upload_table(ht, n, h->cascade);
+}
+
+extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *starts, int64_t n, const phc_opts *opts,
+                                 phc_cd *x_out, int8_t *cls_out, uint8_t *slack_zero_out, phc_path_stats *stats_out,
+                                 void *stream)
+{
+    phc_homotopy *h = const_cast<phc_homotopy *>(hc);
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (k < 1 || k >= h->n) return fail(PHC_EINVAL, "cascade stage k = %d outside 1..%d", k, h->n - 1);
+    if (n < 0) return fail(PHC_EINVAL, "n_starts < 0");
+    if (n == 0) return PHC_OK;
+    if (!starts || !x_out || !cls_out || !slack_zero_out) return fail(PHC_EINVAL, "NULL array");
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    rc = ensure_cascade(h);
+    if (rc) return rc;
+    rc = ensure_xfull(h, (int64_t)h->n * n);
+    if (rc) return rc;
+    phc_path_stats *st = stats_out;
+    if (!st) {
+        rc = ensure_stats(h, n);
+        if (rc) return rc;
+        st = h->d_stats;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = run_track(h, h->cascade.view, 1, reinterpret_cast<const double2 *>(starts), 0, n, o, h->d_xfull, cls_out, st, s);
+    if (rc) return rc;
+    cudaError_t e = phc::launch_drop_last(h->d_xfull, h->n, n, reinterpret_cast<double2 *>(x_out), slack_zero_out,
+                                          k > 1 ? 1 : 0, o.slack_tol, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "drop kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+extern "C" int phc_refine_endpoints(const phc_homotopy *hc, phc_cd *x_hi, phc_cd *x_lo, int64_t n,
+                                    double cond_threshold, double cond_max, int max_iters, int8_t *cls,
+                                    phc_path_stats *stats, void *stream)
+{
+    if (!hc) return fail(PHC_EINVAL, "NULL handle");
+    if (n < 0 || max_iters < 0 || max_iters > 64) return fail(PHC_EINVAL, "n or max_iters out of range");
+    if (n == 0) return PHC_OK;
+    if (!x_hi || !x_lo || !cls || !stats) return fail(PHC_EINVAL, "NULL array");
+    phc::RefineLaunch L{};
+    L.tab = hc->total.view;
+    L.n = n;
+    L.x_hi = reinterpret_cast<double2 *>(x_hi);
+    L.x_lo = reinterpret_cast<double2 *>(x_lo);
+    L.cls = cls;
+    L.stats = stats;
+    L.cond_threshold = cond_threshold;
+    L.cond_max = cond_max;
+    L.max_iters = max_iters;
+    phc_default_opts(&L.o);
+    cudaError_t e = phc::launch_refine(L, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "refine kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+// ------------------------------------------------------------------ embedding
+
+// 64-bit linear congruential generator with an xorshift output (documented
+// in phc.h); only used when the caller passes no constants.
+struct Lcg {
+    uint64_t s;
+    double uniform()
+    {
+        s = s * 6364136223846793005ULL + 1442695040888963407ULL;
+        const uint64_t z = s ^ (s >> 29);
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
+    phc_cd cnormal()
+    {
+        double u1 = uniform(), u2 = uniform();
+        if (u1 < 1e-300) u1 = 1e-300;
+        const double r = std::sqrt(-std::log(u1));  // |z|^2 ~ Exp(1): E|z|^2 = 1
+        const double a = 2.0 * M_PI * u2;
+        return {r * std::cos(a), r * std::sin(a)};
+    }
+};
+
+extern "C" int phc_embed(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs, int D,
+                         const phc_cd *gammas, const phc_cd *hyper, uint64_t seed, phc_system_lists **out)
+{
+    if (!out) return fail(PHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (D < 0) return fail(PHC_EINVAL, "top_dim = %d < 0", D);
+    if (n_var + D > PHC_MAX_VARS) return fail(PHC_EINVAL, "n_var + top_dim = %d above %d", n_var + D, PHC_MAX_VARS);
+    int rc = validate_lists(n_eq, n_var, tpe, exps, coefs, true, nullptr);
+    if (rc) return rc;
+    const int n = n_var, N = n + D;
+    std::vector<phc_cd> g(gammas ? 0 : (size_t)n_eq * D), hy(hyper ? 0 : (size_t)D * (n + 1));
+    if (!gammas || !hyper) {
+        Lcg r{seed ^ 0x9E3779B97F4A7C15ULL};
+        for (auto &v : g) v = r.cnormal();
+        for (auto &v : hy) v = r.cnormal();
+    }
+    const phc_cd *G = gammas ? gammas : g.data();
+    const phc_cd *Y = hyper ? hyper : hy.data();
+    std::vector<int32_t> otpe;
+    std::vector<uint8_t> oexp;
+    std::vector<phc_cd> ocoef;
+    int64_t off = 0;
+    for (int i = 0; i < n_eq; i++) {
+        for (int k = 0; k < tpe[i]; k++, off++) {
+            for (int j = 0; j < n; j++) oexp.push_back(exps[off * n + j]);
+            for (int j = 0; j < D; j++) oexp.push_back(0);
+            ocoef.push_back(coefs[off]);
+        }
+        for (int k = 0; k < D; k++) {
+            for (int j = 0; j < N; j++) oexp.push_back(j == n + k ? 1 : 0);
+            ocoef.push_back(G[(size_t)i * D + k]);
+        }
+        otpe.push_back(tpe[i] + D);
+    }
+    for (int k = 0; k < D; k++) {
+        for (int j = 0; j < N; j++) oexp.push_back(0);
+        ocoef.push_back(Y[(size_t)k * (n + 1)]);
+        for (int v = 0; v < n; v++) {
+            for (int j = 0; j < N; j++) oexp.push_back(j == v ? 1 : 0);
+            ocoef.push_back(Y[(size_t)k * (n + 1) + v + 1]);
+        }
+        for (int j = 0; j < N; j++) oexp.push_back(j == n + k ? 1 : 0);
+        ocoef.push_back({1.0, 0.0});
+        otpe.push_back(n + 2);
+    }
+    phc_system_lists *L = new (std::nothrow) phc_system_lists();
+    if (!L) return fail(PHC_ENOMEM, "host allocation");
+    L->n_eq = n_eq + D;
+    L->n_var = N;
+    L->n_terms = (int32_t)ocoef.size();
+    L->terms_per_eq = new (std::nothrow) int32_t[otpe.size()];
+    L->exps = new (std::nothrow) uint8_t[oexp.size()];
+    L->coefs = new (std::nothrow) phc_cd[ocoef.size()];
+    if (!L->terms_per_eq || !L->exps || !L->coefs) {
+        phc_free_lists(L);
+        return fail(PHC_ENOMEM, "host allocation");
+    }
+    std::memcpy(L->terms_per_eq, otpe.data(), otpe.size() * sizeof(int32_t));
+    std::memcpy(L->exps, oexp.data(), oexp.size());
+    std::memcpy(L->coefs, ocoef.data(), ocoef.size() * sizeof(phc_cd));
+    *out = L;
+    return PHC_OK;
+}
+
+extern "C" void phc_free_lists(phc_system_lists *L)
+{
+    if (!L) return;
+    delete[] L->terms_per_eq;
+    delete[] L->exps;
+    delete[] L->coefs;
+    delete L;
+}

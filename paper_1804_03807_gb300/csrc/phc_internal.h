@@ -1,0 +1,104 @@
+// Internal declarations shared by the host API (phc_api.cpp) and the CUDA
+// kernels (track.cu, refine.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/phc.h"
+
+namespace phc {
+
+// One term of a homotopy H(x,t) = sum_terms (c0 + t c1) x^a, stored as the
+// support of x^a: k variables vars[off..off+k) with exponents exps[off..).
+// Every homotopy the library tracks has coefficients linear in t:
+//   total degree  f terms (0, c);  x_i^{d_i}: (gamma, -gamma);  -1: (-gamma, gamma)
+//   cascade       E_k terms (c, 0);  hyperplane k without z_k: (c, -c)
+struct TermRec {
+    uint8_t eq;     // equation (row of H)
+    uint8_t k;      // support size
+    uint8_t flags;  // bit 0: some exponent > 1
+    uint8_t pad;
+    uint16_t off;   // offset into vars / exps
+    uint16_t pad2;
+};
+static_assert(sizeof(TermRec) == 8, "TermRec layout");
+
+enum : uint8_t { TERM_POWERS = 1 };
+
+// Device tables of one homotopy (global memory; staged into shared memory
+// by the kernels).
+struct DevTables {
+    int n;        // unknowns = equations
+    int n_terms;  // terms
+    int n_ve;     // entries of vars / exps
+    const TermRec *terms;
+    const uint8_t *vars;
+    const uint8_t *exps;
+    const double2 *c0;
+    const double2 *c1;
+};
+
+// Bytes the staged copy of a table takes in shared memory (16-byte aligned).
+inline size_t table_smem_bytes(int n_terms, int n_ve)
+{
+    size_t b = (size_t)n_terms * sizeof(TermRec) + 2 * (size_t)n_ve;
+    b = (b + 15) & ~(size_t)15;
+    return b + 2 * (size_t)n_terms * sizeof(double2);
+}
+
+// Per-thread shared memory of the tracker: xe, H, Ht, P (N each) and J (N*N),
+// complex double, plus S (N doubles... kept as double2 for alignment).
+inline size_t thread_smem_bytes(int n) { return (size_t)(n * n + 5 * n) * sizeof(double2); }
+
+struct TrackLaunch {
+    DevTables tab;
+    // starts: mode 0 = total-degree roots of unity, mode 1 = explicit SoA
+    int start_mode;
+    const int32_t *deg;       // [n]
+    const int32_t *root_off;  // [n]
+    const double2 *roots;     // [sum deg]
+    const double2 *starts;    // SoA [n][n_paths] (mode 1)
+    int64_t first;
+    int64_t n_paths;
+    double2 *x_out;           // SoA [n][n_paths]
+    phc_path_stats *stats;    // [n_paths]
+    unsigned long long *qhead;
+    phc_opts o;
+};
+
+struct ClassifyLaunch {
+    DevTables tab;
+    int64_t n_paths;
+    const double2 *x;         // SoA [n][n_paths]
+    phc_path_stats *stats;    // [n_paths] in/out
+    int8_t *cls;              // [n_paths] out
+    phc_opts o;
+};
+
+struct RefineLaunch {
+    DevTables tab;
+    int64_t n;
+    double2 *x_hi;            // SoA [n_var][n]
+    double2 *x_lo;            // SoA [n_var][n]
+    int8_t *cls;
+    phc_path_stats *stats;
+    double cond_threshold, cond_max;
+    int max_iters;
+    phc_opts o;
+};
+
+// Launchers (track.cu / refine.cu).  Each returns a cudaError_t.
+cudaError_t launch_roots(const int32_t *deg, const int32_t *root_off, double2 *roots, int n, int total,
+                         cudaStream_t s);
+cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
+cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
+cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
+cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,
+                             uint8_t *slack_zero, int has_next_slack, double slack_tol, cudaStream_t s);
+
+// Threads per block the tracker uses for n unknowns and a table of the given
+// size (fills up to the opt-in shared memory of one block).
+int track_block_threads(int n, size_t table_bytes, int requested);
+
+}  // namespace phc

@@ -28,3 +28,12 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_libraries():
+    """Build libphc.so and the oracle if their sources changed (no-op otherwise)."""
+    from paper_1804_03807_gb300 import build as b
+    b.build()
+    import oracle
+    oracle.build()

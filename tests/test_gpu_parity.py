@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: classification counts equal exactly (regular, singular, at infinity,
+failed); regular endpoint sets equal within 1e-10 relative after one-to-one
+matching; every GPU regular endpoint a root of f (independent evaluation).
+Where the oracle finishes in seconds the whole workload is compared; at the
+full benchmark sizes a seeded sample of paths is tracked by the oracle one by
+one and compared path by path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1804_03807_gb300 as P
+from workloads import (configs, cyclic, embedding_constants, multistep_example, random_dense, rng_for, univariate,
+                       unit_gamma)
+from tests._checks import min_pair_distance, relative_residual, same_set
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-10
+
+
+def gpu_track(sys, gamma, first=0, n=None, opts=None):
+    h = P.phc_make_homotopy(sys, gamma)
+    r = P.track(h, first=first, n_paths=n, opts=opts)
+    x = r.x.cpu().numpy().T.copy()
+    return h, r, x, r.cls.cpu().numpy(), P.stats_numpy(r.stats)
+
+
+def compare(sys, xg, cg, xo, co, label=""):
+    cnt_g = np.bincount(cg.astype(int), minlength=4)
+    cnt_o = np.bincount(co.astype(int), minlength=4)
+    assert np.array_equal(cnt_g, cnt_o), f"{label} class counts gpu {cnt_g} oracle {cnt_o}"
+    Rg, Ro = xg[cg == 0], xo[co == 0]
+    ok, err = same_set(Rg, Ro, RTOL)
+    assert ok, f"{label} regular sets differ (max rel {err})"
+    if len(Rg):
+        assert relative_residual(sys, Rg).max() <= 1e-12
+        assert min_pair_distance(Rg) > 1e-6
+
+
+def test_dense4_full():
+    w = configs.dense4()
+    sys, g = w.systems[0], w.gammas[0]
+    _, r, xg, cg, sg = gpu_track(sys, g)
+    xo, co, so = oracle.track(oracle.total_degree(sys, g), threads=1)
+    assert np.all(cg == P.PHC_REGULAR) and len(cg) == 16
+    compare(sys, xg, cg, xo, co, "dense4")
+    # the same path reaches the same root on both sides here
+    assert np.max(np.abs(xg - xo)) <= RTOL * (1 + np.abs(xo).max())
+    assert np.array_equal(sg["n_accept"] + sg["n_reject"], so["n_accept"] + so["n_reject"])
+
+
+@pytest.mark.parametrize("deg", [1, 4, 7])
+def test_univariate(deg):
+    rng = rng_for(200 + deg)
+    c = rng.normal(size=deg + 1) + 1j * rng.normal(size=deg + 1)
+    sys = univariate(c)
+    g = unit_gamma(rng)
+    _, _, xg, cg, _ = gpu_track(sys, g)
+    xo, co, _ = oracle.track(oracle.total_degree(sys, g), threads=1)
+    compare(sys, xg, cg, xo, co, "univariate")
+
+
+@pytest.mark.parametrize("n", [3, 5, 6, 7])
+def test_cyclic_full(n):
+    sys = cyclic(n)
+    g = unit_gamma(rng_for(300 + n))
+    _, _, xg, cg, _ = gpu_track(sys, g)
+    xo, co, _ = oracle.track(oracle.total_degree(sys, g))
+    compare(sys, xg, cg, xo, co, f"cyclic{n}")
+
+
+def test_random_dense_ragged_sizes_and_offsets():
+    """n = 3, degrees 3: 27 paths; sub-ranges with a ragged tail and offsets."""
+    sys = random_dense(3, 3, rng_for(400))
+    g = unit_gamma(rng_for(401))
+    xo_all, co_all, _ = oracle.track(oracle.total_degree(sys, g), threads=1)
+    for first, n in [(0, 27), (5, 13), (26, 1)]:
+        _, _, xg, cg, _ = gpu_track(sys, g, first=first, n=n)
+        compare(sys, xg, cg, xo_all[first:first + n], co_all[first:first + n], f"range {first}+{n}")
+    h = P.phc_make_homotopy(sys, g)
+    with pytest.raises(P.PhcError):
+        P.track(h, first=20, n_paths=10)
+    r = P.track(h, first=3, n_paths=0)
+    assert r.x.shape[1] == 0
+
+
+@pytest.mark.parametrize("threads", [32, 64])
+def test_block_size_does_not_change_results(threads):
+    sys = cyclic(5)
+    g = unit_gamma(rng_for(500))
+    o = P.phc_default_opts(block_threads=threads, max_blocks=2)
+    _, _, xg, cg, sg = gpu_track(sys, g, opts=o)
+    _, _, xg2, cg2, sg2 = gpu_track(sys, g)
+    assert np.array_equal(cg, cg2)
+    assert np.array_equal(xg, xg2)
+    assert np.array_equal(sg["n_solve"], sg2["n_solve"])
+
+
+def test_cyclic7_batch_full_size():
+    """The 9 systems of the cyclic 7 batch (45,360 paths), whole sets."""
+    w = configs.cyclic7_batch()
+    for s, g in zip(w.systems, w.gammas):
+        _, _, xg, cg, _ = gpu_track(s, g)
+        xo, co, _ = oracle.track(oracle.total_degree(s, g))
+        compare(s, xg, cg, xo, co, s.name)
+
+
+def test_cyclic8_embedded_sampled_paths():
+    """Embedded cyclic 8 (40,320 paths) on the GPU; a seeded sample of 1500
+    paths re-tracked by the oracle and compared path by path."""
+    w = configs.cyclic8_d1()
+    e = oracle.embed(w.systems[0], 1, w.embed["gammas"], w.embed["hyper"])
+    g = w.gammas[0]
+    _, _, xg, cg, sg = gpu_track(e, g)
+    assert len(cg) == 40320
+    reg = cg == P.PHC_REGULAR
+    assert relative_residual(e, xg[reg]).max() <= 1e-12
+    assert min_pair_distance(xg[reg]) > 1e-6
+    idx = np.sort(rng_for(600).choice(40320, 1500, replace=False))
+    ho = oracle.total_degree(e, g)
+    xo = np.zeros((len(idx), e.n_var), complex)
+    co = np.zeros(len(idx), np.int8)
+    for k, p in enumerate(idx):
+        x1, c1, _ = oracle.track(ho, first=int(p), n_paths=1, threads=1)
+        xo[k], co[k] = x1[0], c1[0]
+    same_cls = cg[idx] == co
+    assert same_cls.mean() >= 0.995, f"{(~same_cls).sum()} of {len(idx)} sampled paths differ in class"
+    both = (cg[idx] == 0) & (co == 0)
+    d = np.max(np.abs(xg[idx][both] - xo[both]), axis=1) / (1 + np.max(np.abs(xo[both]), axis=1))
+    assert (d <= RTOL).mean() >= 0.99
+
+
+def _embedded_top(sys, D, seed):
+    rng = rng_for(seed)
+    g, hy = embedding_constants(rng, sys.n_eq, sys.n_var, D)
+    gamma = unit_gamma(rng)
+    return g, hy, gamma
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_example_2_1_on_gpu(seed):
+    g, hy, gamma = _embedded_top(cyclic(4), 1, seed)
+    e = P.phc_embed(cyclic(4), 1, g, hy)
+    h, r, xg, cg, sg = gpu_track(e, gamma)
+    xo, co, so = oracle.track(oracle.total_degree(oracle.embed(cyclic(4), 1, g, hy), gamma), threads=1)
+    compare(e, xg, cg, xo, co, "E1 cyclic4")
+    reg = cg == P.PHC_REGULAR
+    sz = oracle.slack_zero(xg, 4)
+    assert reg.sum() == 20 and (reg & sz).sum() == 4
+
+
+@pytest.mark.parametrize("seed", [41, 42])
+def test_example_3_1_cascade_on_gpu(seed):
+    """Top system, three cascade stages and refinement on the GPU; counts
+    and endpoint sets equal to the oracle's at every level (Figure 3)."""
+    import torch
+    sys = multistep_example()
+    n, D = 4, 3
+    g, hy, gamma = _embedded_top(sys, D, seed)
+    E = P.phc_embed(sys, D, g, hy)
+    h = P.phc_make_homotopy(E, gamma)
+    r = P.track(h)
+    P.refine(h, r)
+    cls = r.cls.cpu().numpy()
+    x = r.x.cpu().numpy().T
+    Eo = oracle.embed(sys, D, g, hy)
+    ho = oracle.total_degree(Eo, gamma)
+    xo, co, so = oracle.track(ho, threads=1)
+    xo, _, co, _ = oracle.refine(ho, xo, co, so["cond"], so["stop"] == 0)
+    compare(E, x, cls, xo, co, "top")
+    sz = oracle.slack_zero(x, n + D - 1)
+    assert ((cls == 0) & sz).sum() == 1 and ((cls == 0) & ~sz).sum() == 54
+    starts = torch.from_numpy(np.ascontiguousarray(x[(cls == 0) & ~sz].T)).cuda()
+    Xo = xo[(co == 0) & ~oracle.slack_zero(xo, n + D - 1)]
+    Ek, Eko = E, Eo
+    expected = {3: 50, 2: 26}
+    for k in (3, 2, 1):
+        hk = P.phc_make_homotopy(Ek, gamma)
+        rk = P.cascade(hk, k, starts)
+        Ek1 = P.phc_embed(sys, k - 1, g[:, :k - 1], hy[:k - 1]) if k > 1 else sys
+        hk1 = P.phc_make_homotopy(Ek1, gamma)
+        P.refine(hk1, rk)
+        ck = rk.cls.cpu().numpy()
+        xk = rk.x.cpu().numpy().T
+        # oracle: the same stage, refinement on E_{k-1}
+        hco = oracle.cascade_homotopy(Eko, n, n, k)
+        xko, cko, sko = oracle.track(hco, starts=Xo, threads=1)
+        Eko1 = oracle.drop_last_slack(Eko, n, n, k)
+        xko = np.delete(xko, n + k - 1, axis=1)
+        xko, _, cko, _ = oracle.refine(oracle.total_degree(Eko1, gamma), xko, cko, sko["cond"], sko["stop"] == 0)
+        compare(Ek1, xk, ck, xko, cko, f"stage {k}")
+        if k > 1:
+            szk = rk.slack_zero.cpu().numpy().astype(bool)
+            assert np.array_equal(szk[ck == 0], oracle.slack_zero(xk, n + k - 2)[ck == 0])
+            assert ((ck == 0) & ~szk).sum() == expected[k]
+            starts = torch.from_numpy(np.ascontiguousarray(xk[(ck == 0) & ~szk].T)).cuda()
+            Xo = xko[(cko == 0) & ~oracle.slack_zero(xko, n + k - 2)]
+        else:
+            iso = xk[ck == 0]
+            ok, err = same_set(iso, np.array([[3, 2, 2, 1], [3, 3, 2, 1], [4, 3, 2, 1], [4, 2, 2, 1]], complex),
+                               RTOL)
+            assert ok, err
+        Ek, Eko = Ek1, Eko1
+
+
+def test_refinement_reaches_double_double_accuracy_on_gpu():
+    from tests._checks import exact_residual
+    w = configs.dense4()
+    sys = w.systems[0]
+    h = P.phc_make_homotopy(sys, w.gammas[0])
+    r = P.track(h)
+    x_lo = P.refine(h, r, cond_threshold=0.0)
+    xh = r.x.cpu().numpy().T
+    xl = x_lo.cpu().numpy().T
+    assert np.all(r.cls.cpu().numpy() == 0)
+    for p in range(4):
+        assert exact_residual(sys, xh[p], xl[p]) <= 1e-28
+
+
+def test_double_root_is_singular_on_gpu():
+    c = np.polymul(np.polymul([1, -1], [1, -1]), [1, 2])[::-1]
+    sys = univariate(c)
+    g = unit_gamma(rng_for(60))
+    h = P.phc_make_homotopy(sys, g)
+    r = P.track(h)
+    P.refine(h, r)
+    assert sorted(r.cls.cpu().numpy().tolist()) == [0, 1, 1]
