@@ -1,0 +1,413 @@
+"""Benchmark: paths/s of the GPU path tracker on the cyclic 7 batch.
+
+Workload: cyclic 7-roots plus 8 copies with its supports and random complex
+Gaussian coefficients (seed 2), total-degree homotopies, 9 x 5040 = 45,360
+paths per step.  One step = track every path of the 9 systems (one CUDA
+stream per system), classify the endpoints and refine the ill-conditioned
+ones in double double.  The homotopy tables are resident in HBM before the
+timed region; the L2 is flushed (a 256 MiB write) between steps.
+
+Lines printed (rank 0, one JSON object): the device-timed value, an
+end-to-end value through the C ABI with host buffers (table upload and
+endpoint download inside the timed region), the roofline of the dominant
+kernel (track_kernel, FP64 ALU bound), the oracle timed on the host cores,
+SM clocks sampled during the timed region and the kernel launch count.
+
+``--impl reference`` times the CPU oracle (the reference of this project)
+on the same workload instead.  ``--gpus N`` under torchrun runs N
+independent replicas (paths are independent; nothing is exchanged).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "paths/s at 1e-10 endpoint acc; % FP64 peak; served p50/p99 latency"
+WORKLOAD = "cyclic7 + 8 random-coefficient copies (seed 2): 9 x 5040 = 45,360 total-degree paths"
+# FP64 peak: 152 SMs x 2 FP64 FMA lanes/clk x 2 flops x 2.07 GHz = 1.259 TFLOP/s (the nominal 1.25);
+# an FMA-chain probe on this GPU measured 1.257 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ------------------------------------------------------------------ flop model
+
+def unit_flops(tab_terms, n: int) -> float:
+    """Algorithmic FP64 flops of one evaluate+factor+solve unit of a homotopy
+    whose terms are (support size k, sum of (a_j - 1)) pairs: per term the
+    powers and common factor (sum (a_j-1) complex multiplications), the value
+    and gradient by prefix/suffix products (3k - 2), c(t) x^a and c1 x^a (2),
+    accumulation into H, H_t and k Jacobian entries (k + 2 complex
+    additions), c(t) = c0 + t c1 (4 flops); complex LU 8n^3/3, one solve 8n^2.
+    A complex multiplication is 6 flops, an addition 2."""
+    f = 0.0
+    for k, extra in tab_terms:
+        if k == 0:
+            f += 4 + 2 * 2
+            continue
+        f += 6 * (extra + 3 * k - 2 + 2) + 2 * (k + 2) + 4
+    f += 8.0 * n ** 3 / 3.0 + 8.0 * n ** 2
+    return f
+
+
+def homotopy_terms(sys_):
+    """(k, sum(a_j-1)) of the terms of the total-degree homotopy of sys_."""
+    out = []
+    degs = sys_.degrees()
+    for e in sys_.exps.astype(int):
+        nz = e[e > 0]
+        out.append((len(nz), int((nz - 1).sum())))
+    for d in degs:
+        out.append((1, int(d) - 1))  # x_i^{d_i}
+        out.append((0, 0))  # constant
+    return out
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+
+def oracle_sample(systems, gammas, per_system: int, seed: int = 7):
+    """Time the oracle (work crew on every host core) on a seeded sample of
+    per_system paths of every system; returns (paths/s, cores, paths, secs)."""
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cores = oracle.host_threads()
+    jobs = []
+    for s, g in zip(systems, gammas):
+        h = oracle.total_degree(s, g)
+        P = oracle.num_paths(h)
+        first = int(rng.integers(0, max(1, P - per_system)))
+        jobs.append((h, first, min(per_system, P)))
+    t0 = time.perf_counter()
+    n = 0
+    for h, first, k in jobs:
+        oracle.track(h, first=first, n_paths=k, threads=cores)
+        n += k
+    dt = time.perf_counter() - t0
+    return n / dt, cores, n, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from workloads import configs
+    w = configs.cyclic7_batch()
+    per = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample(w.systems, w.gammas, max(50, per // 10))
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, cores, n, dt = oracle_sample(w.systems, w.gammas, per)
+        vals.append(v)
+        secs.append(dt)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{per} paths per system, 9 systems, seeded offsets"},
+        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per} x 9 paths per step"},
+        "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1804_03807_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1804_03807_gb300 as P
+    from workloads import configs
+
+    w = configs.cyclic7_batch()
+    systems, gammas = w.systems, w.gammas
+    hs = [P.phc_make_homotopy(s, g) for s, g in zip(systems, gammas)]
+    npaths = [P.phc_num_paths(h) for h in hs]
+    total_paths = sum(npaths)
+    streams = [torch.cuda.Stream(device=dev) for _ in hs]
+    main = torch.cuda.current_stream(dev)
+    outs = []
+    for h, n in zip(hs, npaths):
+        x = torch.empty((h.n, n), dtype=torch.complex128, device=dev)
+        cls = torch.empty(n, dtype=torch.int8, device=dev)
+        st = torch.empty((n, P.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+        xlo = torch.empty_like(x)
+        outs.append((x, cls, st, xlo))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    opts = P.phc_default_opts()
+    launches_per_step = 3 * len(hs)  # track, classify, refine per system
+
+    def step(ev_pairs=None):
+        ev_start = torch.cuda.Event(enable_timing=True)
+        ev_start.record(main)
+        for i, (h, n, s) in enumerate(zip(hs, npaths, streams)):
+            s.wait_event(ev_start)
+            x, cls, st, xlo = outs[i]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            P.phc_track_paths(h, 0, n, opts, x, cls, st, stream=s)
+            e1.record(s)
+            P.phc_refine_endpoints(h, x, xlo, n, 1e6, 1e12, 8, cls, st, stream=s)
+            if ev_pairs is not None:
+                ev_pairs.append((e0, e1))
+        for s in streams:
+            main.wait_stream(s)
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1)
+    torch.cuda.synchronize()
+
+    # flop model per unit, per system
+    uf = [unit_flops(homotopy_terms(s), s.n_var) for s in systems]
+
+    barrier(world)
+    torch.cuda.synchronize()
+    times, kernel_pairs = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            pairs = []
+            a.record(main)
+            step(pairs)
+            b.record(main)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+            kernel_pairs.append((a, pairs))
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.summary()
+    total_ms = max_over_ranks(float(np.sum(times)), world, dev)
+    value = world * total_paths * args.steps / (total_ms / 1e3)
+
+    # roofline of track_kernel: algorithmic flops / duration of the tracking calls
+    units = []
+    for i in range(len(hs)):
+        stn = P.stats_numpy(outs[i][2])
+        units.append(int(stn["n_solve"].sum()))
+    flops_step = sum(u * f for u, f in zip(units, uf))
+    # the 9 tracking calls overlap on 9 streams: their kernel time in a step
+    # is the span from the fan-out event to the last call's end
+    spans = [max(a0.elapsed_time(p[1]) for p in pairs) for a0, pairs in kernel_pairs]
+    kern_ms = float(np.mean(spans))
+    achieved = flops_step / (kern_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                "kernel": "track_kernel<7> (+classify)", "flops_per_step": flops_step,
+                "units_per_step": int(sum(units)), "peak_source": "derived: 152 SMs x 4 flops/clk x 2.07 GHz"}
+
+    # end to end through the C ABI with host buffers
+    e2e = end_to_end(P, systems, gammas, dev, args)
+
+    # correctness summary of the last step
+    counts = np.zeros(4, int)
+    for x, cls, st, xlo in outs:
+        counts += np.bincount(cls.cpu().numpy(), minlength=4)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(total_ms / args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas x{world}", "classes_last_step": counts.tolist()},
+        "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, n, dt = oracle_sample(systems, gammas, args.ref_sample)
+        line["cpu_baseline"] = {"value": v, "unit": "paths/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n} paths ({args.ref_sample} per system), {dt:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def end_to_end(P, systems, gammas, dev, args):
+    """Same metric through the C ABI from host lists to host endpoints: per
+    step every homotopy is built from host lists (tables uploaded), tracked,
+    refined, and endpoints and classes are copied to pinned host memory."""
+    import torch
+    h2d = 0
+    d2h = 0
+    pinned = []
+    for s in systems:
+        n = s.bezout()
+        pinned.append((torch.empty((s.n_var, n), dtype=torch.complex128, pin_memory=True),
+                       torch.empty(n, dtype=torch.int8, pin_memory=True)))
+    streams = [torch.cuda.Stream(device=dev) for _ in systems]
+
+    def one():
+        nonlocal h2d, d2h
+        hs = []
+        bytes_in = 0
+        for s, g in zip(systems, gammas):
+            hs.append(P.phc_make_homotopy(s, g))
+            bytes_in += s.exps.nbytes + s.coefs.nbytes + s.terms_per_eq.nbytes
+        bytes_out = 0
+        for i, (h, s, st) in enumerate(zip(hs, systems, streams)):
+            with torch.cuda.stream(st):
+                r = P.track(h, stream=st, device=dev)
+                xlo = torch.empty_like(r.x)
+                P.phc_refine_endpoints(h, r.x, xlo, r.x.shape[1], 1e6, 1e12, 8, r.cls, r.stats, stream=st)
+                pinned[i][0].copy_(r.x, non_blocking=True)
+                pinned[i][1].copy_(r.cls, non_blocking=True)
+                bytes_out += r.x.numel() * 16 + r.cls.numel()
+        torch.cuda.synchronize()
+        return bytes_in, bytes_out
+
+    one()
+    t0 = time.perf_counter()
+    reps = max(1, min(args.steps, 3))
+    for _ in range(reps):
+        bi, bo = one()
+    dt = time.perf_counter() - t0
+    total = sum(s.bezout() for s in systems)
+    return {"value": total * reps / dt, "unit": "paths/s", "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+            "steps": reps}
+
+
+def profile_case():
+    """One random-coefficient cyclic 7 system (5040 paths), tracked twice."""
+    import torch
+    import paper_1804_03807_gb300 as P
+    from workloads import configs
+    w = configs.cyclic7_batch()
+    h = P.phc_make_homotopy(w.systems[1], w.gammas[1])
+    for _ in range(2):
+        r = P.track(h)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_case": w.systems[1].name, "classes": np.bincount(r.cls.cpu().numpy(), minlength=4).tolist(),
+                      "units": int(P.stats_numpy(r.stats)["n_solve"].sum())}))
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--ref-sample", type=int, default=400, help="oracle paths per system per step")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per track launch, if captured")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="track one system of the batch twice (a small case for ncu) and exit")
+    args = ap.parse_args(argv)
+    if args.profile_case:
+        return profile_case()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
