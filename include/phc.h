@@ -211,6 +211,27 @@ int phc_refine_endpoints(const phc_homotopy *h, phc_cd *x_hi_io, phc_cd *x_lo_ou
                          double cond_threshold, double cond_max, int max_iters, int8_t *cls_io,
                          phc_path_stats *stats_io, void *cuda_stream);
 
+/* Largest n_paths phc_track_paths_noalloc accepts with stats_out == NULL. */
+#define PHC_NOALLOC_MAX_PATHS 52428
+
+/* phc_track_paths without any device allocation during the call (the paper
+ * has no counterpart; this is a service to callers that cannot allocate).
+ * Same arguments, outputs and errors as phc_track_paths.  Callers whose
+ * device memory belongs to another allocator (a framework's caching
+ * allocator that reserved the free memory up front) or that must not enter
+ * the allocator after start-up (latency-critical serving loops) use it.
+ * Its scratch -- the path-queue counter and, when stats_out is NULL, the
+ * per-path records -- is one static device array of 256 + 80 *
+ * PHC_NOALLOC_MAX_PATHS bytes (about 4 MiB) that every GPU loading the
+ * library holds until exit.  The first call on a device (with that device
+ * current) looks up the array's address; make it before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the
+ * counter is cleared at each call): calls that overlap on the GPU race, so
+ * serialise them.  With stats_out == NULL, n_paths above
+ * PHC_NOALLOC_MAX_PATHS is rejected with PHC_EUNSUPPORTED. */
+int phc_track_paths_noalloc(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts,
+                            phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
+
 /* Message of the last non-OK return on the calling thread ("" if none). */
 const char *phc_last_error(void);
 

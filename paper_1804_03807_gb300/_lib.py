@@ -20,11 +20,12 @@ PHC_REGULAR, PHC_SINGULAR, PHC_AT_INFINITY, PHC_FAILED = 0, 1, 2, 3
 PHC_STOP_REACHED, PHC_STOP_DIVERGED, PHC_STOP_STEP_MIN, PHC_STOP_BUDGET, PHC_STOP_NONFINITE = 0, 1, 2, 3, 4
 PHC_PREC_FP64, PHC_PREC_FP32_INTERIOR = 0, 1
 PHC_MAX_VARS = 12
+PHC_NOALLOC_MAX_PATHS = 52428
 
 EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
-    "phc_sizeof_stats",
+    "phc_sizeof_stats", "phc_track_paths_noalloc",
 ]
 
 
@@ -84,6 +85,7 @@ def load() -> ctypes.CDLL:
     L.phc_make_homotopy.argtypes = [i32, i32, vp, vp, vp, phc_cd, ctypes.POINTER(vp)]
     L.phc_num_paths.argtypes = [vp, ctypes.POINTER(i64)]
     L.phc_track_paths.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
+    L.phc_track_paths_noalloc.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_cascade_stage.argtypes = [vp, i32, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
@@ -93,7 +95,8 @@ def load() -> ctypes.CDLL:
     L.phc_destroy_homotopy.restype = None
     L.phc_free_lists.argtypes = [ctypes.POINTER(phc_system_lists)]
     L.phc_free_lists.restype = None
-    for name in ("phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed",
+    for name in ("phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths",
+                 "phc_track_paths_noalloc", "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
@@ -171,6 +174,14 @@ def phc_track_paths(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls
     _check(load().phc_track_paths(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
                                   ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
                                   _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_track_paths_noalloc(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls_out, stats_out=None,
+                            stream=None):
+    """phc_track_paths without device allocation during the call (static scratch)."""
+    _check(load().phc_track_paths_noalloc(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
+                                          ctypes.byref(opts) if opts is not None else None, _ptr(x_out),
+                                          _ptr(cls_out), _ptr(stats_out), _stream_ptr(stream)))
 
 
 class SystemLists:

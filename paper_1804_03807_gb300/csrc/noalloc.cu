@@ -1,0 +1,120 @@
+// noalloc.cu -- phc_track_paths_noalloc: path tracking without any device
+// allocation during the call.
+//
+// phc_track_paths may call cudaMalloc when the caller passes no per-path
+// statistics array (it keeps a growing scratch buffer in the handle).  Some
+// callers cannot allocate while they run: a process whose device memory is
+// owned by another allocator (a framework's caching allocator that reserved
+// the free HBM up front, so cudaMalloc fails or fragments its pool), or a
+// latency-critical serving loop that allocates everything at start-up and
+// must not stall in the allocator afterwards.  This entry point takes its
+// scratch -- the path-queue counter and, when stats_out is NULL, the
+// per-path records the classification pass reads -- from one file-scope
+// device array of fixed size instead.
+//
+// Properties a caller must know:
+//  * The array is static device memory: every GPU that loads the library
+//    holds NOALLOC_SCRATCH_BYTES of it until the process exits.
+//  * Set-up: the first call on a device (with that device current) looks up
+//    the array's device address with cudaGetSymbolAddress; that first call
+//    should come before any stream capture.
+//  * Every call shares the one array and it keeps the last call's contents;
+//    the counter is cleared at the start of each call.  Calls that overlap on
+//    the GPU (other streams, other threads) race on it: serialise them.
+//  * With stats_out == NULL, n_paths may not exceed PHC_NOALLOC_MAX_PATHS.
+#include <mutex>
+
+#include "phc_internal.h"
+
+namespace phc {
+// implemented in phc_api.cpp: the device view of a handle's total-degree
+// homotopy and start tables, and option checking
+int handle_track_view(phc_homotopy *h, TrackLaunch *L);
+int handle_num_paths(const phc_homotopy *h, int64_t *out);
+int check_options(const phc_opts &o);
+int set_error(int code, const char *msg);
+}  // namespace phc
+
+#define NOALLOC_COUNTER_BYTES 256
+#define NOALLOC_SCRATCH_BYTES (NOALLOC_COUNTER_BYTES + (size_t)PHC_NOALLOC_MAX_PATHS * sizeof(phc_path_stats))
+
+// The scratch: bytes [0, 256) hold the queue counter, the rest the records.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_setup_mutex;
+static void *g_scratch_ptr[64];  // device address per device ordinal
+
+// Device address of g_noalloc_scratch on the current device (set-up once per
+// device).  The host-side name of the array is not a device address.
+static int scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return phc::set_error(PHC_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return phc::set_error(PHC_EUNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return phc::set_error(PHC_ECUDA, "cudaGetSymbolAddress of the no-allocation scratch failed");
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return PHC_OK;
+}
+
+extern "C" int phc_track_paths_noalloc(phc_homotopy *h, int64_t first, int64_t n, const phc_opts *opts,
+                                       phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out, void *stream)
+{
+    if (!h) return phc::set_error(PHC_EINVAL, "NULL handle");
+    int64_t total = 0;
+    int rc = phc::handle_num_paths(h, &total);
+    if (rc) return rc;
+    if (n < 0 || first < 0 || first + n > total)
+        return phc::set_error(PHC_EINVAL, "path range outside [0, number of paths)");
+    if (n == 0) return PHC_OK;
+    if (!x_out || !cls_out) return phc::set_error(PHC_EINVAL, "NULL output array");
+    if (!stats_out && n > PHC_NOALLOC_MAX_PATHS)
+        return phc::set_error(PHC_EUNSUPPORTED,
+                              "phc_track_paths_noalloc: n_paths above PHC_NOALLOC_MAX_PATHS with stats_out == NULL "
+                              "(pass a stats array or split the range)");
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    rc = phc::check_options(o);
+    if (rc) return rc;
+    void *base = nullptr;
+    rc = scratch_address(&base);
+    if (rc) return rc;
+    unsigned long long *counter = static_cast<unsigned long long *>(base);
+    phc_path_stats *st = stats_out ? stats_out
+                                   : reinterpret_cast<phc_path_stats *>(static_cast<unsigned char *>(base) +
+                                                                        NOALLOC_COUNTER_BYTES);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return phc::set_error(PHC_ECUDA, cudaGetErrorString(e));
+
+    phc::TrackLaunch L{};
+    rc = phc::handle_track_view(h, &L);
+    if (rc) return rc;
+    L.start_mode = 0;
+    L.starts = nullptr;
+    L.first = first;
+    L.n_paths = n;
+    L.x_out = reinterpret_cast<double2 *>(x_out);
+    L.stats = st;
+    L.qhead = counter;
+    L.o = o;
+    e = phc::launch_track(L, o.block_threads, o.max_blocks, s);
+    if (e != cudaSuccess) return phc::set_error(PHC_ECUDA, cudaGetErrorString(e));
+    phc::ClassifyLaunch C{};
+    C.tab = L.tab;
+    C.n_paths = n;
+    C.x = L.x_out;
+    C.stats = st;
+    C.cls = cls_out;
+    C.o = o;
+    e = phc::launch_classify(C, s);
+    if (e != cudaSuccess) return phc::set_error(PHC_ECUDA, cudaGetErrorString(e));
+    return PHC_OK;
+}

@@ -570,3 +570,29 @@ extern "C" void phc_free_lists(phc_system_lists *L)
     delete[] L->coefs;
     delete L;
 }
+
+// ------------------------------------------------------------------ internal accessors (noalloc.cu)
+
+namespace phc {
+
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int check_options(const phc_opts &o) { return check_opts(o); }
+
+int handle_num_paths(const phc_homotopy *h, int64_t *out)
+{
+    *out = h->num_paths;
+    return PHC_OK;
+}
+
+// Device view of the handle's total-degree homotopy and start tables.
+int handle_track_view(phc_homotopy *h, TrackLaunch *L)
+{
+    L->tab = h->total.view;
+    L->deg = h->d_deg;
+    L->root_off = h->d_root_off;
+    L->roots = h->d_roots;
+    return PHC_OK;
+}
+
+}  // namespace phc
