@@ -83,7 +83,7 @@ void orc_default_opts(orc_opts *o)
     o->corr_tol = 1e-9;
     o->corr_contract = 0.5;
     o->max_steps = 20000;
-    o->diverge_norm = 1e8;
+    o->diverge_norm = 1e6;
     o->stall_inf_norm = 1e4;
     o->end_zone = 0.9;
     o->growth_inf = 1.1220184543019633; /* 10^0.05 */
