@@ -2,8 +2,8 @@
 
 Workload: cyclic 7-roots plus 8 copies with its supports and random complex
 Gaussian coefficients (seed 2), total-degree homotopies, 9 x 5040 = 45,360
-paths per step.  One step = track every path of the 9 systems (one CUDA
-stream per system), classify the endpoints and refine the ill-conditioned
+paths per step.  One step = track every path of the 9 systems (one batch
+handle, one launch), classify the endpoints and refine the ill-conditioned
 ones in double double.  The homotopy tables are resident in HBM before the
 timed region; the L2 is flushed (a 256 MiB write) between steps.
 
@@ -225,97 +225,79 @@ def run_gpu(args):
 
     w = configs.cyclic7_batch()
     systems, gammas = w.systems, w.gammas
-    hs = [P.phc_make_homotopy(s, g) for s, g in zip(systems, gammas)]
-    npaths = [P.phc_num_paths(h) for h in hs]
-    total_paths = sum(npaths)
-    streams = [torch.cuda.Stream(device=dev) for _ in hs]
+    # one handle for the 9 systems (shared supports): one launch, one path queue
+    h = P.phc_make_homotopy_batch(systems, gammas)
+    total_paths = P.phc_num_paths(h)
     main = torch.cuda.current_stream(dev)
-    outs = []
-    for h, n in zip(hs, npaths):
-        x = torch.empty((h.n, n), dtype=torch.complex128, device=dev)
-        cls = torch.empty(n, dtype=torch.int8, device=dev)
-        st = torch.empty((n, P.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
-        xlo = torch.empty_like(x)
-        outs.append((x, cls, st, xlo))
+    x = torch.empty((h.n, total_paths), dtype=torch.complex128, device=dev)
+    cls = torch.empty(total_paths, dtype=torch.int8, device=dev)
+    st = torch.empty((total_paths, P.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    xlo = torch.empty_like(x)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    opts = P.phc_default_opts()
-    launches_per_step = 3 * len(hs)  # track, classify, refine per system
+    opts = P.phc_default_opts(precision=args.precision)
+    launches_per_step = 3  # track, classify, refine
 
-    def step(ev_pairs=None):
-        ev_start = torch.cuda.Event(enable_timing=True)
-        ev_start.record(main)
-        for i, (h, n, s) in enumerate(zip(hs, npaths, streams)):
-            s.wait_event(ev_start)
-            x, cls, st, xlo = outs[i]
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            P.phc_track_paths(h, 0, n, opts, x, cls, st, stream=s)
-            e1.record(s)
-            P.phc_refine_endpoints(h, x, xlo, n, 1e6, 1e12, 8, cls, st, stream=s)
-            if ev_pairs is not None:
-                ev_pairs.append((e0, e1))
-        for s in streams:
-            main.wait_stream(s)
+    def step(pair=None):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        P.phc_track_paths(h, 0, total_paths, opts, x, cls, st, stream=main)
+        e1.record(main)
+        P.phc_refine_endpoints(h, x, xlo, total_paths, 1e6, 1e12, 8, cls, st, stream=main)
+        if pair is not None:
+            pair.append((e0, e1))
 
     for _ in range(args.warmup):
         step()
         flush.fill_(1)
     torch.cuda.synchronize()
 
-    # flop model per unit, per system
-    uf = [unit_flops(homotopy_terms(s), s.n_var) for s in systems]
+    # flop model per unit (all systems share the structure)
+    uf = unit_flops(homotopy_terms(systems[0]), systems[0].n_var)
 
     barrier(world)
     torch.cuda.synchronize()
-    times, kernel_pairs = [], []
+    times, pairs = [], []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            pairs = []
             a.record(main)
             step(pairs)
             b.record(main)
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
-            kernel_pairs.append((a, pairs))
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.summary()
     total_ms = max_over_ranks(float(np.sum(times)), world, dev)
     value = world * total_paths * args.steps / (total_ms / 1e3)
 
-    # roofline of track_kernel: algorithmic flops / duration of the tracking calls
-    units = []
-    for i in range(len(hs)):
-        stn = P.stats_numpy(outs[i][2])
-        units.append(int(stn["n_solve"].sum()))
-    flops_step = sum(u * f for u, f in zip(units, uf))
-    # the 9 tracking calls overlap on 9 streams: their kernel time in a step
-    # is the span from the fan-out event to the last call's end
-    spans = [max(a0.elapsed_time(p[1]) for p in pairs) for a0, pairs in kernel_pairs]
-    kern_ms = float(np.mean(spans))
+    # roofline of track_kernel: algorithmic flops / duration of the tracking call
+    stn = P.stats_numpy(st)
+    units = int(stn["n_solve"].sum())
+    flops_step = units * uf
+    kern_ms = float(np.mean([p0.elapsed_time(p1) for p0, p1 in pairs]))
     achieved = flops_step / (kern_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
-                "kernel": "track_kernel<7> (+classify)", "flops_per_step": flops_step,
-                "units_per_step": int(sum(units)), "peak_source": "derived: 152 SMs x 4 flops/clk x 2.07 GHz"}
+                "kernel": "track_kernel<7> (+classify_kernel<7>, <0.1 %)", "flops_per_step": flops_step,
+                "units_per_step": units, "kernel_ms": kern_ms,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
 
     # end to end through the C ABI with host buffers
     e2e = end_to_end(P, systems, gammas, dev, args)
 
     # correctness summary of the last step
-    counts = np.zeros(4, int)
-    for x, cls, st, xlo in outs:
-        counts += np.bincount(cls.cpu().numpy(), minlength=4)
+    counts = np.bincount(cls.cpu().numpy(), minlength=4)
 
     line = {
         "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(total_ms / args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "flushed (256 MiB write) between steps",
+        "config": {"workload": WORKLOAD, "precision": ["fp64", "fp32-interior"][args.precision],
+                   "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas x{world}", "classes_last_step": counts.tolist()},
         "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
     }
@@ -333,44 +315,32 @@ def run_gpu(args):
 
 def end_to_end(P, systems, gammas, dev, args):
     """Same metric through the C ABI from host lists to host endpoints: per
-    step every homotopy is built from host lists (tables uploaded), tracked,
-    refined, and endpoints and classes are copied to pinned host memory."""
+    step the batch homotopy is built from host lists (tables uploaded),
+    tracked, refined, and endpoints and classes are copied to pinned host
+    memory."""
     import torch
-    h2d = 0
-    d2h = 0
-    pinned = []
-    for s in systems:
-        n = s.bezout()
-        pinned.append((torch.empty((s.n_var, n), dtype=torch.complex128, pin_memory=True),
-                       torch.empty(n, dtype=torch.int8, pin_memory=True)))
-    streams = [torch.cuda.Stream(device=dev) for _ in systems]
+    total = sum(s.bezout() for s in systems)
+    xh = torch.empty((systems[0].n_var, total), dtype=torch.complex128, pin_memory=True)
+    ch = torch.empty(total, dtype=torch.int8, pin_memory=True)
+    opts = P.phc_default_opts(precision=args.precision)
 
     def one():
-        nonlocal h2d, d2h
-        hs = []
-        bytes_in = 0
-        for s, g in zip(systems, gammas):
-            hs.append(P.phc_make_homotopy(s, g))
-            bytes_in += s.exps.nbytes + s.coefs.nbytes + s.terms_per_eq.nbytes
-        bytes_out = 0
-        for i, (h, s, st) in enumerate(zip(hs, systems, streams)):
-            with torch.cuda.stream(st):
-                r = P.track(h, stream=st, device=dev)
-                xlo = torch.empty_like(r.x)
-                P.phc_refine_endpoints(h, r.x, xlo, r.x.shape[1], 1e6, 1e12, 8, r.cls, r.stats, stream=st)
-                pinned[i][0].copy_(r.x, non_blocking=True)
-                pinned[i][1].copy_(r.cls, non_blocking=True)
-                bytes_out += r.x.numel() * 16 + r.cls.numel()
+        h = P.phc_make_homotopy_batch(systems, gammas)
+        bytes_in = sum(s.exps.nbytes + s.coefs.nbytes + s.terms_per_eq.nbytes for s in systems)
+        r = P.track(h, opts=opts, device=dev)
+        xlo = torch.empty_like(r.x)
+        P.phc_refine_endpoints(h, r.x, xlo, total, 1e6, 1e12, 8, r.cls, r.stats)
+        xh.copy_(r.x, non_blocking=True)
+        ch.copy_(r.cls, non_blocking=True)
         torch.cuda.synchronize()
-        return bytes_in, bytes_out
+        return bytes_in, r.x.numel() * 16 + r.cls.numel()
 
     one()
-    t0 = time.perf_counter()
     reps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
     for _ in range(reps):
         bi, bo = one()
     dt = time.perf_counter() - t0
-    total = sum(s.bezout() for s in systems)
     return {"value": total * reps / dt, "unit": "paths/s", "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
             "steps": reps}
 
@@ -399,6 +369,7 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=400, help="oracle paths per system per step")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per track launch, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, help="0 = FP64, 1 = FP32 interior")
     ap.add_argument("--profile-case", action="store_true",
                     help="track one system of the batch twice (a small case for ncu) and exit")
     args = ap.parse_args(argv)

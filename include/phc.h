@@ -122,7 +122,7 @@ typedef struct {
     int32_t stop;                 /* PHC_STOP_*                           */
     int32_t n_fp32;               /* evaluate + solve units in single precision */
     int32_t grew;                 /* 1 when the growth test flagged the path */
-    int32_t reserved;
+    int32_t system;               /* system of the path in a batch handle  */
 } phc_path_stats;
 
 /* Host-side system lists, library-allocated (phc_embed); free with
@@ -151,7 +151,19 @@ int phc_default_opts(phc_opts *opts);
 int phc_make_homotopy(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps,
                       const phc_cd *coefs, phc_cd gamma, phc_homotopy **out);
 
-/* Number of paths of the total-degree homotopy, prod d_i (host call). */
+/* A batch of n_systems total-degree homotopies that share the supports of
+ * one square system (terms_per_eq, exps as in phc_make_homotopy) and differ
+ * in their coefficients coefs [n_systems][T] and constants gammas
+ * [n_systems] (host arrays): the same problem solved for many coefficient
+ * values, e.g. a system and copies of it with random coefficients.  Path
+ * p of system s has the global index s * prod d_i + p, so one
+ * phc_track_paths call tracks every system in one launch; the stats record
+ * of a path names its system.  Errors as phc_make_homotopy. */
+int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps, int n_systems,
+                            const phc_cd *coefs, const phc_cd *gammas, phc_homotopy **out);
+
+/* Number of paths of the total-degree homotopy, prod d_i (host call); for a
+ * batch handle, n_systems * prod d_i. */
 int phc_num_paths(const phc_homotopy *h, int64_t *out);
 
 /* Track paths first_path .. first_path + n_paths - 1 of the total-degree

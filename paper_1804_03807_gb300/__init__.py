@@ -14,13 +14,15 @@ import numpy as np
 from ._lib import (PHC_AT_INFINITY, PHC_FAILED, PHC_MAX_VARS, PHC_PREC_FP32_INTERIOR, PHC_PREC_FP64,
                    PHC_REGULAR, PHC_SINGULAR, PHC_STOP_REACHED, STATS_DTYPE, Homotopy, PhcError, SystemLists,
                    load, phc_cascade_stage, phc_default_opts, phc_embed, phc_last_error, phc_make_homotopy,
+                   phc_make_homotopy_batch,
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
                    phc_track_paths_noalloc)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
     "PHC_SINGULAR", "PHC_STOP_REACHED", "STATS_DTYPE", "Homotopy", "PhcError", "SystemLists", "load",
-    "phc_cascade_stage", "phc_default_opts", "phc_embed", "phc_last_error", "phc_make_homotopy", "phc_num_paths",
+    "phc_cascade_stage", "phc_default_opts", "phc_embed", "phc_last_error", "phc_make_homotopy",
+    "phc_make_homotopy_batch", "phc_num_paths",
     "phc_opts", "phc_refine_endpoints", "phc_track_paths", "phc_track_paths_noalloc", "Tracked", "track", "cascade", "refine",
     "stats_numpy",
 ]

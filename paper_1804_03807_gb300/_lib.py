@@ -25,7 +25,7 @@ PHC_NOALLOC_MAX_PATHS = 52428
 EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
-    "phc_sizeof_stats", "phc_track_paths_noalloc",
+    "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch",
 ]
 
 
@@ -57,7 +57,7 @@ class phc_opts(ctypes.Structure):
 STATS_DTYPE = np.dtype([
     ("t", "f8"), ("h", "f8"), ("cond", "f8"), ("relres", "f8"), ("norm_x", "f8"), ("growth", "f8"),
     ("n_accept", "i4"), ("n_reject", "i4"), ("n_newton", "i4"), ("n_solve", "i4"), ("stop", "i4"),
-    ("n_fp32", "i4"), ("grew", "i4"), ("reserved", "i4"),
+    ("n_fp32", "i4"), ("grew", "i4"), ("system", "i4"),
 ])
 
 
@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
     vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     L.phc_default_opts.argtypes = [ctypes.POINTER(phc_opts)]
     L.phc_make_homotopy.argtypes = [i32, i32, vp, vp, vp, phc_cd, ctypes.POINTER(vp)]
+    L.phc_make_homotopy_batch.argtypes = [i32, i32, vp, vp, i32, vp, vp, ctypes.POINTER(vp)]
     L.phc_num_paths.argtypes = [vp, ctypes.POINTER(i64)]
     L.phc_track_paths.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_track_paths_noalloc.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
@@ -95,7 +96,8 @@ def load() -> ctypes.CDLL:
     L.phc_destroy_homotopy.restype = None
     L.phc_free_lists.argtypes = [ctypes.POINTER(phc_system_lists)]
     L.phc_free_lists.restype = None
-    for name in ("phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths",
+    for name in ("phc_default_opts", "phc_make_homotopy", "phc_make_homotopy_batch", "phc_num_paths",
+                 "phc_track_paths",
                  "phc_track_paths_noalloc", "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats"):
         getattr(L, name).restype = ctypes.c_int
@@ -160,6 +162,22 @@ def phc_make_homotopy(sys, gamma: complex) -> Homotopy:
     _check(L.phc_make_homotopy(int(sys.n_eq), int(sys.n_var), tpe.ctypes.data, exps.ctypes.data, coefs.ctypes.data,
                                phc_cd(float(np.real(gamma)), float(np.imag(gamma))), ctypes.byref(out)))
     return Homotopy(out.value, int(sys.n_var))
+
+
+def phc_make_homotopy_batch(systems, gammas) -> Homotopy:
+    """One handle for systems that share supports (terms_per_eq, exps) and
+    differ in coefficients and gamma; path p of system s is s * P + p."""
+    L = load()
+    tpe, exps, _ = _lists(systems[0])
+    for s in systems[1:]:
+        if not (np.array_equal(np.asarray(s.terms_per_eq), tpe) and np.array_equal(np.asarray(s.exps), exps)):
+            raise ValueError("systems of a batch must share terms_per_eq and exps")
+    coefs = np.ascontiguousarray(np.stack([np.asarray(s.coefs, dtype=np.complex128) for s in systems]))
+    gam = np.ascontiguousarray(np.asarray(gammas, dtype=np.complex128))
+    out = ctypes.c_void_p()
+    _check(L.phc_make_homotopy_batch(int(systems[0].n_eq), int(systems[0].n_var), tpe.ctypes.data, exps.ctypes.data,
+                                     len(systems), coefs.ctypes.data, gam.ctypes.data, ctypes.byref(out)))
+    return Homotopy(out.value, int(systems[0].n_var))
 
 
 def phc_num_paths(h: Homotopy) -> int:

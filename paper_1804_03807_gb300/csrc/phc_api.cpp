@@ -95,12 +95,14 @@ struct DeviceTable {
 
 struct phc_homotopy {
     int n = 0;
-    // host copy of the system lists
+    int n_sys = 1;              // systems sharing the supports (batch handle)
+    // host copy of the system lists (coefficients of system 0 for a batch)
     std::vector<int32_t> tpe;
     std::vector<uint8_t> exps;
     std::vector<phc_cd> coefs;
     phc_cd gamma{1.0, 0.0};
     std::vector<int32_t> deg;
+    int64_t paths_per_system = 0;
     int64_t num_paths = 0;
     // device
     int device = 0;
@@ -146,27 +148,35 @@ struct HostTerms {
         c0.push_back(c0v);
         c1.push_back(c1v);
     }
+    // coefficients of one more system of a batch (same structure)
+    void add_coef(double2 c0v, double2 c1v)
+    {
+        c0.push_back(c0v);
+        c1.push_back(c1v);
+    }
 };
 
 static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
 {
     const size_t T = ht.recs.size(), V = ht.vars.size();
+    const size_t C = ht.c0.size();  // T per system
+    const int n_sys = (int)(C / T);
     if (V > 65535) return fail(PHC_EUNSUPPORTED, "system too large (%zu exponent entries)", V);
     const size_t o_terms = 0;
     const size_t o_vars = o_terms + T * sizeof(TermRec);
     const size_t o_exps = o_vars + V;
     size_t o_c0 = o_exps + V;
     o_c0 = (o_c0 + 15) & ~(size_t)15;
-    const size_t o_c1 = o_c0 + T * sizeof(double2);
-    const size_t bytes = o_c1 + T * sizeof(double2);
+    const size_t o_c1 = o_c0 + C * sizeof(double2);
+    const size_t bytes = o_c1 + C * sizeof(double2);
     std::vector<char> host(bytes, 0);
     std::memcpy(host.data() + o_terms, ht.recs.data(), T * sizeof(TermRec));
     if (V) {
         std::memcpy(host.data() + o_vars, ht.vars.data(), V);
         std::memcpy(host.data() + o_exps, ht.exps.data(), V);
     }
-    std::memcpy(host.data() + o_c0, ht.c0.data(), T * sizeof(double2));
-    std::memcpy(host.data() + o_c1, ht.c1.data(), T * sizeof(double2));
+    std::memcpy(host.data() + o_c0, ht.c0.data(), C * sizeof(double2));
+    std::memcpy(host.data() + o_c1, ht.c1.data(), C * sizeof(double2));
     void *blob = nullptr;
     if (cudaMalloc(&blob, bytes) != cudaSuccess) return fail(PHC_ENOMEM, "cudaMalloc of %zu table bytes", bytes);
     if (cudaMemcpy(blob, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -178,6 +188,7 @@ static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
     out.view.n = n;
     out.view.n_terms = (int)T;
     out.view.n_ve = (int)V;
+    out.view.n_sys = n_sys;
     out.view.terms = reinterpret_cast<const TermRec *>(b + o_terms);
     out.view.vars = reinterpret_cast<const uint8_t *>(b + o_vars);
     out.view.exps = reinterpret_cast<const uint8_t *>(b + o_exps);
@@ -212,49 +223,74 @@ static int validate_lists(int n_eq, int n_var, const int32_t *tpe, const uint8_t
     return PHC_OK;
 }
 
-extern "C" int phc_make_homotopy(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
-                                 phc_cd gamma, phc_homotopy **out)
+extern "C" int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, int n_sys,
+                                       const phc_cd *coefs, const phc_cd *gammas, phc_homotopy **out)
 {
     if (!out) return fail(PHC_EINVAL, "out is NULL");
     *out = nullptr;
+    if (n_sys < 1) return fail(PHC_EINVAL, "n_systems = %d < 1", n_sys);
+    if (!gammas) return fail(PHC_EINVAL, "gammas is NULL");
     std::vector<int32_t> deg;
     int rc = validate_lists(n_eq, n_var, tpe, exps, coefs, true, &deg);
     if (rc) return rc;
-    if (!std::isfinite(gamma.re) || !std::isfinite(gamma.im) || (gamma.re == 0.0 && gamma.im == 0.0))
-        return fail(PHC_EINVAL, "gamma must be finite and nonzero");
     const int n = n_var;
     int64_t T = 0;
     for (int i = 0; i < n_eq; i++) T += tpe[i];
+    for (int s = 0; s < n_sys; s++) {
+        const phc_cd g = gammas[s];
+        if (!std::isfinite(g.re) || !std::isfinite(g.im) || (g.re == 0.0 && g.im == 0.0))
+            return fail(PHC_EINVAL, "gamma of system %d must be finite and nonzero", s);
+        for (int64_t k = 0; k < T; k++) {
+            const phc_cd c = coefs[s * T + k];
+            if (!std::isfinite(c.re) || !std::isfinite(c.im))
+                return fail(PHC_EINVAL, "coefficient %lld of system %d is not finite", (long long)k, s);
+        }
+    }
 
     phc_homotopy *h = new (std::nothrow) phc_homotopy();
     if (!h) return fail(PHC_ENOMEM, "host allocation");
     h->n = n;
+    h->n_sys = n_sys;
     h->tpe.assign(tpe, tpe + n_eq);
     h->exps.assign(exps, exps + T * n);
     h->coefs.assign(coefs, coefs + T);
-    h->gamma = gamma;
+    h->gamma = gammas[0];
     h->deg = deg;
-    h->num_paths = 1;
+    h->paths_per_system = 1;
     for (int i = 0; i < n; i++) {
-        if (h->num_paths > (int64_t)1 << 50) {
+        if (h->paths_per_system > (int64_t)1 << 40) {
             delete h;
             return fail(PHC_EUNSUPPORTED, "Bezout number too large");
         }
-        h->num_paths *= deg[i];
+        h->paths_per_system *= deg[i];
     }
+    h->num_paths = h->paths_per_system * n_sys;
     cudaGetDevice(&h->device);
 
     // total-degree homotopy: f terms (0, c); x_i^{d_i}: (gamma, -gamma); -1: (-gamma, gamma)
     HostTerms ht;
-    int64_t off = 0;
-    for (int i = 0; i < n; i++) {
-        for (int k = 0; k < tpe[i]; k++, off++)
-            ht.add(i, exps + off * n, n, make_double2(0.0, 0.0), make_double2(coefs[off].re, coefs[off].im));
-        std::vector<uint8_t> a(n, 0);
-        a[i] = (uint8_t)deg[i];
-        ht.add(i, a.data(), n, make_double2(gamma.re, gamma.im), make_double2(-gamma.re, -gamma.im));
-        std::vector<uint8_t> z(n, 0);
-        ht.add(i, z.data(), n, make_double2(-gamma.re, -gamma.im), make_double2(gamma.re, gamma.im));
+    for (int s = 0; s < n_sys; s++) {
+        const phc_cd gamma = gammas[s];
+        const phc_cd *cs = coefs + s * T;
+        int64_t off = 0;
+        for (int i = 0; i < n; i++) {
+            for (int k = 0; k < tpe[i]; k++, off++) {
+                const double2 c0 = make_double2(0.0, 0.0), c1 = make_double2(cs[off].re, cs[off].im);
+                if (s == 0) ht.add(i, exps + off * n, n, c0, c1);
+                else ht.add_coef(c0, c1);
+            }
+            const double2 g0 = make_double2(gamma.re, gamma.im), g1 = make_double2(-gamma.re, -gamma.im);
+            if (s == 0) {
+                std::vector<uint8_t> a(n, 0);
+                a[i] = (uint8_t)deg[i];
+                ht.add(i, a.data(), n, g0, g1);
+                std::vector<uint8_t> z(n, 0);
+                ht.add(i, z.data(), n, g1, g0);
+            } else {
+                ht.add_coef(g0, g1);
+                ht.add_coef(g1, g0);
+            }
+        }
     }
     rc = upload_table(ht, n, h->total);
     if (rc) {
@@ -285,6 +321,12 @@ extern "C" int phc_make_homotopy(int n_eq, int n_var, const int32_t *tpe, const 
     }
     *out = h;
     return PHC_OK;
+}
+
+extern "C" int phc_make_homotopy(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                                 phc_cd gamma, phc_homotopy **out)
+{
+    return phc_make_homotopy_batch(n_eq, n_var, tpe, exps, 1, coefs, &gamma, out);
 }
 
 extern "C" void phc_destroy_homotopy(phc_homotopy *h)
@@ -353,6 +395,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.starts = starts;
     L.first = first;
     L.n_paths = n;
+    L.paths_per_system = h->paths_per_system > 0 ? h->paths_per_system : 1;
     L.x_out = x_out;
     L.stats = stats;
     L.qhead = h->d_qhead;
@@ -426,6 +469,7 @@ extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *st
     phc_homotopy *h = const_cast<phc_homotopy *>(hc);
     if (!h) return fail(PHC_EINVAL, "NULL handle");
     if (k < 1 || k >= h->n) return fail(PHC_EINVAL, "cascade stage k = %d outside 1..%d", k, h->n - 1);
+    if (h->n_sys != 1) return fail(PHC_EUNSUPPORTED, "cascade stages need a single-system handle");
     if (n < 0) return fail(PHC_EINVAL, "n_starts < 0");
     if (n == 0) return PHC_OK;
     if (!starts || !x_out || !cls_out || !slack_zero_out) return fail(PHC_EINVAL, "NULL array");
@@ -592,6 +636,7 @@ int handle_track_view(phc_homotopy *h, TrackLaunch *L)
     L->deg = h->d_deg;
     L->root_off = h->d_root_off;
     L->roots = h->d_roots;
+    L->paths_per_system = h->paths_per_system;
     return PHC_OK;
 }
 

@@ -28,10 +28,13 @@ enum : uint8_t { TERM_POWERS = 1 };
 
 // Device tables of one homotopy (global memory; staged into shared memory
 // by the kernels).
+// A batch of n_sys homotopies shares terms/vars/exps; system s has the
+// coefficients c0[s * n_terms + q], c1[s * n_terms + q].
 struct DevTables {
     int n;        // unknowns = equations
     int n_terms;  // terms
     int n_ve;     // entries of vars / exps
+    int n_sys;    // systems sharing the structure
     const TermRec *terms;
     const uint8_t *vars;
     const uint8_t *exps;
@@ -39,12 +42,22 @@ struct DevTables {
     const double2 *c1;
 };
 
-// Bytes the staged copy of a table takes in shared memory (16-byte aligned).
-inline size_t table_smem_bytes(int n_terms, int n_ve)
+// Coefficients of all systems are staged into shared memory up to this size;
+// larger batches read them through L1.
+constexpr size_t COEF_SMEM_LIMIT = 48 * 1024;
+
+__host__ __device__ inline bool coefs_in_smem(const DevTables &t)
 {
-    size_t b = (size_t)n_terms * sizeof(TermRec) + 2 * (size_t)n_ve;
+    return 2 * (size_t)t.n_terms * (size_t)t.n_sys * 16 <= COEF_SMEM_LIMIT;
+}
+
+// Bytes the staged copy of a table takes in shared memory (16-byte aligned).
+__host__ __device__ inline size_t table_smem_bytes(const DevTables &t)
+{
+    size_t b = (size_t)t.n_terms * sizeof(TermRec) + 2 * (size_t)t.n_ve;
     b = (b + 15) & ~(size_t)15;
-    return b + 2 * (size_t)n_terms * sizeof(double2);
+    if (coefs_in_smem(t)) b += 2 * (size_t)t.n_terms * (size_t)t.n_sys * 16;
+    return b;
 }
 
 // Per-thread shared memory of the tracker: xe, H, Ht, P (N each) and J (N*N),
@@ -61,6 +74,7 @@ struct TrackLaunch {
     const double2 *starts;    // SoA [n][n_paths] (mode 1)
     int64_t first;
     int64_t n_paths;
+    int64_t paths_per_system; // global path p belongs to system p / paths_per_system
     double2 *x_out;           // SoA [n][n_paths]
     phc_path_stats *stats;    // [n_paths]
     unsigned long long *qhead;

@@ -85,14 +85,15 @@ __device__ __forceinline__ double cdd_absinf(cdd a)
 
 // Table reads go through the read-only path (few endpoints are refined).
 template <int N>
-__device__ void eval_dd(const DevTables &tab, const cdd *x, cdd *H, cdd *J)
+__device__ void eval_dd(const DevTables &tab, int sys, const cdd *x, cdd *H, cdd *J)
 {
+    const size_t cof = (size_t)sys * tab.n_terms;
     const cdd zero = {{0.0, 0.0}, {0.0, 0.0}};
     for (int i = 0; i < N; i++) H[i] = zero;
     for (int i = 0; i < N * N; i++) J[i] = zero;
     for (int q = 0; q < tab.n_terms; q++) {
         const TermRec r = tab.terms[q];
-        const double2 c0 = __ldg(&tab.c0[q]), c1 = __ldg(&tab.c1[q]);
+        const double2 c0 = __ldg(&tab.c0[cof + q]), c1 = __ldg(&tab.c1[cof + q]);
         // coefficient at t = 1 (exact: the pairs are (0,c), (g,-g), (c,0), (c,-c))
         const double2 c = make_double2(c0.x + c1.x, c0.y + c1.y);
         if (c.x == 0.0 && c.y == 0.0) continue;
@@ -159,8 +160,9 @@ __device__ bool solve_dd(cdd *J, cdd *b)
 // classification: max_j sum_i |(J^-1)_ji|_1 (1 + scale_i) / (1 + ||x||)),
 // computed here in double double for simplicity.
 template <int N>
-__device__ double cond_at(const DevTables &tab, const double2 *x2)
+__device__ double cond_at(const DevTables &tab, int sys, const double2 *x2)
 {
+    const size_t cof = (size_t)sys * tab.n_terms;
     cdd x[N], H[N], J[N * N], col[N];
     double scale[N];
     for (int j = 0; j < N; j++) x[j] = cdd_from(x2[j]);
@@ -168,7 +170,7 @@ __device__ double cond_at(const DevTables &tab, const double2 *x2)
     // scale_i from a plain double evaluation of the monomials
     for (int q = 0; q < tab.n_terms; q++) {
         const TermRec r = tab.terms[q];
-        const double2 c0 = __ldg(&tab.c0[q]), c1 = __ldg(&tab.c1[q]);
+        const double2 c0 = __ldg(&tab.c0[cof + q]), c1 = __ldg(&tab.c1[cof + q]);
         const double2 c = make_double2(c0.x + c1.x, c0.y + c1.y);
         double2 mono = make_double2(1.0, 0.0);
         for (int j = 0; j < r.k; j++) {
@@ -178,9 +180,8 @@ __device__ double cond_at(const DevTables &tab, const double2 *x2)
         }
         scale[r.eq] += (fabs(c.x) + fabs(c.y)) * (fabs(mono.x) + fabs(mono.y));
     }
-    eval_dd<N>(tab, x, H, J);
-    // LU once, then one solve per unit vector (copy of the factors each time
-    // keeps solve_dd simple: N is at most 12)
+    eval_dd<N>(tab, sys, x, H, J);
+    // one full solve per unit vector (N <= 12; only refined endpoints get here)
     double rowacc[N];
     for (int j = 0; j < N; j++) rowacc[j] = 0.0;
     cdd Jc[N * N];
@@ -215,7 +216,7 @@ __global__ void refine_kernel(const RefineLaunch L)
         for (int j = 0; j < N; j++) x[j] = cdd_from(L.x_hi[(int64_t)j * n + q]);
         bool conv = false;
         for (int it = 0; it < L.max_iters; it++) {
-            eval_dd<N>(L.tab, x, H, J);
+            eval_dd<N>(L.tab, s.system, x, H, J);
             if (!solve_dd<N>(J, H)) break;
             double dn = 0.0, xn = 0.0;
             for (int j = 0; j < N; j++) {
@@ -237,7 +238,7 @@ __global__ void refine_kernel(const RefineLaunch L)
             L.x_hi[(int64_t)j * n + q] = xh[j];
             L.x_lo[(int64_t)j * n + q] = make_double2(x[j].re.lo, x[j].im.lo);
         }
-        const double c = cond_at<N>(L.tab, xh);
+        const double c = cond_at<N>(L.tab, s.system, xh);
         s.cond = c;
         L.stats[q] = s;
         L.cls[q] = (conv && c <= L.cond_max) ? PHC_REGULAR : PHC_SINGULAR;

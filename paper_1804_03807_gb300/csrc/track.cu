@@ -61,7 +61,7 @@ struct SmTab {
     const TermRec *terms;
     const uint8_t *vars;
     const uint8_t *exps;
-    const double2 *c0;
+    const double2 *c0;  // system 0; system s at + s * n_terms (shared or global memory)
     const double2 *c1;
 };
 
@@ -73,24 +73,30 @@ __device__ SmTab stage_table(const DevTables &g, char *smem)
     uint8_t *exps = vars + g.n_ve;
     size_t b = (size_t)g.n_terms * sizeof(TermRec) + 2 * (size_t)g.n_ve;
     b = (b + 15) & ~(size_t)15;
-    double2 *c0 = reinterpret_cast<double2 *>(smem + b);
-    double2 *c1 = c0 + g.n_terms;
-    for (int i = threadIdx.x; i < g.n_terms; i += blockDim.x) {
-        terms[i] = g.terms[i];
-        c0[i] = g.c0[i];
-        c1[i] = g.c1[i];
-    }
+    for (int i = threadIdx.x; i < g.n_terms; i += blockDim.x) terms[i] = g.terms[i];
     for (int i = threadIdx.x; i < g.n_ve; i += blockDim.x) {
         vars[i] = g.vars[i];
         exps[i] = g.exps[i];
+    }
+    if (coefs_in_smem(g)) {
+        const int nc = g.n_terms * g.n_sys;
+        double2 *c0 = reinterpret_cast<double2 *>(smem + b);
+        double2 *c1 = c0 + nc;
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            c0[i] = g.c0[i];
+            c1[i] = g.c1[i];
+        }
+        s.c0 = c0;
+        s.c1 = c1;
+    } else {
+        s.c0 = g.c0;
+        s.c1 = g.c1;
     }
     __syncthreads();
     s.n_terms = g.n_terms;
     s.terms = terms;
     s.vars = vars;
     s.exps = exps;
-    s.c0 = c0;
-    s.c1 = c1;
     return s;
 }
 
@@ -105,9 +111,11 @@ __device__ SmTab stage_table(const DevTables &g, char *smem)
 // With SCALE, S[i].x accumulates sum over the terms of equation i of
 // |c(t)|_1 |x^a|_1 (for the relative residual and the condition number).
 template <int N, bool SCALE>
-__device__ __forceinline__ void evaluate(const SmTab &tb, double t, const double2 *xe, double2 *H, double2 *Ht,
-                                         double2 *J, double2 *P, double2 *S, int bt)
+__device__ __forceinline__ void evaluate(const SmTab &tb, int sys, double t, const double2 *xe, double2 *H,
+                                         double2 *Ht, double2 *J, double2 *P, double2 *S, int bt)
 {
+    const double2 *C0 = tb.c0 + (size_t)sys * tb.n_terms;
+    const double2 *C1 = tb.c1 + (size_t)sys * tb.n_terms;
     const double2 zero = make_double2(0.0, 0.0);
 #pragma unroll
     for (int i = 0; i < N; i++) {
@@ -120,7 +128,7 @@ __device__ __forceinline__ void evaluate(const SmTab &tb, double t, const double
 
     for (int q = 0; q < tb.n_terms; q++) {
         const TermRec r = tb.terms[q];
-        const double2 c0 = tb.c0[q], c1 = tb.c1[q];
+        const double2 c0 = C0[q], c1 = C1[q];
         const double2 ct = make_double2(fma(t, c1.x, c0.x), fma(t, c1.y, c0.y));
         const int k = r.k;
         if (k == 0) {
@@ -279,6 +287,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
     double2 x0[N], acc[N];
     int perm[N];
     int64_t q = -1;
+    int sys = 0;
     double t = 0.0, h = 0.0, he = 0.0, t1 = 0.0, te = 0.0, prev = 0.0, next_s = 0.0;
     double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0;  // last five decade checkpoints, r4 newest
     int streak = 0, steps = 0, phase = 0, it = 0, nck = 0;
@@ -327,7 +336,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
         s.stop = stop;
         s.n_fp32 = 0;
         s.grew = grew;
-        s.reserved = 0;
+        s.system = sys;
         L.stats[q] = s;
         q = -1;
     };
@@ -397,7 +406,9 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             if (c >= (unsigned long long)np) break;
             q = (int64_t)c;
             if (L.start_mode == 0) {
-                int64_t pid = L.first + q;
+                const int64_t gid = L.first + q;
+                sys = (int)(gid / L.paths_per_system);
+                int64_t pid = gid - (int64_t)sys * L.paths_per_system;
 #pragma unroll
                 for (int i = 0; i < N; i++) {
                     const int d = L.deg[i];
@@ -420,7 +431,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
         }
 
         // one unit: evaluate, factor, solve
-        evaluate<N, false>(tb, te, A.xe, A.H, A.Ht, A.J, A.P, A.S, bt);
+        evaluate<N, false>(tb, sys, te, A.xe, A.H, A.Ht, A.J, A.P, A.S, bt);
         double2 *b = (phase < 4) ? A.Ht : A.H;
         const bool ok = lu_factor<N>(A.J, perm, bt);
         if (ok) lu_solve<N>(A.J, perm, b, bt);
@@ -547,8 +558,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const ClassifyLaunch L, s
     const int64_t np = L.n_paths;
     int perm[N];
 
-    for (int64_t q = (int64_t)blockIdx.x * bt + threadIdx.x; q - threadIdx.x < np; q += (int64_t)gridDim.x * bt) {
-        const bool active = q < np;
+    for (int64_t q = (int64_t)blockIdx.x * bt + threadIdx.x; q < np; q += (int64_t)gridDim.x * bt) {
+        const bool active = true;
         phc_path_stats s;
         bool fin = true;
         double nx = 0.0;
@@ -563,13 +574,11 @@ __global__ void __launch_bounds__(256) classify_kernel(const ClassifyLaunch L, s
                 if (!(a <= nx)) nx = a;
             }
         }
-        // every thread of the block evaluates (inactive ones on stale data) so
-        // the loop stays uniform
         int8_t cls = PHC_FAILED;
         double cond = NAN, relres = NAN;
         const bool measure = active && fin && s.stop != PHC_STOP_DIVERGED;
         if (measure) {
-            evaluate<N, true>(tb, 1.0, A.xe, A.H, A.Ht, A.J, A.P, A.S, bt);
+            evaluate<N, true>(tb, s.system, 1.0, A.xe, A.H, A.Ht, A.J, A.P, A.S, bt);
             double rr = 0.0;
 #pragma unroll
             for (int i = 0; i < N; i++) {
@@ -685,7 +694,7 @@ int track_block_threads(int n, size_t table_bytes, int requested)
 template <int N>
 static cudaError_t launch_track_n(const TrackLaunch &L, int bt, int max_blocks, cudaStream_t s)
 {
-    const size_t tb = table_smem_bytes(L.tab.n_terms, L.tab.n_ve);
+    const size_t tb = table_smem_bytes(L.tab);
     const size_t smem = tb + (size_t)bt * thread_smem_bytes(N);
     cudaError_t e = cudaFuncSetAttribute(track_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -705,7 +714,7 @@ static cudaError_t launch_track_n(const TrackLaunch &L, int bt, int max_blocks, 
 template <int N>
 static cudaError_t launch_classify_n(const ClassifyLaunch &L, cudaStream_t s)
 {
-    const size_t tb = table_smem_bytes(L.tab.n_terms, L.tab.n_ve);
+    const size_t tb = table_smem_bytes(L.tab);
     const int bt = track_block_threads(N, tb, 128);
     if (bt == 0) return cudaErrorInvalidConfiguration;
     const size_t smem = tb + (size_t)bt * thread_smem_bytes(N);
@@ -739,7 +748,7 @@ cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks
 {
     device_limits();
     if (L.n_paths <= 0) return cudaSuccess;
-    const size_t tb = table_smem_bytes(L.tab.n_terms, L.tab.n_ve);
+    const size_t tb = table_smem_bytes(L.tab);
     const int bt = track_block_threads(L.tab.n, tb, block_threads);
     if (bt == 0) return cudaErrorInvalidConfiguration;
 #define PHC_CALL_TRACK(NN) launch_track_n<NN>(L, bt, max_blocks, s)

@@ -107,6 +107,49 @@ def test_cyclic7_batch_full_size():
         compare(s, xg, cg, xo, co, s.name)
 
 
+def test_batch_handle_one_launch_matches_oracle_and_single_handles():
+    """cyclic 5 and three random-coefficient copies in one batch handle (one
+    launch): per system the same classes and endpoints as the oracle, and
+    path for path the same results as separate handles."""
+    w = configs.cyclic_batch(5, 3, seed=801)
+    hb = P.phc_make_homotopy_batch(w.systems, w.gammas)
+    Pn = w.systems[0].bezout()
+    assert P.phc_num_paths(hb) == 4 * Pn
+    r = P.track(hb)
+    x = r.x.cpu().numpy().T
+    c = r.cls.cpu().numpy()
+    st = P.stats_numpy(r.stats)
+    for s_i, (s, g) in enumerate(zip(w.systems, w.gammas)):
+        sl = slice(s_i * Pn, (s_i + 1) * Pn)
+        assert np.all(st["system"][sl] == s_i)
+        xo, co, _ = oracle.track(oracle.total_degree(s, g))
+        compare(s, x[sl], c[sl], xo, co, f"batch system {s_i}")
+        _, _, x1, c1, _ = gpu_track(s, g)
+        assert np.array_equal(c1, c[sl])
+        assert np.array_equal(x1, x[sl])
+    # a sub-range across a system boundary
+    r2 = P.track(hb, first=Pn - 7, n_paths=20)
+    assert np.array_equal(r2.x.cpu().numpy().T, x[Pn - 7:Pn + 13])
+
+
+def test_cyclic7_batch_one_launch_full_size():
+    """The bench workload: 45,360 paths in one launch, each system's classes
+    and regular set equal to the oracle's."""
+    w = configs.cyclic7_batch()
+    hb = P.phc_make_homotopy_batch(w.systems, w.gammas)
+    r = P.track(hb)
+    P.refine(hb, r)
+    x = r.x.cpu().numpy().T
+    c = r.cls.cpu().numpy()
+    Pn = 5040
+    for s_i, (s, g) in enumerate(zip(w.systems, w.gammas)):
+        sl = slice(s_i * Pn, (s_i + 1) * Pn)
+        ho = oracle.total_degree(s, g)
+        xo, co, so = oracle.track(ho)
+        xo, _, co, _ = oracle.refine(ho, xo, co, so["cond"], so["stop"] == 0)
+        compare(s, x[sl], c[sl], xo, co, s.name)
+
+
 def test_cyclic8_embedded_sampled_paths():
     """Embedded cyclic 8 (40,320 paths) on the GPU; a seeded sample of 1500
     paths re-tracked by the oracle and compared path by path."""
