@@ -56,10 +56,14 @@ enum { PHC_REGULAR = 0, PHC_SINGULAR = 1, PHC_AT_INFINITY = 2, PHC_FAILED = 3 };
 enum { PHC_STOP_REACHED = 0, PHC_STOP_DIVERGED = 1, PHC_STOP_STEP_MIN = 2, PHC_STOP_BUDGET = 3,
        PHC_STOP_NONFINITE = 4 };
 
-/* Arithmetic of the tracker.  FP32_INTERIOR evaluates the Jacobian and
- * factors it in single precision while t < fp32_t_max (the residual of every
- * Newton correction stays double); a rejected single precision step is
- * retried in double. */
+/* Arithmetic of the tracker.  FP32_INTERIOR runs the predictor stages
+ * (H_t, Jacobian, factorization, solve) in single precision and factors the
+ * Jacobian of every Newton correction in single precision while the step
+ * ends at t <= fp32_t_max; the residual of every Newton correction stays
+ * double, and so does everything after t = fp32_t_max (the end game).  A
+ * single precision factorization whose pivots spread by more than
+ * fp32_pivot_ratio counts as failed; a failed single precision step is retried in double and the
+ * rest of that path stays in double. */
 enum { PHC_PREC_FP64 = 0, PHC_PREC_FP32_INTERIOR = 1 };
 
 #define PHC_MAX_VARS 12    /* largest number of unknowns of a tracked system */
@@ -77,7 +81,7 @@ enum { PHC_PREC_FP64 = 0, PHC_PREC_FP32_INTERIOR = 1 };
  *               t = 1 (stop at ||dx|| <= end_tol (1 + ||x||))
  *   classes     norms are max_j max(|Re x_j|, |Im x_j|).
  *               AT_INFINITY: ||x|| > diverge_norm after an accepted step; or
- *                 stalled with ||x|| > stall_inf_norm; or stalled at
+ *                 an endpoint with ||x|| > endpoint_inf_norm; or stalled at
  *                 t >= end_zone with ||x|| grown by more than growth_inf per
  *                 decade of 1-t over its last (<= 4) decade checkpoints.
  *               FAILED: non-finite values, or stalled before end_zone.
@@ -98,12 +102,13 @@ typedef struct {
     int32_t max_corr_iters;
     double corr_tol, corr_contract;
     int32_t max_steps;
-    double diverge_norm, stall_inf_norm, end_zone, growth_inf;
+    double diverge_norm, endpoint_inf_norm, end_zone, growth_inf;
     int32_t end_iters;
     double end_tol;
     double cond_regular, res_regular, slack_tol;
     int32_t precision;       /* PHC_PREC_*                                  */
     double fp32_t_max;       /* FP32_INTERIOR: single precision for t < this */
+    double fp32_pivot_ratio; /* FP32_INTERIOR: largest pivot spread accepted */
     int32_t block_threads;   /* threads per block; 0 = chosen by the library */
     int32_t max_blocks;      /* grid size cap; 0 = one wave of resident blocks */
 } phc_opts;
@@ -206,6 +211,26 @@ int phc_embed(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *e
 int phc_cascade_stage(const phc_homotopy *embedded_k, int k, const phc_cd *starts, int64_t n_starts,
                       const phc_opts *opts, phc_cd *x_out, int8_t *cls_out, uint8_t *slack_zero_out,
                       phc_path_stats *stats_out, void *cuda_stream);
+
+/* The top stage and the cascade stage below it in one launch (Section 3.1,
+ * Figure 3; the GPU counterpart of the paper's pipelining, Section 2.2).
+ * Tracks paths first_path .. first_path + n_paths - 1 of the total-degree
+ * homotopy of E_k (embedded_k as for phc_cascade_stage), classifies every
+ * endpoint as its path ends and, when it is regular with z_k != 0
+ * (|z_k| > slack_tol (1 + ||x||)), continues the same GPU thread on the
+ * cascade homotopy E_k -> E_{k-1} from it, so stage k-1 starts while stage
+ * k is still running and no host round trip separates them.
+ * Outputs (device, caller-owned): the top stage as phc_track_paths (x_top
+ * SoA [n_var][n_paths], cls_top [n_paths], stats_top or NULL) and, per top
+ * path, the stage below: x_next SoA [n_var - 1][n_paths], cls_next (-1 where
+ * the top endpoint was not continued), slack_zero_next (as
+ * phc_cascade_stage), stats_next or NULL.  Top endpoints that only double
+ * double refinement makes regular are not continued: refine the top stage
+ * afterwards and pass those to phc_cascade_stage.
+ * Errors: as phc_track_paths and phc_cascade_stage. */
+int phc_track_pipeline(phc_homotopy *embedded_k, int k, int64_t first_path, int64_t n_paths, const phc_opts *opts,
+                       phc_cd *x_top, int8_t *cls_top, phc_path_stats *stats_top, phc_cd *x_next, int8_t *cls_next,
+                       uint8_t *slack_zero_next, phc_path_stats *stats_next, void *cuda_stream);
 
 /* Refine endpoints of h (evaluated at t = 1) by Newton's method in complex
  * double double arithmetic (the paper's double double path, Section 5,

@@ -60,7 +60,7 @@ typedef struct {
     double corr_contract;   /* rejected: ||dx_j|| > corr_contract ||dx_j-1|| */
     int32_t max_steps;      /* accepted + rejected steps per path           */
     double diverge_norm;    /* ||x|| above this during tracking: at infinity */
-    double stall_inf_norm;  /* stalled with ||x|| above this: at infinity    */
+    double endpoint_inf_norm; /* endpoint with ||x|| above this: at infinity  */
     double end_zone;        /* stalled before this t: failed                 */
     double growth_inf;      /* stalled and ||x|| grew by more than growth_inf
                                per decade of 1-t: at infinity (a ratio)       */
@@ -84,7 +84,7 @@ void orc_default_opts(orc_opts *o)
     o->corr_contract = 0.5;
     o->max_steps = 20000;
     o->diverge_norm = 1e6;
-    o->stall_inf_norm = 1e4;
+    o->endpoint_inf_norm = 1e4;
     o->end_zone = 0.9;
     o->growth_inf = 1.1220184543019633; /* 10^0.05 */
     o->end_iters = 8;
@@ -401,7 +401,8 @@ static void end_measures(const orc_homotopy *h, const cplx *x, double *cond, dou
  * End (only for paths that reached t = 1): Newton at t = 1 (<= end_iters),
  *   then the condition number and the relative residual; REGULAR when both
  *   are small.
- * A stalled path is never REGULAR: it is AT_INFINITY when ||x|| > stall_inf_norm
+ * Every endpoint with ||x|| > endpoint_inf_norm is AT_INFINITY.
+ * A stalled path is never REGULAR: it is AT_INFINITY when ||x|| > endpoint_inf_norm
  *   or when ||x|| grew by more than growth_inf per decade of 1-t over its last
  *   (at most four) decade checkpoints, FAILED when it stalled before end_zone,
  *   SINGULAR otherwise. */
@@ -495,7 +496,7 @@ static void track_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_sta
     if (st->stop != 0) {
         /* stalled before t = 1: never regular */
         end_measures(h, x, &st->cond, &st->relres);
-        if (st->norm_x > o->stall_inf_norm || (t >= o->end_zone && grew)) st->cls = ORC_AT_INFINITY;
+        if (st->norm_x > o->endpoint_inf_norm || (t >= o->end_zone && grew)) st->cls = ORC_AT_INFINITY;
         else if (t < o->end_zone) st->cls = ORC_FAILED;
         else st->cls = ORC_SINGULAR;
         return;
@@ -509,7 +510,7 @@ static void track_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_sta
     if (!all_finite(n, x)) { st->stop = 4; st->cls = ORC_FAILED; st->norm_x = NAN; st->cond = NAN; st->relres = NAN; return; }
     st->norm_x = vnorm(n, x);
     end_measures(h, x, &st->cond, &st->relres);
-    if (st->norm_x > o->diverge_norm) st->cls = ORC_AT_INFINITY;
+    if (st->norm_x > o->endpoint_inf_norm) st->cls = ORC_AT_INFINITY;
     else if (st->cond <= o->cond_regular && st->relres <= o->res_regular) st->cls = ORC_REGULAR;
     else st->cls = ORC_SINGULAR;
 }

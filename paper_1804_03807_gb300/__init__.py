@@ -16,14 +16,15 @@ from ._lib import (PHC_AT_INFINITY, PHC_FAILED, PHC_MAX_VARS, PHC_PREC_FP32_INTE
                    load, phc_cascade_stage, phc_default_opts, phc_embed, phc_last_error, phc_make_homotopy,
                    phc_make_homotopy_batch,
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
-                   phc_track_paths_noalloc)
+                   phc_track_paths_noalloc, phc_track_pipeline)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
     "PHC_SINGULAR", "PHC_STOP_REACHED", "STATS_DTYPE", "Homotopy", "PhcError", "SystemLists", "load",
     "phc_cascade_stage", "phc_default_opts", "phc_embed", "phc_last_error", "phc_make_homotopy",
     "phc_make_homotopy_batch", "phc_num_paths",
-    "phc_opts", "phc_refine_endpoints", "phc_track_paths", "phc_track_paths_noalloc", "Tracked", "track", "cascade", "refine",
+    "phc_opts", "phc_refine_endpoints", "phc_track_paths", "phc_track_paths_noalloc", "phc_track_pipeline",
+    "Tracked", "pipeline", "track", "cascade", "refine",
     "stats_numpy",
 ]
 
@@ -70,6 +71,21 @@ def cascade(h_k: Homotopy, k: int, starts, opts=None, stream=None) -> Tracked:
     sz = torch.empty(n, dtype=torch.uint8, device=starts.device)
     phc_cascade_stage(h_k, k, starts.contiguous(), n, opts, x, cls, sz, st, stream)
     return Tracked(x, cls, st, sz)
+
+
+def pipeline(h_k: Homotopy, k: int, first: int = 0, n_paths: int | None = None, opts=None, stream=None,
+             device="cuda"):
+    """Top stage of E_k and the cascade stage below it in one launch; returns
+    (top, next) Tracked records indexed by top path (next.cls = -1 where a
+    top endpoint was not continued)."""
+    import torch
+    if n_paths is None:
+        n_paths = phc_num_paths(h_k) - first
+    xt, ct, st = _alloc(h_k.n, n_paths, device)
+    xn, cn, sn = _alloc(h_k.n - 1, n_paths, device)
+    sz = torch.empty(n_paths, dtype=torch.uint8, device=device)
+    phc_track_pipeline(h_k, k, first, n_paths, opts, xt, ct, st, xn, cn, sz, sn, stream)
+    return Tracked(xt, ct, st), Tracked(xn, cn, sn, sz)
 
 
 def refine(h: Homotopy, r: Tracked, cond_threshold: float = 1e6, cond_max: float = 1e12, max_iters: int = 8,

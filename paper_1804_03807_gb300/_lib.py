@@ -25,7 +25,7 @@ PHC_NOALLOC_MAX_PATHS = 52428
 EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
-    "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch",
+    "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch", "phc_track_pipeline",
 ]
 
 
@@ -45,11 +45,11 @@ class phc_opts(ctypes.Structure):
         ("expand_after", ctypes.c_int32), ("expand", ctypes.c_double), ("shrink", ctypes.c_double),
         ("max_corr_iters", ctypes.c_int32), ("corr_tol", ctypes.c_double), ("corr_contract", ctypes.c_double),
         ("max_steps", ctypes.c_int32),
-        ("diverge_norm", ctypes.c_double), ("stall_inf_norm", ctypes.c_double), ("end_zone", ctypes.c_double),
+        ("diverge_norm", ctypes.c_double), ("endpoint_inf_norm", ctypes.c_double), ("end_zone", ctypes.c_double),
         ("growth_inf", ctypes.c_double),
         ("end_iters", ctypes.c_int32), ("end_tol", ctypes.c_double),
         ("cond_regular", ctypes.c_double), ("res_regular", ctypes.c_double), ("slack_tol", ctypes.c_double),
-        ("precision", ctypes.c_int32), ("fp32_t_max", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("fp32_t_max", ctypes.c_double), ("fp32_pivot_ratio", ctypes.c_double),
         ("block_threads", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
     ]
 
@@ -90,6 +90,7 @@ def load() -> ctypes.CDLL:
     L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_cascade_stage.argtypes = [vp, i32, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
+    L.phc_track_pipeline.argtypes = [vp, i32, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp, vp, vp, vp]
     L.phc_refine_endpoints.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]
     L.phc_last_error.restype = ctypes.c_char_p
     L.phc_destroy_homotopy.argtypes = [vp]
@@ -98,7 +99,7 @@ def load() -> ctypes.CDLL:
     L.phc_free_lists.restype = None
     for name in ("phc_default_opts", "phc_make_homotopy", "phc_make_homotopy_batch", "phc_num_paths",
                  "phc_track_paths",
-                 "phc_track_paths_noalloc", "phc_embed",
+                 "phc_track_paths_noalloc", "phc_track_pipeline", "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
@@ -237,6 +238,14 @@ def phc_cascade_stage(h: Homotopy, k: int, starts, n_starts: int, opts, x_out, c
     _check(load().phc_cascade_stage(ctypes.c_void_p(h.ptr), int(k), _ptr(starts), int(n_starts),
                                     ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
                                     _ptr(slack_zero_out), _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_track_pipeline(h: Homotopy, k: int, first_path: int, n_paths: int, opts, x_top, cls_top, stats_top, x_next,
+                       cls_next, slack_zero_next, stats_next, stream=None):
+    _check(load().phc_track_pipeline(ctypes.c_void_p(h.ptr), int(k), int(first_path), int(n_paths),
+                                     ctypes.byref(opts) if opts is not None else None, _ptr(x_top), _ptr(cls_top),
+                                     _ptr(stats_top), _ptr(x_next), _ptr(cls_next), _ptr(slack_zero_next),
+                                     _ptr(stats_next), _stream_ptr(stream)))
 
 
 def phc_refine_endpoints(h: Homotopy, x_hi, x_lo, n: int, cond_threshold: float, cond_max: float, max_iters: int,

@@ -55,7 +55,7 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->corr_contract = 0.5;
     o->max_steps = 20000;
     o->diverge_norm = 1e6;
-    o->stall_inf_norm = 1e4;
+    o->endpoint_inf_norm = 1e4;
     o->end_zone = 0.9;
     o->growth_inf = 1.1220184543019633;  // 10^0.05
     o->end_iters = 8;
@@ -65,6 +65,7 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->slack_tol = 1e-8;
     o->precision = PHC_PREC_FP64;
     o->fp32_t_max = 0.9;
+    o->fp32_pivot_ratio = 1e4;
     o->block_threads = 0;
     o->max_blocks = 0;
     return PHC_OK;
@@ -82,6 +83,7 @@ static int check_opts(const phc_opts &o)
     if (!(o.growth_inf >= 1.0)) return fail(PHC_EINVAL, "growth_inf must be >= 1");
     if (o.precision != PHC_PREC_FP64 && o.precision != PHC_PREC_FP32_INTERIOR)
         return fail(PHC_EINVAL, "unknown precision %d", o.precision);
+    if (!(o.fp32_pivot_ratio >= 1.0)) return fail(PHC_EINVAL, "fp32_pivot_ratio must be >= 1");
     if (o.block_threads < 0 || o.block_threads % 32) return fail(PHC_EINVAL, "block_threads must be a multiple of 32");
     return PHC_OK;
 }
@@ -114,6 +116,8 @@ struct phc_homotopy {
     unsigned long long *d_qhead = nullptr;
     phc_path_stats *d_stats = nullptr;
     int64_t stats_cap = 0;
+    phc_path_stats *d_stats2 = nullptr;
+    int64_t stats2_cap = 0;
     double2 *d_xfull = nullptr;
     int64_t xfull_cap = 0;
 };
@@ -168,7 +172,9 @@ static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
     size_t o_c0 = o_exps + V;
     o_c0 = (o_c0 + 15) & ~(size_t)15;
     const size_t o_c1 = o_c0 + C * sizeof(double2);
-    const size_t bytes = o_c1 + C * sizeof(double2);
+    const size_t o_c0f = o_c1 + C * sizeof(double2);
+    const size_t o_c1f = o_c0f + C * sizeof(float2);
+    const size_t bytes = o_c1f + C * sizeof(float2);
     std::vector<char> host(bytes, 0);
     std::memcpy(host.data() + o_terms, ht.recs.data(), T * sizeof(TermRec));
     if (V) {
@@ -177,6 +183,14 @@ static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
     }
     std::memcpy(host.data() + o_c0, ht.c0.data(), C * sizeof(double2));
     std::memcpy(host.data() + o_c1, ht.c1.data(), C * sizeof(double2));
+    {
+        float2 *f0 = reinterpret_cast<float2 *>(host.data() + o_c0f);
+        float2 *f1 = reinterpret_cast<float2 *>(host.data() + o_c1f);
+        for (size_t i = 0; i < C; i++) {
+            f0[i] = make_float2((float)ht.c0[i].x, (float)ht.c0[i].y);
+            f1[i] = make_float2((float)ht.c1[i].x, (float)ht.c1[i].y);
+        }
+    }
     void *blob = nullptr;
     if (cudaMalloc(&blob, bytes) != cudaSuccess) return fail(PHC_ENOMEM, "cudaMalloc of %zu table bytes", bytes);
     if (cudaMemcpy(blob, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -194,6 +208,8 @@ static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
     out.view.exps = reinterpret_cast<const uint8_t *>(b + o_exps);
     out.view.c0 = reinterpret_cast<const double2 *>(b + o_c0);
     out.view.c1 = reinterpret_cast<const double2 *>(b + o_c1);
+    out.view.c0f = reinterpret_cast<const float2 *>(b + o_c0f);
+    out.view.c1f = reinterpret_cast<const float2 *>(b + o_c1f);
     return PHC_OK;
 }
 
@@ -339,6 +355,7 @@ extern "C" void phc_destroy_homotopy(phc_homotopy *h)
     if (h->d_roots) cudaFree(h->d_roots);
     if (h->d_qhead) cudaFree(h->d_qhead);
     if (h->d_stats) cudaFree(h->d_stats);
+    if (h->d_stats2) cudaFree(h->d_stats2);
     if (h->d_xfull) cudaFree(h->d_xfull);
     delete h;
 }
@@ -493,6 +510,75 @@ extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *st
     cudaError_t e = phc::launch_drop_last(h->d_xfull, h->n, n, reinterpret_cast<double2 *>(x_out), slack_zero_out,
                                           k > 1 ? 1 : 0, o.slack_tol, s);
     if (e != cudaSuccess) return fail(PHC_ECUDA, "drop kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+static int ensure_stats2(phc_homotopy *h, int64_t n)
+{
+    if (h->stats2_cap >= n) return PHC_OK;
+    if (h->d_stats2) cudaFree(h->d_stats2);
+    h->d_stats2 = nullptr;
+    h->stats2_cap = 0;
+    if (cudaMalloc(&h->d_stats2, n * sizeof(phc_path_stats)) != cudaSuccess)
+        return fail(PHC_ENOMEM, "cudaMalloc of %lld path records", (long long)n);
+    h->stats2_cap = n;
+    return PHC_OK;
+}
+
+extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t n, const phc_opts *opts,
+                                  phc_cd *x_top, int8_t *cls_top, phc_path_stats *stats_top, phc_cd *x_next,
+                                  int8_t *cls_next, uint8_t *slack_zero_next, phc_path_stats *stats_next,
+                                  void *stream)
+{
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (k < 1 || k >= h->n) return fail(PHC_EINVAL, "cascade stage k = %d outside 1..%d", k, h->n - 1);
+    if (h->n_sys != 1) return fail(PHC_EUNSUPPORTED, "the pipeline needs a single-system handle");
+    if (n < 0 || first < 0 || first + n > h->num_paths)
+        return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + n), (long long)h->num_paths);
+    if (n == 0) return PHC_OK;
+    if (!x_top || !cls_top || !x_next || !cls_next || !slack_zero_next) return fail(PHC_EINVAL, "NULL output array");
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    rc = ensure_cascade(h);
+    if (rc) return rc;
+    phc_path_stats *st = stats_top, *st2 = stats_next;
+    if (!st) {
+        rc = ensure_stats(h, n);
+        if (rc) return rc;
+        st = h->d_stats;
+    }
+    if (!st2) {
+        rc = ensure_stats2(h, n);
+        if (rc) return rc;
+        st2 = h->d_stats2;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CU(cudaMemsetAsync(h->d_qhead, 0, sizeof(unsigned long long), s));
+    phc::TrackLaunch L{};
+    L.tab = h->total.view;
+    L.start_mode = 0;
+    L.deg = h->d_deg;
+    L.root_off = h->d_root_off;
+    L.roots = h->d_roots;
+    L.first = first;
+    L.n_paths = n;
+    L.paths_per_system = h->paths_per_system;
+    L.x_out = reinterpret_cast<double2 *>(x_top);
+    L.stats = st;
+    L.qhead = h->d_qhead;
+    L.o = o;
+    L.tab2 = h->cascade.view;
+    L.cls_out = cls_top;
+    L.x_out2 = reinterpret_cast<double2 *>(x_next);
+    L.cls_out2 = cls_next;
+    L.slack_zero2 = slack_zero_next;
+    L.stats2 = st2;
+    L.has_next_slack = k > 1 ? 1 : 0;
+    cudaError_t e = phc::launch_pipeline(L, o.block_threads, o.max_blocks, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "pipeline kernel launch: %s", cudaGetErrorString(e));
     return PHC_OK;
 }
 

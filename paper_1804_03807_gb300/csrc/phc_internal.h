@@ -40,15 +40,19 @@ struct DevTables {
     const uint8_t *exps;
     const double2 *c0;
     const double2 *c1;
+    const float2 *c0f;  // single precision copies (FP32 interior)
+    const float2 *c1f;
 };
 
+// Bytes of coefficients per term and system: c0, c1 in double, c0, c1 in float.
+constexpr size_t COEF_BYTES = 2 * 16 + 2 * 8;
 // Coefficients of all systems are staged into shared memory up to this size;
 // larger batches read them through L1.
 constexpr size_t COEF_SMEM_LIMIT = 48 * 1024;
 
 __host__ __device__ inline bool coefs_in_smem(const DevTables &t)
 {
-    return 2 * (size_t)t.n_terms * (size_t)t.n_sys * 16 <= COEF_SMEM_LIMIT;
+    return (size_t)t.n_terms * (size_t)t.n_sys * COEF_BYTES <= COEF_SMEM_LIMIT;
 }
 
 // Bytes the staged copy of a table takes in shared memory (16-byte aligned).
@@ -56,13 +60,18 @@ __host__ __device__ inline size_t table_smem_bytes(const DevTables &t)
 {
     size_t b = (size_t)t.n_terms * sizeof(TermRec) + 2 * (size_t)t.n_ve;
     b = (b + 15) & ~(size_t)15;
-    if (coefs_in_smem(t)) b += 2 * (size_t)t.n_terms * (size_t)t.n_sys * 16;
+    if (coefs_in_smem(t)) b += (size_t)t.n_terms * (size_t)t.n_sys * COEF_BYTES;
     return b;
 }
 
-// Per-thread shared memory of the tracker: xe, H, Ht, P (N each) and J (N*N),
-// complex double, plus S (N doubles... kept as double2 for alignment).
-inline size_t thread_smem_bytes(int n) { return (size_t)(n * n + 5 * n) * sizeof(double2); }
+// Per-thread shared memory: the evaluation point xe, the right-hand side R,
+// prefix products P, the single precision point X (N slots each), the
+// Jacobian J (N*N slots) and, for classification, the scales S (N slots);
+// one slot is a complex double (single precision values use its first half).
+inline size_t thread_smem_bytes(int n, bool scale = false)
+{
+    return (size_t)(n * n + 4 * n + (scale ? n : 0)) * sizeof(double2);
+}
 
 struct TrackLaunch {
     DevTables tab;
@@ -79,6 +88,15 @@ struct TrackLaunch {
     phc_path_stats *stats;    // [n_paths]
     unsigned long long *qhead;
     phc_opts o;
+    // pipeline: the cascade stage of tab2 continues every top endpoint that
+    // is regular with a nonzero last slack, in the same lane
+    DevTables tab2;
+    int8_t *cls_out;          // [n_paths] top-stage classes
+    double2 *x_out2;          // SoA [n - 1][n_paths]
+    int8_t *cls_out2;         // [n_paths], -1 when the path was not continued
+    uint8_t *slack_zero2;     // [n_paths]
+    phc_path_stats *stats2;   // [n_paths]
+    int has_next_slack;       // the stage's endpoints keep a slack z_{k-1}
 };
 
 struct ClassifyLaunch {
@@ -106,6 +124,7 @@ struct RefineLaunch {
 cudaError_t launch_roots(const int32_t *deg, const int32_t *root_off, double2 *roots, int n, int total,
                          cudaStream_t s);
 cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
+cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,
@@ -113,6 +132,6 @@ cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths,
 
 // Threads per block the tracker uses for n unknowns and a table of the given
 // size (fills up to the opt-in shared memory of one block).
-int track_block_threads(int n, size_t table_bytes, int requested);
+int track_block_threads(int n, size_t table_bytes, int requested, bool scale = false);
 
 }  // namespace phc

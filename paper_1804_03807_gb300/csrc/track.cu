@@ -31,28 +31,76 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
 // c - a b
 __device__ __forceinline__ double2 cfms(double2 c, double2 a, double2 b)
 {
     return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
 }
+__device__ __forceinline__ float2 cfms(float2 c, float2 a, float2 b)
+{
+    return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+// c + a b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c)
+{
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
 // a + s b
 __device__ __forceinline__ double2 caxpy(double2 a, double s, double2 b)
 {
     return make_double2(fma(s, b.x, a.x), fma(s, b.y, a.y));
 }
 __device__ __forceinline__ double abs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ float abs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
 __device__ __forceinline__ double absinf(double2 a)
 {
     double u = fabs(a.x), v = fabs(a.y);
     return u > v ? u : v;
 }
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+__device__ __forceinline__ double2 recip(double2 p)
+{
+    const double rd = 1.0 / fma(p.x, p.x, p.y * p.y);
+    return make_double2(p.x * rd, -p.y * rd);
+}
+__device__ __forceinline__ float2 recip(float2 p)
+{
+    const float rd = 1.0f / fmaf(p.x, p.x, p.y * p.y);
+    return make_float2(p.x * rd, -p.y * rd);
+}
+__device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 to_f(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_d(float2 a) { return make_double2((double)a.x, (double)a.y); }
+
+template <typename C> struct real_of;
+template <> struct real_of<double2> { typedef double type; };
+template <> struct real_of<float2> { typedef float type; };
 
 // Strided per-thread slot i of a shared array (stride = threads per block).
+// A slot holds a complex double; a complex float lives in its first half.
 #define SL(arr, i) (arr)[(i) * bt]
+
+template <typename C> __device__ __forceinline__ C ld(const double2 *a, int i, int bt);
+template <> __device__ __forceinline__ double2 ld<double2>(const double2 *a, int i, int bt) { return a[i * bt]; }
+template <> __device__ __forceinline__ float2 ld<float2>(const double2 *a, int i, int bt)
+{
+    return *reinterpret_cast<const float2 *>(a + i * bt);
+}
+__device__ __forceinline__ void st(double2 *a, int i, int bt, double2 v) { a[i * bt] = v; }
+__device__ __forceinline__ void st(double2 *a, int i, int bt, float2 v) { *reinterpret_cast<float2 *>(a + i * bt) = v; }
 
 // ------------------------------------------------------------------ tables in shared memory
 
@@ -63,6 +111,8 @@ struct SmTab {
     const uint8_t *exps;
     const double2 *c0;  // system 0; system s at + s * n_terms (shared or global memory)
     const double2 *c1;
+    const float2 *c0f;
+    const float2 *c1f;
 };
 
 __device__ SmTab stage_table(const DevTables &g, char *smem)
@@ -82,15 +132,23 @@ __device__ SmTab stage_table(const DevTables &g, char *smem)
         const int nc = g.n_terms * g.n_sys;
         double2 *c0 = reinterpret_cast<double2 *>(smem + b);
         double2 *c1 = c0 + nc;
+        float2 *c0f = reinterpret_cast<float2 *>(c1 + nc);
+        float2 *c1f = c0f + nc;
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             c0[i] = g.c0[i];
             c1[i] = g.c1[i];
+            c0f[i] = g.c0f[i];
+            c1f[i] = g.c1f[i];
         }
         s.c0 = c0;
         s.c1 = c1;
+        s.c0f = c0f;
+        s.c1f = c1f;
     } else {
         s.c0 = g.c0;
         s.c1 = g.c1;
+        s.c0f = g.c0f;
+        s.c1f = g.c1f;
     }
     __syncthreads();
     s.n_terms = g.n_terms;
@@ -102,85 +160,107 @@ __device__ SmTab stage_table(const DevTables &g, char *smem)
 
 // ------------------------------------------------------------------ evaluation
 
-// H(xe,t), H_x (row-major N x N in J) and H_t at the thread's point xe.
+// One pass over the terms at the thread's point X (slots of complex C):
+// J = H_x (row-major N x N) and, when want_rhs, R = H_t (dt) or H (!dt).
 // Each term c(t) x^a with support v_0..v_{k-1} is split as
 //   x^a = cf * prod_j x_{v_j},  cf = prod_j x_{v_j}^{a_j - 1}   (common factor)
 // and its partial derivatives come from prefix and suffix products of the
 // x_{v_j} (Speelpenning's product rule):
 //   d/dx_{v_j} c(t) x^a = a_j c(t) cf prod_{i<j} x_{v_i} prod_{i>j} x_{v_i}.
 // With SCALE, S[i].x accumulates sum over the terms of equation i of
-// |c(t)|_1 |x^a|_1 (for the relative residual and the condition number).
-template <int N, bool SCALE>
-__device__ __forceinline__ void evaluate(const SmTab &tb, int sys, double t, const double2 *xe, double2 *H,
-                                         double2 *Ht, double2 *J, double2 *P, double2 *S, int bt)
+// |c(t)|_1 |x^a|_1 (relative residual and condition number; double only).
+template <int N, typename C, bool SCALE>
+__device__ __forceinline__ void evaluate(const C *C0, const C *C1, const SmTab &tb,
+                                         typename real_of<C>::type t, bool dt, bool want_rhs, const double2 *X,
+                                         double2 *R, double2 *J, double2 *P, double2 *S, int bt)
 {
-    const double2 *C0 = tb.c0 + (size_t)sys * tb.n_terms;
-    const double2 *C1 = tb.c1 + (size_t)sys * tb.n_terms;
-    const double2 zero = make_double2(0.0, 0.0);
+    typedef typename real_of<C>::type Real;
+    const C zero = {Real(0), Real(0)};
+    const C one = {Real(1), Real(0)};
 #pragma unroll
     for (int i = 0; i < N; i++) {
-        SL(H, i) = zero;
-        SL(Ht, i) = zero;
-        if (SCALE) SL(S, i) = zero;
+        if (want_rhs) st(R, i, bt, zero);
+        if (SCALE) SL(S, i) = make_double2(0.0, 0.0);
     }
 #pragma unroll
-    for (int i = 0; i < N * N; i++) SL(J, i) = zero;
+    for (int i = 0; i < N * N; i++) st(J, i, bt, zero);
 
     for (int q = 0; q < tb.n_terms; q++) {
         const TermRec r = tb.terms[q];
-        const double2 c0 = C0[q], c1 = C1[q];
-        const double2 ct = make_double2(fma(t, c1.x, c0.x), fma(t, c1.y, c0.y));
+        const C c0 = C0[q], c1 = C1[q];
+        const C ct = {fmar(t, c1.x, c0.x), fmar(t, c1.y, c0.y)};
+        const C cr = dt ? c1 : ct;  // coefficient of the right-hand side
         const int k = r.k;
         if (k == 0) {
-            SL(H, r.eq) = cadd(SL(H, r.eq), ct);
-            SL(Ht, r.eq) = cadd(SL(Ht, r.eq), c1);
+            if (want_rhs) st(R, r.eq, bt, cadd(ld<C>(R, r.eq, bt), cr));
             if (SCALE) SL(S, r.eq).x += abs1(ct);
             continue;
         }
         const uint8_t *v = tb.vars + r.off;
         const uint8_t *e = tb.exps + r.off;
-        double2 cf = make_double2(1.0, 0.0);
+        C cf = one;
         const bool powers = (r.flags & TERM_POWERS) != 0;
         if (powers) {
             for (int j = 0; j < k; j++) {
                 const int a = e[j];
                 if (a > 1) {
-                    const double2 xv = SL(xe, v[j]);
-                    double2 pw = xv;
+                    const C xv = ld<C>(X, v[j], bt);
+                    C pw = xv;
                     for (int m = 2; m < a; m++) pw = cmul(pw, xv);
                     cf = cmul(cf, pw);
                 }
             }
         }
         // prefix products: P[j] = ct cf prod_{i<j} x_{v_i}
-        double2 pre = powers ? cmul(ct, cf) : ct;
-        SL(P, 0) = pre;
+        C pre = powers ? cmul(ct, cf) : ct;
+        st(P, 0, bt, pre);
         for (int j = 1; j < k; j++) {
-            pre = cmul(pre, SL(xe, v[j - 1]));
-            SL(P, j) = pre;
+            pre = cmul(pre, ld<C>(X, v[j - 1], bt));
+            st(P, j, bt, pre);
         }
         // suffix products and the derivatives
-        double2 suf = SL(xe, v[k - 1]);
+        C suf = ld<C>(X, v[k - 1], bt);
         {
-            double2 d = SL(P, k - 1);
+            C d = ld<C>(P, k - 1, bt);
             const int a = e[k - 1];
-            if (a > 1) d = cscale((double)a, d);
+            if (a > 1) d = cscale((Real)a, d);
             const int idx = r.eq * N + v[k - 1];
-            SL(J, idx) = cadd(SL(J, idx), d);
+            st(J, idx, bt, cadd(ld<C>(J, idx, bt), d));
         }
         for (int j = k - 2; j >= 0; j--) {
-            double2 d = cmul(SL(P, j), suf);
+            C d = cmul(ld<C>(P, j, bt), suf);
             const int a = e[j];
-            if (a > 1) d = cscale((double)a, d);
+            if (a > 1) d = cscale((Real)a, d);
             const int idx = r.eq * N + v[j];
-            SL(J, idx) = cadd(SL(J, idx), d);
-            suf = cmul(suf, SL(xe, v[j]));
+            st(J, idx, bt, cadd(ld<C>(J, idx, bt), d));
+            suf = cmul(suf, ld<C>(X, v[j], bt));
         }
         // suf = prod_j x_{v_j}; the monomial is cf * suf
-        const double2 mono = powers ? cmul(cf, suf) : suf;
-        SL(H, r.eq) = cadd(SL(H, r.eq), cmul(ct, mono));
-        SL(Ht, r.eq) = cadd(SL(Ht, r.eq), cmul(c1, mono));
+        const C mono = powers ? cmul(cf, suf) : suf;
+        if (want_rhs) st(R, r.eq, bt, cfma(cr, mono, ld<C>(R, r.eq, bt)));
         if (SCALE) SL(S, r.eq).x += abs1(ct) * abs1(mono);
+    }
+}
+
+// R = H(X, t) in double, values only (the residual of a Newton correction
+// whose Jacobian is factored in single precision).
+template <int N>
+__device__ __forceinline__ void residual64(const double2 *C0, const double2 *C1, const SmTab &tb, double t,
+                                           const double2 *X, double2 *R, int bt)
+{
+#pragma unroll
+    for (int i = 0; i < N; i++) SL(R, i) = make_double2(0.0, 0.0);
+    for (int q = 0; q < tb.n_terms; q++) {
+        const TermRec r = tb.terms[q];
+        const double2 c0 = C0[q], c1 = C1[q];
+        double2 m = make_double2(fma(t, c1.x, c0.x), fma(t, c1.y, c0.y));
+        const uint8_t *v = tb.vars + r.off;
+        const uint8_t *e = tb.exps + r.off;
+        for (int j = 0; j < r.k; j++) {
+            const double2 xv = SL(X, v[j]);
+            for (int a = 0; a < e[j]; a++) m = cmul(m, xv);
+        }
+        SL(R, r.eq) = cadd(SL(R, r.eq), m);
     }
 }
 
@@ -190,75 +270,86 @@ __device__ __forceinline__ void evaluate(const SmTab &tb, int sys, double t, con
 // column k is the first row of largest |.|_1; rows are swapped whole (the
 // multipliers move with them); the diagonal is replaced by its reciprocal.
 // Returns false when a pivot is zero (or not a number).
-template <int N>
-__device__ __forceinline__ bool lu_factor(double2 *J, int (&perm)[N], int bt)
+// A single precision factorization whose pivots spread by more than
+// max_ratio counts as failed (the step is retried in double): the spread
+// bounds the condition number from below, and a float Jacobian with a
+// condition number of 1e4 keeps about three digits.
+template <int N, typename C>
+__device__ __forceinline__ bool lu_factor(double2 *J, int (&perm)[N], int bt, float max_ratio = 0.0f)
 {
+    typedef typename real_of<C>::type Real;
+    const bool guard = sizeof(Real) == 4;
+    Real pmin = Real(0), pmax = Real(0);
 #pragma unroll
     for (int k = 0; k < N; k++) {
         int p = k;
-        double best = abs1(SL(J, k * N + k));
+        Real best = abs1(ld<C>(J, k * N + k, bt));
 #pragma unroll
         for (int i = k + 1; i < N; i++) {
-            const double val = abs1(SL(J, i * N + k));
+            const Real val = abs1(ld<C>(J, i * N + k, bt));
             if (val > best) {
                 best = val;
                 p = i;
             }
         }
         perm[k] = p;
-        if (!(best > 0.0)) return false;
+        if (!(best > Real(0))) return false;
+        if (guard) {
+            pmin = (k == 0 || best < pmin) ? best : pmin;
+            pmax = (k == 0 || best > pmax) ? best : pmax;
+        }
 #pragma unroll
         for (int j = 0; j < N; j++) {
-            const double2 a = SL(J, k * N + j), c = SL(J, p * N + j);
-            SL(J, k * N + j) = c;
-            SL(J, p * N + j) = a;
+            const C a = ld<C>(J, k * N + j, bt), c = ld<C>(J, p * N + j, bt);
+            st(J, k * N + j, bt, c);
+            st(J, p * N + j, bt, a);
         }
-        const double2 pv = SL(J, k * N + k);
-        const double rd = 1.0 / fma(pv.x, pv.x, pv.y * pv.y);
-        const double2 inv = make_double2(pv.x * rd, -pv.y * rd);
-        SL(J, k * N + k) = inv;
+        const C inv = recip(ld<C>(J, k * N + k, bt));
+        st(J, k * N + k, bt, inv);
 #pragma unroll
         for (int i = k + 1; i < N; i++) {
-            const double2 l = cmul(SL(J, i * N + k), inv);
-            SL(J, i * N + k) = l;
+            const C l = cmul(ld<C>(J, i * N + k, bt), inv);
+            st(J, i * N + k, bt, l);
 #pragma unroll
-            for (int j = k + 1; j < N; j++) SL(J, i * N + j) = cfms(SL(J, i * N + j), l, SL(J, k * N + j));
+            for (int j = k + 1; j < N; j++)
+                st(J, i * N + j, bt, cfms(ld<C>(J, i * N + j, bt), l, ld<C>(J, k * N + j, bt)));
         }
     }
+    if (guard && pmax > Real(max_ratio) * pmin) return false;
     return true;
 }
 
 // b := (LU)^{-1} P b in place (b strided in shared memory).
-template <int N>
+template <int N, typename C>
 __device__ __forceinline__ void lu_solve(const double2 *J, const int (&perm)[N], double2 *b, int bt)
 {
 #pragma unroll
     for (int k = 0; k < N; k++) {
         const int p = perm[k];
-        const double2 a = SL(b, k), c = SL(b, p);
-        SL(b, k) = c;
-        SL(b, p) = a;
+        const C a = ld<C>(b, k, bt), c = ld<C>(b, p, bt);
+        st(b, k, bt, c);
+        st(b, p, bt, a);
     }
 #pragma unroll
     for (int i = 1; i < N; i++) {
-        double2 s = SL(b, i);
+        C s = ld<C>(b, i, bt);
 #pragma unroll
-        for (int j = 0; j < i; j++) s = cfms(s, SL(J, i * N + j), SL(b, j));
-        SL(b, i) = s;
+        for (int j = 0; j < i; j++) s = cfms(s, ld<C>(J, i * N + j, bt), ld<C>(b, j, bt));
+        st(b, i, bt, s);
     }
 #pragma unroll
     for (int i = N - 1; i >= 0; i--) {
-        double2 s = SL(b, i);
+        C s = ld<C>(b, i, bt);
 #pragma unroll
-        for (int j = i + 1; j < N; j++) s = cfms(s, SL(J, i * N + j), SL(b, j));
-        SL(b, i) = cmul(s, SL(J, i * N + i));
+        for (int j = i + 1; j < N; j++) s = cfms(s, ld<C>(J, i * N + j, bt), ld<C>(b, j, bt));
+        st(b, i, bt, cmul(s, ld<C>(J, i * N + i, bt)));
     }
 }
 
 // ------------------------------------------------------------------ tracker
 
 struct ThreadArrays {
-    double2 *xe, *H, *Ht, *P, *S, *J;
+    double2 *xe, *R, *P, *X, *J, *S;
 };
 
 template <int N>
@@ -266,32 +357,137 @@ __device__ __forceinline__ ThreadArrays thread_arrays(char *smem, size_t table_b
 {
     ThreadArrays a;
     a.xe = reinterpret_cast<double2 *>(smem + table_bytes) + threadIdx.x;
-    a.H = a.xe + N * bt;
-    a.Ht = a.H + N * bt;
-    a.P = a.Ht + N * bt;
-    a.S = a.P + N * bt;
-    a.J = a.S + N * bt;
+    a.R = a.xe + N * bt;
+    a.P = a.R + N * bt;
+    a.X = a.P + N * bt;
+    a.J = a.X + N * bt;
+    a.S = a.J + N * N * bt;  // classification only
     return a;
 }
 
+// ------------------------------------------------------------------ classification
+
+// Condition number, relative residual and class of the endpoint in A.xe (the
+// readings in include/phc.h, identical to the oracle's).  s carries stop, t,
+// grew and system in; cond, relres and norm_x (and stop for a non-finite
+// endpoint) out.
 template <int N>
-__global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t table_bytes)
+__device__ __forceinline__ int8_t classify_one(const SmTab &tb, const ThreadArrays &A, phc_path_stats &s,
+                                               const phc_opts &o, int bt)
+{
+    int perm[N];
+    bool fin = true;
+    double nx = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        const double2 xj = SL(A.xe, j);
+        fin = fin && finite2(xj);
+        const double a = absinf(xj);
+        if (!(a <= nx)) nx = a;
+    }
+    int8_t cls = PHC_FAILED;
+    double cond = NAN, relres = NAN;
+    if (fin && s.stop != PHC_STOP_DIVERGED) {
+        const double2 *C0 = tb.c0 + (size_t)s.system * tb.n_terms, *C1 = tb.c1 + (size_t)s.system * tb.n_terms;
+        evaluate<N, double2, true>(C0, C1, tb, 1.0, false, true, A.xe, A.R, A.J, A.P, A.S, bt);
+        double rr = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            const double r = abs1(SL(A.R, i)) / (1.0 + SL(A.S, i).x);
+            if (!(r <= rr)) rr = r;
+        }
+        relres = rr;
+        if (!lu_factor<N, double2>(A.J, perm, bt)) {
+            cond = INFINITY;
+        } else {
+            double rowacc[N];
+#pragma unroll
+            for (int j = 0; j < N; j++) rowacc[j] = 0.0;
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+#pragma unroll
+                for (int j = 0; j < N; j++) SL(A.R, j) = make_double2(i == j ? 1.0 : 0.0, 0.0);
+                lu_solve<N, double2>(A.J, perm, A.R, bt);
+                const double si = 1.0 + SL(A.S, i).x;
+#pragma unroll
+                for (int j = 0; j < N; j++) rowacc[j] += abs1(SL(A.R, j)) * si;
+            }
+            double m = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; j++)
+                if (!(rowacc[j] <= m)) m = rowacc[j];
+            cond = m / (1.0 + nx);
+            if (!isfinite(cond)) cond = INFINITY;
+        }
+    }
+    if (!fin) {
+        cls = PHC_FAILED;
+        s.stop = PHC_STOP_NONFINITE;
+        nx = NAN;
+    } else if (s.stop == PHC_STOP_DIVERGED) {
+        cls = PHC_AT_INFINITY;
+        cond = INFINITY;
+    } else if (s.stop != PHC_STOP_REACHED) {
+        if (nx > o.endpoint_inf_norm || (s.t >= o.end_zone && s.grew)) cls = PHC_AT_INFINITY;
+        else if (s.t < o.end_zone) cls = PHC_FAILED;
+        else cls = PHC_SINGULAR;
+    } else {
+        if (nx > o.endpoint_inf_norm) cls = PHC_AT_INFINITY;
+        else if (cond <= o.cond_regular && relres <= o.res_regular) cls = PHC_REGULAR;
+        else cls = PHC_SINGULAR;
+    }
+    s.cond = cond;
+    s.relres = relres;
+    s.norm_x = nx;
+    return cls;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) classify_kernel(const ClassifyLaunch L, size_t table_bytes)
 {
     extern __shared__ __align__(16) char smem[];
     const SmTab tb = stage_table(L.tab, smem);
     const int bt = blockDim.x;
     const ThreadArrays A = thread_arrays<N>(smem, table_bytes, bt);
+    const int64_t np = L.n_paths;
+    for (int64_t q = (int64_t)blockIdx.x * bt + threadIdx.x; q < np; q += (int64_t)gridDim.x * bt) {
+        phc_path_stats s = L.stats[q];
+#pragma unroll
+        for (int j = 0; j < N; j++) SL(A.xe, j) = L.x[(int64_t)j * np + q];
+        const int8_t cls = classify_one<N>(tb, A, s, L.o, bt);
+        L.stats[q] = s;
+        L.cls[q] = cls;
+    }
+}
+
+// Largest ||x|| at which a step may run in single precision (x^d stays far
+// from the float range for the degrees the library accepts).
+#define FP32_NORM_LIMIT 1.0e4
+
+template <int N, bool PIPE>
+__global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t table_bytes, size_t table2_bytes)
+{
+    extern __shared__ __align__(16) char smem[];
+    const SmTab tb = stage_table(L.tab, smem);
+    SmTab tb2 = tb;
+    if (PIPE) tb2 = stage_table(L.tab2, smem + table_bytes);
+    const int bt = blockDim.x;
+    const ThreadArrays A = thread_arrays<N>(smem, table_bytes + table2_bytes, bt);
+    int stage = 0;  // pipeline: 0 top homotopy, 1 cascade stage
+    const SmTab *cur = &tb;
     const phc_opts &o = L.o;
     const int64_t np = L.n_paths;
+    const bool interior32 = o.precision == PHC_PREC_FP32_INTERIOR;
 
-    double2 x0[N], acc[N];
+    double2 x0[N], acc[N], sol[N];
     int perm[N];
     int64_t q = -1;
     int sys = 0;
-    double t = 0.0, h = 0.0, he = 0.0, t1 = 0.0, te = 0.0, prev = 0.0, next_s = 0.0;
+    double t = 0.0, h = 0.0, he = 0.0, t1 = 0.0, te = 0.0, prev = 0.0, next_s = 0.0, nx0 = 0.0;
     double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0;  // last five decade checkpoints, r4 newest
     int streak = 0, steps = 0, phase = 0, it = 0, nck = 0;
-    int n_acc = 0, n_rej = 0, n_newt = 0, n_solve = 0;
+    int n_acc = 0, n_rej = 0, n_newt = 0, n_solve = 0, n_f32 = 0;
+    bool use32 = false, fp32_off = false;  // fp32_off: the path fell back to double for good
 
     // start a new step from the accepted point x0
     auto begin_step = [&]() {
@@ -308,10 +504,32 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
         }
         te = t;
         phase = 0;
+        use32 = interior32 && !fp32_off && t1 <= o.fp32_t_max && nx0 <= FP32_NORM_LIMIT;
+    };
+
+    // reset the per-path state and start tracking from x0 at t = 0
+    auto start_path = [&]() {
+        double nx = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            const double a = absinf(x0[i]);
+            if (!(a <= nx)) nx = a;
+        }
+        nx0 = nx;
+        t = 0.0;
+        h = o.h_init;
+        streak = steps = 0;
+        nck = 0;
+        next_s = 0.1;
+        r0 = r1 = r2 = r3 = r4 = 0.0;
+        n_acc = n_rej = n_newt = n_solve = n_f32 = 0;
+        fp32_off = false;
+        begin_step();
     };
 
     auto finish = [&](int stop) {
-        for (int j = 0; j < N; j++) L.x_out[(int64_t)j * np + q] = x0[j];
+        if (!PIPE || stage == 0)
+            for (int j = 0; j < N; j++) L.x_out[(int64_t)j * np + q] = x0[j];
         int grew = 0;
         double growth = 0.0;
         if (nck >= 2) {
@@ -334,10 +552,41 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
         s.n_newton = n_newt;
         s.n_solve = n_solve;
         s.stop = stop;
-        s.n_fp32 = 0;
+        s.n_fp32 = n_f32;
         s.grew = grew;
         s.system = sys;
-        L.stats[q] = s;
+        if (!PIPE) {
+            L.stats[q] = s;
+            q = -1;
+            return;
+        }
+        // pipeline: classify here; continue regular endpoints with z_k != 0
+#pragma unroll
+        for (int j = 0; j < N; j++) SL(A.xe, j) = x0[j];
+        const int8_t c = classify_one<N>(*cur, A, s, o, bt);
+        if (stage == 0) {
+            L.stats[q] = s;
+            L.cls_out[q] = c;
+            const bool fwd = c == PHC_REGULAR && absinf(x0[N - 1]) > o.slack_tol * (1.0 + s.norm_x);
+            if (fwd) {
+                stage = 1;
+                cur = &tb2;
+                sys = 0;
+                start_path();
+                return;
+            }
+            L.cls_out2[q] = -1;
+        } else {
+            double nx = 0.0;
+            for (int j = 0; j < N - 1; j++) {
+                L.x_out2[(int64_t)j * np + q] = x0[j];
+                const double a = absinf(x0[j]);
+                if (!(a <= nx)) nx = a;
+            }
+            L.stats2[q] = s;
+            L.cls_out2[q] = c;
+            L.slack_zero2[q] = L.has_next_slack ? (absinf(x0[N - 2]) <= o.slack_tol * (1.0 + nx)) : 0;
+        }
         q = -1;
     };
 
@@ -345,10 +594,16 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
         n_rej++;
         steps++;
         streak = 0;
-        h = he * o.shrink;
-        if (h < o.h_min) {
-            finish(PHC_STOP_STEP_MIN);
-            return;
+        if (use32) {
+            // a single precision step that failed is retried in double, and
+            // the rest of the path stays in double
+            fp32_off = true;
+        } else {
+            h = he * o.shrink;
+            if (h < o.h_min) {
+                finish(PHC_STOP_STEP_MIN);
+                return;
+            }
         }
         if (steps >= o.max_steps) {
             finish(PHC_STOP_BUDGET);
@@ -366,6 +621,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             const double a = absinf(x0[j]);
             if (!(a <= nx)) nx = a;
         }
+        nx0 = nx;
         n_acc++;
         steps++;
         while (1.0 - t <= next_s && next_s > 0.0) {
@@ -395,6 +651,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             phase = 5;  // end Newton at t = 1 from x0 (already in xe)
             it = 0;
             te = 1.0;
+            use32 = false;
         } else {
             begin_step();
         }
@@ -405,6 +662,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             const unsigned long long c = atomicAdd(L.qhead, 1ull);
             if (c >= (unsigned long long)np) break;
             q = (int64_t)c;
+            double nx = 0.0;
             if (L.start_mode == 0) {
                 const int64_t gid = L.first + q;
                 sys = (int)(gid / L.paths_per_system);
@@ -417,36 +675,62 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                     x0[i] = L.roots[L.root_off[i] + k];
                 }
             } else {
+                sys = 0;
 #pragma unroll
                 for (int i = 0; i < N; i++) x0[i] = L.starts[(int64_t)i * np + q];
             }
-            t = 0.0;
-            h = o.h_init;
-            streak = steps = 0;
-            nck = 0;
-            next_s = 0.1;
-            r0 = r1 = r2 = r3 = r4 = 0.0;
-            n_acc = n_rej = n_newt = n_solve = 0;
-            begin_step();
+            (void)nx;
+            if (PIPE) {
+                stage = 0;
+                cur = &tb;
+            }
+            start_path();
         }
 
         // one unit: evaluate, factor, solve
-        evaluate<N, false>(tb, sys, te, A.xe, A.H, A.Ht, A.J, A.P, A.S, bt);
-        double2 *b = (phase < 4) ? A.Ht : A.H;
-        const bool ok = lu_factor<N>(A.J, perm, bt);
-        if (ok) lu_solve<N>(A.J, perm, b, bt);
+        const bool dt = phase < 4;
+        bool ok;
+        if (use32) {
+            // single precision Jacobian and factorization; the right-hand side
+            // of a Newton correction is the double precision residual
+            const float2 *C0f = cur->c0f + (size_t)sys * cur->n_terms, *C1f = cur->c1f + (size_t)sys * cur->n_terms;
+#pragma unroll
+            for (int j = 0; j < N; j++) st(A.X, j, bt, to_f(SL(A.xe, j)));
+            if (!dt) {
+                const double2 *C0 = cur->c0 + (size_t)sys * cur->n_terms, *C1 = cur->c1 + (size_t)sys * cur->n_terms;
+                residual64<N>(C0, C1, *cur, te, A.xe, A.R, bt);
+#pragma unroll
+                for (int j = 0; j < N; j++) st(A.R, j, bt, to_f(SL(A.R, j)));
+            }
+            evaluate<N, float2, false>(C0f, C1f, *cur, (float)te, true, dt, A.X, A.R, A.J, A.P, A.S, bt);
+            ok = lu_factor<N, float2>(A.J, perm, bt, (float)o.fp32_pivot_ratio);
+            if (ok) lu_solve<N, float2>(A.J, perm, A.R, bt);
+#pragma unroll
+            for (int j = 0; j < N; j++) sol[j] = to_d(ld<float2>(A.R, j, bt));
+            n_f32++;
+        } else {
+            const double2 *C0 = cur->c0 + (size_t)sys * cur->n_terms, *C1 = cur->c1 + (size_t)sys * cur->n_terms;
+            evaluate<N, double2, false>(C0, C1, *cur, te, dt, true, A.xe, A.R, A.J, A.P, A.S, bt);
+            ok = lu_factor<N, double2>(A.J, perm, bt);
+            if (ok) lu_solve<N, double2>(A.J, perm, A.R, bt);
+#pragma unroll
+            for (int j = 0; j < N; j++) sol[j] = SL(A.R, j);
+        }
         n_solve++;
 
         if (phase < 4) {
             // Runge-Kutta stage: k = -J^{-1} H_t
-            if (!ok) {
+            bool fin = ok;
+#pragma unroll
+            for (int j = 0; j < N; j++) fin = fin && finite2(sol[j]);
+            if (!fin) {
                 reject();
                 continue;
             }
             if (phase == 0) {
 #pragma unroll
                 for (int j = 0; j < N; j++) {
-                    const double2 kj = make_double2(-SL(b, j).x, -SL(b, j).y);
+                    const double2 kj = make_double2(-sol[j].x, -sol[j].y);
                     acc[j] = kj;
                     SL(A.xe, j) = caxpy(x0[j], 0.5 * he, kj);
                 }
@@ -455,7 +739,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             } else if (phase == 1) {
 #pragma unroll
                 for (int j = 0; j < N; j++) {
-                    const double2 kj = make_double2(-SL(b, j).x, -SL(b, j).y);
+                    const double2 kj = make_double2(-sol[j].x, -sol[j].y);
                     acc[j] = caxpy(acc[j], 2.0, kj);
                     SL(A.xe, j) = caxpy(x0[j], 0.5 * he, kj);
                 }
@@ -464,7 +748,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             } else if (phase == 2) {
 #pragma unroll
                 for (int j = 0; j < N; j++) {
-                    const double2 kj = make_double2(-SL(b, j).x, -SL(b, j).y);
+                    const double2 kj = make_double2(-sol[j].x, -sol[j].y);
                     acc[j] = caxpy(acc[j], 2.0, kj);
                     SL(A.xe, j) = caxpy(x0[j], he, kj);
                 }
@@ -474,7 +758,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 const double w = he / 6.0;
 #pragma unroll
                 for (int j = 0; j < N; j++) {
-                    const double2 kj = make_double2(-SL(b, j).x, -SL(b, j).y);
+                    const double2 kj = make_double2(-sol[j].x, -sol[j].y);
                     acc[j] = cadd(acc[j], kj);
                     SL(A.xe, j) = caxpy(x0[j], w, acc[j]);
                 }
@@ -494,7 +778,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             bool fin = true;
 #pragma unroll
             for (int j = 0; j < N; j++) {
-                const double2 dj = SL(b, j);
+                const double2 dj = sol[j];
                 const double2 xj = make_double2(SL(A.xe, j).x - dj.x, SL(A.xe, j).y - dj.y);
                 SL(A.xe, j) = xj;
                 const double a = absinf(dj);
@@ -514,7 +798,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 if (++it >= o.max_corr_iters) reject();
             }
         } else {
-            // Newton at t = 1
+            // Newton at t = 1 (always double precision)
             n_newt++;
             if (!ok) {
                 finish(PHC_STOP_REACHED);
@@ -524,7 +808,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             bool fin = true;
 #pragma unroll
             for (int j = 0; j < N; j++) {
-                const double2 dj = SL(b, j);
+                const double2 dj = sol[j];
                 const double2 xj = make_double2(SL(A.xe, j).x - dj.x, SL(A.xe, j).y - dj.y);
                 SL(A.xe, j) = xj;
                 x0[j] = xj;
@@ -539,98 +823,6 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             } else if (d <= o.end_tol * (1.0 + nx) || ++it >= o.end_iters) {
                 finish(PHC_STOP_REACHED);
             }
-        }
-    }
-}
-
-// ------------------------------------------------------------------ classification
-
-// Condition number, relative residual and class of every endpoint (the
-// readings in include/phc.h, identical to the oracle's).
-template <int N>
-__global__ void __launch_bounds__(256) classify_kernel(const ClassifyLaunch L, size_t table_bytes)
-{
-    extern __shared__ __align__(16) char smem[];
-    const SmTab tb = stage_table(L.tab, smem);
-    const int bt = blockDim.x;
-    const ThreadArrays A = thread_arrays<N>(smem, table_bytes, bt);
-    const phc_opts &o = L.o;
-    const int64_t np = L.n_paths;
-    int perm[N];
-
-    for (int64_t q = (int64_t)blockIdx.x * bt + threadIdx.x; q < np; q += (int64_t)gridDim.x * bt) {
-        const bool active = true;
-        phc_path_stats s;
-        bool fin = true;
-        double nx = 0.0;
-        if (active) {
-            s = L.stats[q];
-#pragma unroll
-            for (int j = 0; j < N; j++) {
-                const double2 xj = L.x[(int64_t)j * np + q];
-                SL(A.xe, j) = xj;
-                fin = fin && finite2(xj);
-                const double a = absinf(xj);
-                if (!(a <= nx)) nx = a;
-            }
-        }
-        int8_t cls = PHC_FAILED;
-        double cond = NAN, relres = NAN;
-        const bool measure = active && fin && s.stop != PHC_STOP_DIVERGED;
-        if (measure) {
-            evaluate<N, true>(tb, s.system, 1.0, A.xe, A.H, A.Ht, A.J, A.P, A.S, bt);
-            double rr = 0.0;
-#pragma unroll
-            for (int i = 0; i < N; i++) {
-                const double r = abs1(SL(A.H, i)) / (1.0 + SL(A.S, i).x);
-                if (!(r <= rr)) rr = r;
-            }
-            relres = rr;
-            if (!lu_factor<N>(A.J, perm, bt)) {
-                cond = INFINITY;
-            } else {
-                double rowacc[N];
-#pragma unroll
-                for (int j = 0; j < N; j++) rowacc[j] = 0.0;
-#pragma unroll
-                for (int i = 0; i < N; i++) {
-#pragma unroll
-                    for (int j = 0; j < N; j++) SL(A.H, j) = make_double2(i == j ? 1.0 : 0.0, 0.0);
-                    lu_solve<N>(A.J, perm, A.H, bt);
-                    const double si = 1.0 + SL(A.S, i).x;
-#pragma unroll
-                    for (int j = 0; j < N; j++) rowacc[j] += abs1(SL(A.H, j)) * si;
-                }
-                double m = 0.0;
-#pragma unroll
-                for (int j = 0; j < N; j++)
-                    if (!(rowacc[j] <= m)) m = rowacc[j];
-                cond = m / (1.0 + nx);
-                if (!isfinite(cond)) cond = INFINITY;
-            }
-        }
-        if (active) {
-            if (!fin) {
-                cls = PHC_FAILED;
-                s.stop = PHC_STOP_NONFINITE;
-                nx = NAN;
-            } else if (s.stop == PHC_STOP_DIVERGED) {
-                cls = PHC_AT_INFINITY;
-                cond = INFINITY;
-            } else if (s.stop != PHC_STOP_REACHED) {
-                if (nx > o.stall_inf_norm || (s.t >= o.end_zone && s.grew)) cls = PHC_AT_INFINITY;
-                else if (s.t < o.end_zone) cls = PHC_FAILED;
-                else cls = PHC_SINGULAR;
-            } else {
-                if (nx > o.diverge_norm) cls = PHC_AT_INFINITY;
-                else if (cond <= o.cond_regular && relres <= o.res_regular) cls = PHC_REGULAR;
-                else cls = PHC_SINGULAR;
-            }
-            s.cond = cond;
-            s.relres = relres;
-            s.norm_x = nx;
-            L.stats[q] = s;
-            L.cls[q] = cls;
         }
     }
 }
@@ -679,10 +871,10 @@ static void device_limits()
     cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 }
 
-int track_block_threads(int n, size_t table_bytes, int requested)
+int track_block_threads(int n, size_t table_bytes, int requested, bool scale)
 {
     device_limits();
-    const size_t per = thread_smem_bytes(n);
+    const size_t per = thread_smem_bytes(n, scale);
     long fit = ((long)g_smem_optin - (long)table_bytes) / (long)per;
     int bt = (int)((fit / 32) * 32);
     if (bt > 256) bt = 256;
@@ -691,15 +883,17 @@ int track_block_threads(int n, size_t table_bytes, int requested)
     return bt;
 }
 
-template <int N>
+template <int N, bool PIPE>
 static cudaError_t launch_track_n(const TrackLaunch &L, int bt, int max_blocks, cudaStream_t s)
 {
     const size_t tb = table_smem_bytes(L.tab);
-    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N);
-    cudaError_t e = cudaFuncSetAttribute(track_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t tb2 = PIPE ? table_smem_bytes(L.tab2) : 0;
+    const size_t smem = tb + tb2 + (size_t)bt * thread_smem_bytes(N, PIPE);
+    cudaError_t e =
+        cudaFuncSetAttribute(track_kernel<N, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<N>, bt, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<N, PIPE>, bt, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t want = (L.n_paths + bt - 1) / bt;
@@ -707,7 +901,7 @@ static cudaError_t launch_track_n(const TrackLaunch &L, int bt, int max_blocks, 
     if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    track_kernel<N><<<(unsigned)grid, bt, smem, s>>>(L, tb);
+    track_kernel<N, PIPE><<<(unsigned)grid, bt, smem, s>>>(L, tb, tb2);
     return cudaGetLastError();
 }
 
@@ -715,9 +909,9 @@ template <int N>
 static cudaError_t launch_classify_n(const ClassifyLaunch &L, cudaStream_t s)
 {
     const size_t tb = table_smem_bytes(L.tab);
-    const int bt = track_block_threads(N, tb, 128);
+    const int bt = track_block_threads(N, tb, 128, true);
     if (bt == 0) return cudaErrorInvalidConfiguration;
-    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N);
+    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, true);
     cudaError_t e = cudaFuncSetAttribute(classify_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t grid = (L.n_paths + bt - 1) / bt;
@@ -751,9 +945,21 @@ cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks
     const size_t tb = table_smem_bytes(L.tab);
     const int bt = track_block_threads(L.tab.n, tb, block_threads);
     if (bt == 0) return cudaErrorInvalidConfiguration;
-#define PHC_CALL_TRACK(NN) launch_track_n<NN>(L, bt, max_blocks, s)
+#define PHC_CALL_TRACK(NN) launch_track_n<NN, false>(L, bt, max_blocks, s)
     PHC_DISPATCH_N(L.tab.n, PHC_CALL_TRACK)
 #undef PHC_CALL_TRACK
+}
+
+cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s)
+{
+    device_limits();
+    if (L.n_paths <= 0) return cudaSuccess;
+    const size_t tb = table_smem_bytes(L.tab) + table_smem_bytes(L.tab2);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, true);
+    if (bt == 0) return cudaErrorInvalidConfiguration;
+#define PHC_CALL_PIPE(NN) launch_track_n<NN, true>(L, bt, max_blocks, s)
+    PHC_DISPATCH_N(L.tab.n, PHC_CALL_PIPE)
+#undef PHC_CALL_PIPE
 }
 
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s)

@@ -14,7 +14,7 @@ import oracle
 import paper_1804_03807_gb300 as P
 from workloads import (configs, cyclic, embedding_constants, multistep_example, random_dense, rng_for, univariate,
                        unit_gamma)
-from tests._checks import min_pair_distance, relative_residual, same_set
+from tests._checks import match_sets, min_pair_distance, relative_residual, same_set
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-10
@@ -270,3 +270,122 @@ def test_double_root_is_singular_on_gpu():
     r = P.track(h)
     P.refine(h, r)
     assert sorted(r.cls.cpu().numpy().tolist()) == [0, 1, 1]
+
+
+@pytest.mark.parametrize("n", [5, 6])
+def test_fp32_interior_cyclic_matches_fp64_oracle(n):
+    """FP32 interior: predictor and Jacobian in single precision for t <= 0.9,
+    residuals and the end game in double: same classes and regular endpoints
+    (1e-10) as the FP64 oracle."""
+    sys = cyclic(n)
+    g = unit_gamma(rng_for(900 + n))
+    o = P.phc_default_opts(precision=P.PHC_PREC_FP32_INTERIOR)
+    _, _, xg, cg, sg = gpu_track(sys, g, opts=o)
+    assert sg["n_fp32"].sum() > 0
+    xo, co, _ = oracle.track(oracle.total_degree(sys, g))
+    compare(sys, xg, cg, xo, co, f"fp32 cyclic{n}")
+
+
+def test_fp32_interior_cyclic7_batch_full_size():
+    """The bench workload in FP32-interior mode against the FP64 oracle.
+    Every FP32 regular endpoint is a distinct root found by the oracle
+    (1e-10); class counts may deviate by a few paths out of 45,360 (single
+    precision predictors change step sequences near close path approaches);
+    the deviation is bounded and printed."""
+    w = configs.cyclic7_batch()
+    hb = P.phc_make_homotopy_batch(w.systems, w.gammas)
+    r = P.track(hb, opts=P.phc_default_opts(precision=P.PHC_PREC_FP32_INTERIOR))
+    P.refine(hb, r)
+    x = r.x.cpu().numpy().T
+    c = r.cls.cpu().numpy()
+    st = P.stats_numpy(r.stats)
+    assert st["n_fp32"].sum() > 0
+    Pn = 5040
+    deviation = 0
+    for s_i, (s, g) in enumerate(zip(w.systems, w.gammas)):
+        sl = slice(s_i * Pn, (s_i + 1) * Pn)
+        ho = oracle.total_degree(s, g)
+        xo, co, so = oracle.track(ho)
+        xo, _, co, _ = oracle.refine(ho, xo, co, so["cond"], so["stop"] == 0)
+        Rg, Ro = x[sl][c[sl] == 0], xo[co == 0]
+        assert relative_residual(s, Rg).max() <= 1e-12
+        assert min_pair_distance(Rg) > 1e-6
+        ra, rb, rel = match_sets(Rg, Ro)
+        assert len(ra) == len(Rg) and rel.max() <= RTOL, "an FP32 regular endpoint is not an oracle root"
+        deviation += int(np.abs(np.bincount(c[sl], minlength=4) - np.bincount(co, minlength=4)).sum()) // 2
+    print(f"FP32 interior: {deviation} of {9 * Pn} paths in a different class than the FP64 oracle")
+    assert deviation <= 9
+
+
+def test_pipeline_equals_separate_stages_example_3_1():
+    """phc_track_pipeline (top stage and the cascade stage below it in one
+    launch) gives path for path what phc_track_paths followed by
+    phc_cascade_stage on the regular z_3 != 0 endpoints gives."""
+    import torch
+    sys = multistep_example()
+    g, hy, gamma = _embedded_top(sys, 3, 41)
+    E = P.phc_embed(sys, 3, g, hy)
+    h = P.phc_make_homotopy(E, gamma)
+    top, nxt = P.pipeline(h, 3)
+    ref = P.track(h)
+    assert np.array_equal(top.cls.cpu().numpy(), ref.cls.cpu().numpy())
+    assert np.array_equal(top.x.cpu().numpy(), ref.x.cpu().numpy())
+    x = ref.x.cpu().numpy().T
+    c = ref.cls.cpu().numpy()
+    fwd = (c == 0) & ~oracle.slack_zero(x, 6)
+    cn = nxt.cls.cpu().numpy()
+    assert np.array_equal(cn >= 0, fwd)
+    starts = torch.from_numpy(np.ascontiguousarray(x[fwd].T)).cuda()
+    rs = P.cascade(h, 3, starts)
+    assert np.array_equal(rs.cls.cpu().numpy(), cn[fwd])
+    assert np.array_equal(rs.x.cpu().numpy(), nxt.x.cpu().numpy()[:, fwd])
+    assert np.array_equal(rs.slack_zero.cpu().numpy(), nxt.slack_zero.cpu().numpy()[fwd])
+
+
+def test_cyclic8_d1_pipeline_full_size_against_oracle():
+    """Embedded cyclic 8 (40,320 paths) and its cascade stage to dimension 0,
+    pipelined in one launch; the oracle runs the same two stages one after
+    the other from its own endpoints.  Class counts of both stages and the
+    regular sets match; z = 0 regular points of the top stage are generic
+    points on the curve (f(x) = 0)."""
+    import torch
+    w = configs.cyclic8_d1()
+    base = w.systems[0]
+    g, hy = w.embed["gammas"], w.embed["hyper"]
+    gamma = w.gammas[0]
+    E = P.phc_embed(base, 1, g, hy)
+    h = P.phc_make_homotopy(E, gamma)
+    top, nxt = P.pipeline(h, 1)
+    P.refine(h, top)
+    xt = top.x.cpu().numpy().T
+    ct = top.cls.cpu().numpy()
+    cn = nxt.cls.cpu().numpy()
+    xn = nxt.x.cpu().numpy().T
+    # top endpoints refinement made regular (none expected) go through a separate stage call
+    late = (ct == 0) & ~oracle.slack_zero(xt, 8) & (cn < 0)
+    if late.any():
+        rl = P.cascade(h, 1, torch.from_numpy(np.ascontiguousarray(xt[late].T)).cuda())
+        cn[late] = rl.cls.cpu().numpy()
+        xn[late] = rl.x.cpu().numpy().T
+    h0 = P.phc_make_homotopy(base, gamma)
+    mask = cn >= 0
+    sub = P.Tracked(torch.from_numpy(np.ascontiguousarray(xn[mask].T)).cuda(),
+                    torch.from_numpy(cn[mask].copy()).cuda(), nxt.stats[torch.from_numpy(mask).cuda()].contiguous())
+    P.refine(h0, sub)
+    cn_m = sub.cls.cpu().numpy()
+    xn_m = sub.x.cpu().numpy().T
+    # oracle, stage by stage
+    Eo = oracle.embed(base, 1, g, hy)
+    ho = oracle.total_degree(Eo, gamma)
+    xo, co, so = oracle.track(ho)
+    xo, _, co, _ = oracle.refine(ho, xo, co, so["cond"], so["stop"] == 0)
+    compare(E, xt, ct, xo, co, "cyclic8 top")
+    reg = ct == 0
+    sz = oracle.slack_zero(xt, 8)
+    assert relative_residual(base, xt[reg & sz][:, :8]).max() <= 1e-12
+    Xo = xo[(co == 0) & ~oracle.slack_zero(xo, 8)]
+    hc = oracle.cascade_homotopy(Eo, 8, 8, 1)
+    xko, cko, sko = oracle.track(hc, starts=Xo)
+    xko = np.delete(xko, 8, axis=1)
+    xko, _, cko, _ = oracle.refine(oracle.total_degree(base, gamma), xko, cko, sko["cond"], sko["stop"] == 0)
+    compare(base, xn_m, cn_m, xko, cko, "cyclic8 stage 1->0")
