@@ -212,6 +212,21 @@ int phc_cascade_stage(const phc_homotopy *embedded_k, int k, const phc_cd *start
                       const phc_opts *opts, phc_cd *x_out, int8_t *cls_out, uint8_t *slack_zero_out,
                       phc_path_stats *stats_out, void *cuda_stream);
 
+/* Track every path of n_h homotopies of different systems together (the
+ * batching of many small problems: the paper's work crew over the paths of
+ * many systems, Section 1).  Systems with the same number of unknowns share
+ * one launch: each warp works on one system at a time with that system's
+ * tables in its own shared memory, its lanes refill from the system's path
+ * queue, and a warp whose lanes are all idle moves on to a system with
+ * unclaimed paths.  hs: host array of n_h single-system handles; x_out,
+ * cls_out, stats_out: host arrays of n_h device pointers, each as the
+ * corresponding argument of phc_track_paths for that handle (stats_out or
+ * any of its entries may be NULL).  The results equal n_h phc_track_paths
+ * calls.  Errors: PHC_EINVAL for NULL or batch handles and NULL outputs,
+ * PHC_ENOMEM, PHC_ECUDA. */
+int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
+                   int8_t *const *cls_out, phc_path_stats *const *stats_out, void *cuda_stream);
+
 /* The top stage and the cascade stage below it in one launch (Section 3.1,
  * Figure 3; the GPU counterpart of the paper's pipelining, Section 2.2).
  * Tracks paths first_path .. first_path + n_paths - 1 of the total-degree

@@ -16,14 +16,15 @@ from ._lib import (PHC_AT_INFINITY, PHC_FAILED, PHC_MAX_VARS, PHC_PREC_FP32_INTE
                    load, phc_cascade_stage, phc_default_opts, phc_embed, phc_last_error, phc_make_homotopy,
                    phc_make_homotopy_batch,
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
-                   phc_track_paths_noalloc, phc_track_pipeline)
+                   phc_track_many, phc_track_paths_noalloc, phc_track_pipeline)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
     "PHC_SINGULAR", "PHC_STOP_REACHED", "STATS_DTYPE", "Homotopy", "PhcError", "SystemLists", "load",
     "phc_cascade_stage", "phc_default_opts", "phc_embed", "phc_last_error", "phc_make_homotopy",
     "phc_make_homotopy_batch", "phc_num_paths",
-    "phc_opts", "phc_refine_endpoints", "phc_track_paths", "phc_track_paths_noalloc", "phc_track_pipeline",
+    "phc_opts", "phc_refine_endpoints", "phc_track_many", "phc_track_paths", "phc_track_paths_noalloc",
+    "phc_track_pipeline", "track_many",
     "Tracked", "pipeline", "track", "cascade", "refine",
     "stats_numpy",
 ]
@@ -71,6 +72,13 @@ def cascade(h_k: Homotopy, k: int, starts, opts=None, stream=None) -> Tracked:
     sz = torch.empty(n, dtype=torch.uint8, device=starts.device)
     phc_cascade_stage(h_k, k, starts.contiguous(), n, opts, x, cls, sz, st, stream)
     return Tracked(x, cls, st, sz)
+
+
+def track_many(hs, opts=None, stream=None, device="cuda"):
+    """Every path of every handle in hs (different systems), into new tensors."""
+    outs = [_alloc(h.n, phc_num_paths(h), device) for h in hs]
+    phc_track_many(hs, opts, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], stream)
+    return [Tracked(*o) for o in outs]
 
 
 def pipeline(h_k: Homotopy, k: int, first: int = 0, n_paths: int | None = None, opts=None, stream=None,

@@ -26,6 +26,7 @@ EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
     "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch", "phc_track_pipeline",
+    "phc_track_many",
 ]
 
 
@@ -90,6 +91,7 @@ def load() -> ctypes.CDLL:
     L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_cascade_stage.argtypes = [vp, i32, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
+    L.phc_track_many.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_track_pipeline.argtypes = [vp, i32, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp, vp, vp, vp]
     L.phc_refine_endpoints.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]
     L.phc_last_error.restype = ctypes.c_char_p
@@ -99,7 +101,7 @@ def load() -> ctypes.CDLL:
     L.phc_free_lists.restype = None
     for name in ("phc_default_opts", "phc_make_homotopy", "phc_make_homotopy_batch", "phc_num_paths",
                  "phc_track_paths",
-                 "phc_track_paths_noalloc", "phc_track_pipeline", "phc_embed",
+                 "phc_track_paths_noalloc", "phc_track_pipeline", "phc_track_many", "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
@@ -238,6 +240,17 @@ def phc_cascade_stage(h: Homotopy, k: int, starts, n_starts: int, opts, x_out, c
     _check(load().phc_cascade_stage(ctypes.c_void_p(h.ptr), int(k), _ptr(starts), int(n_starts),
                                     ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
                                     _ptr(slack_zero_out), _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_track_many(hs, opts, x_outs, cls_outs, stats_outs=None, stream=None):
+    """Track every path of the handles hs in one launch per number of unknowns."""
+    n = len(hs)
+    H = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in x_outs])
+    C = (ctypes.c_void_p * n)(*[_ptr(c) for c in cls_outs])
+    S = None if stats_outs is None else (ctypes.c_void_p * n)(*[_ptr(t) for t in stats_outs])
+    _check(load().phc_track_many(H, n, ctypes.byref(opts) if opts is not None else None, X, C, S,
+                                 _stream_ptr(stream)))
 
 
 def phc_track_pipeline(h: Homotopy, k: int, first_path: int, n_paths: int, opts, x_top, cls_top, stats_top, x_next,

@@ -513,6 +513,76 @@ extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *st
     return PHC_OK;
 }
 
+extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
+                              int8_t *const *cls_out, phc_path_stats *const *stats_out, void *stream)
+{
+    if (n_h < 0 || (n_h > 0 && (!hs || !x_out || !cls_out))) return fail(PHC_EINVAL, "NULL argument");
+    if (n_h == 0) return PHC_OK;
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    for (int i = 0; i < n_h; i++) {
+        if (!hs[i]) return fail(PHC_EINVAL, "handle %d is NULL", i);
+        if (hs[i]->n_sys != 1) return fail(PHC_EUNSUPPORTED, "handle %d is a batch handle", i);
+        if (!x_out[i] || !cls_out[i]) return fail(PHC_EINVAL, "NULL output array of handle %d", i);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int n = 1; n <= PHC_MAX_VARS; n++) {
+        std::vector<phc::SysDesc> descs;
+        std::vector<int64_t> prefix(1, 0);
+        int wtb = 0;
+        for (int i = 0; i < n_h; i++) {
+            phc_homotopy *h = hs[i];
+            if (h->n != n || h->num_paths == 0) continue;
+            phc::SysDesc d{};
+            d.tab = h->total.view;
+            d.deg = h->d_deg;
+            d.root_off = h->d_root_off;
+            d.roots = h->d_roots;
+            d.n_paths = h->num_paths;
+            d.x_out = reinterpret_cast<double2 *>(x_out[i]);
+            d.cls_out = cls_out[i];
+            phc_path_stats *sp = stats_out ? stats_out[i] : nullptr;
+            if (!sp) {
+                rc = ensure_stats(h, h->num_paths);
+                if (rc) return rc;
+                sp = h->d_stats;
+            }
+            d.stats = sp;
+            descs.push_back(d);
+            prefix.push_back(prefix.back() + h->num_paths);
+            const int b = (int)phc::warp_table_bytes(h->total.view.n_terms, h->total.view.n_ve);
+            if (b > wtb) wtb = b;
+        }
+        if (descs.empty()) continue;
+        const int m = (int)descs.size();
+        const size_t bytes = m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long) + (m + 1) * sizeof(int64_t);
+        void *blob = nullptr;
+        CU(cudaMallocAsync(&blob, bytes, st));
+        char *b = static_cast<char *>(blob);
+        phc::SysDesc *d_desc = reinterpret_cast<phc::SysDesc *>(b);
+        unsigned long long *d_q = reinterpret_cast<unsigned long long *>(b + m * sizeof(phc::SysDesc));
+        int64_t *d_pre = reinterpret_cast<int64_t *>(b + m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long));
+        CU(cudaMemcpyAsync(d_desc, descs.data(), m * sizeof(phc::SysDesc), cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(d_q, 0, m * sizeof(unsigned long long), st));
+        CU(cudaMemcpyAsync(d_pre, prefix.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        phc::TrackLaunch L{};
+        L.n_paths = prefix.back();
+        L.o = o;
+        L.multi = d_desc;
+        L.multi_q = d_q;
+        L.multi_prefix = d_pre;
+        L.n_multi = m;
+        L.warp_table_bytes = wtb;
+        cudaError_t e = phc::launch_multi(L, n, o.block_threads, o.max_blocks, st);
+        cudaFreeAsync(blob, st);
+        if (e != cudaSuccess) return fail(PHC_ECUDA, "multi-system kernel launch (n = %d): %s", n,
+                                          cudaGetErrorString(e));
+    }
+    return PHC_OK;
+}
+
 static int ensure_stats2(phc_homotopy *h, int64_t n)
 {
     if (h->stats2_cap >= n) return PHC_OK;

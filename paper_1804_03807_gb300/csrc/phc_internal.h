@@ -73,6 +73,19 @@ inline size_t thread_smem_bytes(int n, bool scale = false)
     return (size_t)(n * n + 4 * n + (scale ? n : 0)) * sizeof(double2);
 }
 
+// One system of a multi-system launch (systems of different structure and
+// equal number of unknowns tracked in one kernel).
+struct SysDesc {
+    DevTables tab;
+    const int32_t *deg;
+    const int32_t *root_off;
+    const double2 *roots;
+    int64_t n_paths;
+    double2 *x_out;           // SoA [n][n_paths]
+    int8_t *cls_out;          // [n_paths]
+    phc_path_stats *stats;    // [n_paths]
+};
+
 struct TrackLaunch {
     DevTables tab;
     // starts: mode 0 = total-degree roots of unity, mode 1 = explicit SoA
@@ -97,7 +110,22 @@ struct TrackLaunch {
     uint8_t *slack_zero2;     // [n_paths]
     phc_path_stats *stats2;   // [n_paths]
     int has_next_slack;       // the stage's endpoints keep a slack z_{k-1}
+    // multi-system launch: every warp tracks one system at a time
+    const SysDesc *multi;     // [n_multi]
+    unsigned long long *multi_q;   // [n_multi] path counters
+    const int64_t *multi_prefix;   // [n_multi + 1] prefix sums of path counts
+    int n_multi;
+    int warp_table_bytes;     // shared memory per warp for one system's table
 };
+
+// Bytes of shared memory one warp needs for a table of T terms and V
+// exponent entries (single system, 16-byte aligned).
+__host__ __device__ inline size_t warp_table_bytes(int T, int V)
+{
+    size_t b = (size_t)T * sizeof(TermRec) + 2 * (size_t)V;
+    b = (b + 15) & ~(size_t)15;
+    return b + (size_t)T * COEF_BYTES;
+}
 
 struct ClassifyLaunch {
     DevTables tab;
@@ -125,6 +153,7 @@ cudaError_t launch_roots(const int32_t *deg, const int32_t *root_off, double2 *r
                          cudaStream_t s);
 cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
+cudaError_t launch_multi(const TrackLaunch &L, int n, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,

@@ -1,0 +1,20 @@
+// track_pipe.cu -- launcher of the pipelined tracker (top stage and cascade
+// stage in one launch); a translation unit of its own so it compiles in
+// parallel with the other modes.
+#include "track_impl.cuh"
+
+namespace phc {
+
+cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s)
+{
+    device_limits();
+    if (L.n_paths <= 0) return cudaSuccess;
+    const size_t tb = table_smem_bytes(L.tab) + table_smem_bytes(L.tab2);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, true);
+    if (bt == 0) return cudaErrorInvalidConfiguration;
+#define PHC_CALL_PIPE(NN) launch_track_n<NN, MODE_PIPE>(L, bt, max_blocks, L.n_paths, s)
+    PHC_DISPATCH_N(L.tab.n, PHC_CALL_PIPE)
+#undef PHC_CALL_PIPE
+}
+
+}  // namespace phc

@@ -389,3 +389,48 @@ def test_cyclic8_d1_pipeline_full_size_against_oracle():
     xko = np.delete(xko, 8, axis=1)
     xko, _, cko, _ = oracle.refine(oracle.total_degree(base, gamma), xko, cko, sko["cond"], sko["stop"] == 0)
     compare(base, xn_m, cn_m, xko, cko, "cyclic8 stage 1->0")
+
+
+def test_track_many_equals_separate_calls_and_oracle():
+    """Twelve random sparse systems of different size in one call (one
+    launch per number of unknowns): path for path the results of separate
+    phc_track_paths calls, and the oracle's classes and regular sets."""
+    w = configs.sparse_batch(count=12, seed=1001, bezout_range=(100, 3000))
+    hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
+    rs = P.track_many(hs)
+    for i, (h, s, g) in enumerate(zip(hs, w.systems, w.gammas)):
+        ref = P.track(h)
+        assert np.array_equal(rs[i].cls.cpu().numpy(), ref.cls.cpu().numpy()), s.name
+        assert np.array_equal(rs[i].x.cpu().numpy(), ref.x.cpu().numpy()), s.name
+        if i < 4:
+            xo, co, _ = oracle.track(oracle.total_degree(s, g))
+            compare(s, rs[i].x.cpu().numpy().T, rs[i].cls.cpu().numpy(), xo, co, s.name)
+
+
+def test_sparse_batch_full_size_sampled():
+    """The batching workload: 256 random sparse systems (4.3 million paths)
+    in one call; 12 seeded paths per system re-tracked by the oracle."""
+    w = configs.sparse_batch()
+    hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
+    rs = P.track_many(hs)
+    rng = rng_for(1100)
+    agree = total = reg_ok = reg_total = 0
+    for h, s, g, r in zip(hs, w.systems, w.gammas, rs):
+        n = P.phc_num_paths(h)
+        idx = rng.choice(n, size=min(12, n), replace=False)
+        ho = oracle.total_degree(s, g)
+        xg = r.x.cpu().numpy().T
+        cg = r.cls.cpu().numpy()
+        for p in idx:
+            xo, co, _ = oracle.track(ho, first=int(p), n_paths=1, threads=1)
+            total += 1
+            agree += int(cg[p] == co[0])
+            if cg[p] == 0 and co[0] == 0:
+                reg_total += 1
+                d = np.max(np.abs(xg[p] - xo[0])) / (1 + np.max(np.abs(xo[0])))
+                reg_ok += int(d <= RTOL)
+        reg = cg == 0
+        if reg.any():
+            assert relative_residual(s, xg[reg]).max() <= 1e-12
+    assert agree / total >= 0.995, (agree, total)
+    assert reg_ok / max(reg_total, 1) >= 0.99, (reg_ok, reg_total)
