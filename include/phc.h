@@ -54,7 +54,7 @@ enum { PHC_REGULAR = 0, PHC_SINGULAR = 1, PHC_AT_INFINITY = 2, PHC_FAILED = 3 };
 
 /* Why tracking stopped (phc_path_stats.stop). */
 enum { PHC_STOP_REACHED = 0, PHC_STOP_DIVERGED = 1, PHC_STOP_STEP_MIN = 2, PHC_STOP_BUDGET = 3,
-       PHC_STOP_NONFINITE = 4 };
+       PHC_STOP_NONFINITE = 4, PHC_STOP_SKIPPED = 5 /* not a start of this stage (phc_cascade_from) */ };
 
 /* Arithmetic of the tracker.  FP32_INTERIOR runs the predictor stages
  * (H_t, Jacobian, factorization, solve) in single precision and factors the
@@ -76,7 +76,8 @@ enum { PHC_PREC_FP64 = 0, PHC_PREC_FP32_INTERIOR = 1 };
  *               fails to shrink by corr_contract or none converges
  *   step        clamped to land on t = 1; times `expand` (<= h_max) after
  *               expand_after accepted steps in a row; times `shrink` after
- *               a rejection; h < h_min or max_steps steps stall the path
+ *               a rejection; h < h_min, max_steps steps, or max_steps_decade
+ *               steps without 1-t crossing a power of ten stall the path
  *   end         a path that reaches t = 1 gets <= end_iters Newton steps at
  *               t = 1 (stop at ||dx|| <= end_tol (1 + ||x||))
  *   classes     norms are max_j max(|Re x_j|, |Im x_j|).
@@ -102,6 +103,7 @@ typedef struct {
     int32_t max_corr_iters;
     double corr_tol, corr_contract;
     int32_t max_steps;
+    int32_t max_steps_decade;
     double diverge_norm, endpoint_inf_norm, end_zone, growth_inf;
     int32_t end_iters;
     double end_tol;
@@ -211,6 +213,22 @@ int phc_embed(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *e
 int phc_cascade_stage(const phc_homotopy *embedded_k, int k, const phc_cd *starts, int64_t n_starts,
                       const phc_opts *opts, phc_cd *x_out, int8_t *cls_out, uint8_t *slack_zero_out,
                       phc_path_stats *stats_out, void *cuda_stream);
+
+/* phc_cascade_stage fed directly by the previous stage's device outputs:
+ * x_prev SoA [n_var(E_k)][n] with cls_prev [n] and slack_zero_prev [n] (the
+ * outputs of phc_track_paths / phc_cascade_stage / phc_track_pipeline for
+ * E_k); the stage tracks exactly the entries that start the next stage in
+ * Section 3.1 -- regular endpoints whose slack z_k is not zero (cls_prev ==
+ * PHC_REGULAR and slack_zero_prev == 0; slack_zero_prev NULL tests
+ * |z_k| <= slack_tol (1 + ||x||) on x_prev) -- without compacting them, so a
+ * chain of stages runs on one stream with no host round trip.  Outputs are
+ * indexed like the inputs: x_out SoA [n_var(E_k) - 1][n], cls_out [n] (-1
+ * for entries that were not starts), slack_zero_out [n], stats_out [n] or
+ * NULL (stop = PHC_STOP_SKIPPED for entries that were not starts).
+ * Errors: as phc_cascade_stage. */
+int phc_cascade_from(const phc_homotopy *embedded_k, int k, const phc_cd *x_prev, const int8_t *cls_prev,
+                     const uint8_t *slack_zero_prev, int64_t n, const phc_opts *opts, phc_cd *x_out, int8_t *cls_out,
+                     uint8_t *slack_zero_out, phc_path_stats *stats_out, void *cuda_stream);
 
 /* Track every path of n_h homotopies of different systems together (the
  * batching of many small problems: the paper's work crew over the paths of

@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
         ("h_init", ctypes.c_double), ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
         ("expand_after", ctypes.c_int32), ("expand", ctypes.c_double), ("shrink", ctypes.c_double),
         ("max_corr_iters", ctypes.c_int32), ("corr_tol", ctypes.c_double), ("corr_contract", ctypes.c_double),
-        ("max_steps", ctypes.c_int32), ("diverge_norm", ctypes.c_double), ("endpoint_inf_norm", ctypes.c_double),
+        ("max_steps", ctypes.c_int32), ("max_steps_decade", ctypes.c_int32), ("diverge_norm", ctypes.c_double), ("endpoint_inf_norm", ctypes.c_double),
         ("end_zone", ctypes.c_double), ("growth_inf", ctypes.c_double), ("end_iters", ctypes.c_int32), ("end_tol", ctypes.c_double),
         ("cond_regular", ctypes.c_double), ("res_regular", ctypes.c_double), ("slack_tol", ctypes.c_double),
     ]

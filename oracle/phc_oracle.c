@@ -59,6 +59,7 @@ typedef struct {
     double corr_tol;        /* converged: ||dx|| <= corr_tol (1 + ||x||)    */
     double corr_contract;   /* rejected: ||dx_j|| > corr_contract ||dx_j-1|| */
     int32_t max_steps;      /* accepted + rejected steps per path           */
+    int32_t max_steps_decade; /* steps without crossing a decade of 1-t: stalled */
     double diverge_norm;    /* ||x|| above this during tracking: at infinity */
     double endpoint_inf_norm; /* endpoint with ||x|| above this: at infinity  */
     double end_zone;        /* stalled before this t: failed                 */
@@ -83,6 +84,7 @@ void orc_default_opts(orc_opts *o)
     o->corr_tol = 1e-9;
     o->corr_contract = 0.5;
     o->max_steps = 20000;
+    o->max_steps_decade = 300;
     o->diverge_norm = 1e6;
     o->endpoint_inf_norm = 1e4;
     o->end_zone = 0.9;
@@ -396,8 +398,9 @@ static void end_measures(const orc_homotopy *h, const cplx *x, double *cond, dou
  * Step control: the step is clamped to land on t = 1; after expand_after
  *   consecutive accepts it grows by `expand` (at most h_max), a rejection
  *   multiplies it by `shrink`.
- * Stop: t = 1; ||x|| > diverge_norm (at infinity); h < h_min or max_steps
- *   (stalled); non-finite values (failed).
+ * Stop: t = 1; ||x|| > diverge_norm (at infinity); h < h_min, max_steps, or
+ *   max_steps_decade steps without 1-t crossing a power of ten (stalled);
+ *   non-finite values (failed).
  * End (only for paths that reached t = 1): Newton at t = 1 (<= end_iters),
  *   then the condition number and the relative residual; REGULAR when both
  *   are small.
@@ -417,6 +420,7 @@ static void track_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_sta
     double ck[5];
     int nck = 0;
     double next_s = 0.1;
+    int since_ck = 0; /* steps since the last decade checkpoint (or the start) */
     memset(st, 0, sizeof *st);
     st->stop = 0;
 
@@ -456,6 +460,7 @@ static void track_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_sta
             while (1.0 - t <= next_s && next_s > 0.0) {
                 ck[nck % 5] = vnorm(n, x);
                 nck++;
+                since_ck = 0;
                 next_s *= 0.1;
                 if (nck >= 40) next_s = 0.0;
             }
@@ -473,6 +478,7 @@ static void track_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_sta
             if (step < o->h_min) { st->stop = 2; break; }
         }
         if (steps >= o->max_steps) { st->stop = 3; break; }
+        if (++since_ck >= o->max_steps_decade && t < 1.0) { st->stop = 3; break; }
     }
     st->t = t;
     st->h = step;

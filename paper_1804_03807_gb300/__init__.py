@@ -11,7 +11,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from ._lib import (PHC_AT_INFINITY, PHC_FAILED, PHC_MAX_VARS, PHC_PREC_FP32_INTERIOR, PHC_PREC_FP64,
+from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAILED, PHC_MAX_VARS, PHC_PREC_FP32_INTERIOR, PHC_PREC_FP64,
                    PHC_REGULAR, PHC_SINGULAR, PHC_STOP_REACHED, STATS_DTYPE, Homotopy, PhcError, SystemLists,
                    load, phc_cascade_stage, phc_default_opts, phc_embed, phc_last_error, phc_make_homotopy,
                    phc_make_homotopy_batch,
@@ -24,7 +24,7 @@ __all__ = [
     "phc_cascade_stage", "phc_default_opts", "phc_embed", "phc_last_error", "phc_make_homotopy",
     "phc_make_homotopy_batch", "phc_num_paths",
     "phc_opts", "phc_refine_endpoints", "phc_track_many", "phc_track_paths", "phc_track_paths_noalloc",
-    "phc_track_pipeline", "track_many",
+    "phc_track_pipeline", "track_many", "phc_cascade_from", "PHC_STOP_SKIPPED", "cascade_from",
     "Tracked", "pipeline", "track", "cascade", "refine",
     "stats_numpy",
 ]
@@ -71,6 +71,17 @@ def cascade(h_k: Homotopy, k: int, starts, opts=None, stream=None) -> Tracked:
     x, cls, st = _alloc(h_k.n - 1, n, starts.device)
     sz = torch.empty(n, dtype=torch.uint8, device=starts.device)
     phc_cascade_stage(h_k, k, starts.contiguous(), n, opts, x, cls, sz, st, stream)
+    return Tracked(x, cls, st, sz)
+
+
+def cascade_from(h_k: Homotopy, k: int, prev: Tracked, opts=None, stream=None) -> Tracked:
+    """The cascade stage from E_k fed by the previous stage's outputs (prev.x
+    in E_k's unknowns); outputs indexed like prev (cls -1 where no start)."""
+    import torch
+    n = int(prev.x.shape[1])
+    x, cls, st = _alloc(h_k.n - 1, n, prev.x.device)
+    sz = torch.empty(n, dtype=torch.uint8, device=prev.x.device)
+    phc_cascade_from(h_k, k, prev.x, prev.cls, prev.slack_zero, n, opts, x, cls, sz, st, stream)
     return Tracked(x, cls, st, sz)
 
 

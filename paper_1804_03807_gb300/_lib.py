@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libphc.so")
 PHC_OK, PHC_EINVAL, PHC_ENOMEM, PHC_ECUDA, PHC_ETIMEOUT, PHC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 PHC_REGULAR, PHC_SINGULAR, PHC_AT_INFINITY, PHC_FAILED = 0, 1, 2, 3
 PHC_STOP_REACHED, PHC_STOP_DIVERGED, PHC_STOP_STEP_MIN, PHC_STOP_BUDGET, PHC_STOP_NONFINITE = 0, 1, 2, 3, 4
+PHC_STOP_SKIPPED = 5
 PHC_PREC_FP64, PHC_PREC_FP32_INTERIOR = 0, 1
 PHC_MAX_VARS = 12
 PHC_NOALLOC_MAX_PATHS = 52428
@@ -26,7 +27,7 @@ EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
     "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch", "phc_track_pipeline",
-    "phc_track_many",
+    "phc_track_many", "phc_cascade_from",
 ]
 
 
@@ -45,7 +46,7 @@ class phc_opts(ctypes.Structure):
         ("h_init", ctypes.c_double), ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
         ("expand_after", ctypes.c_int32), ("expand", ctypes.c_double), ("shrink", ctypes.c_double),
         ("max_corr_iters", ctypes.c_int32), ("corr_tol", ctypes.c_double), ("corr_contract", ctypes.c_double),
-        ("max_steps", ctypes.c_int32),
+        ("max_steps", ctypes.c_int32), ("max_steps_decade", ctypes.c_int32),
         ("diverge_norm", ctypes.c_double), ("endpoint_inf_norm", ctypes.c_double), ("end_zone", ctypes.c_double),
         ("growth_inf", ctypes.c_double),
         ("end_iters", ctypes.c_int32), ("end_tol", ctypes.c_double),
@@ -91,6 +92,7 @@ def load() -> ctypes.CDLL:
     L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_cascade_stage.argtypes = [vp, i32, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
+    L.phc_cascade_from.argtypes = [vp, i32, vp, vp, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
     L.phc_track_many.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_track_pipeline.argtypes = [vp, i32, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp, vp, vp, vp]
     L.phc_refine_endpoints.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]
@@ -101,7 +103,8 @@ def load() -> ctypes.CDLL:
     L.phc_free_lists.restype = None
     for name in ("phc_default_opts", "phc_make_homotopy", "phc_make_homotopy_batch", "phc_num_paths",
                  "phc_track_paths",
-                 "phc_track_paths_noalloc", "phc_track_pipeline", "phc_track_many", "phc_embed",
+                 "phc_track_paths_noalloc", "phc_track_pipeline", "phc_track_many", "phc_cascade_from",
+                 "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
@@ -240,6 +243,14 @@ def phc_cascade_stage(h: Homotopy, k: int, starts, n_starts: int, opts, x_out, c
     _check(load().phc_cascade_stage(ctypes.c_void_p(h.ptr), int(k), _ptr(starts), int(n_starts),
                                     ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
                                     _ptr(slack_zero_out), _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_cascade_from(h: Homotopy, k: int, x_prev, cls_prev, slack_zero_prev, n: int, opts, x_out, cls_out,
+                     slack_zero_out, stats_out=None, stream=None):
+    _check(load().phc_cascade_from(ctypes.c_void_p(h.ptr), int(k), _ptr(x_prev), _ptr(cls_prev),
+                                   _ptr(slack_zero_prev), int(n), ctypes.byref(opts) if opts is not None else None,
+                                   _ptr(x_out), _ptr(cls_out), _ptr(slack_zero_out), _ptr(stats_out),
+                                   _stream_ptr(stream)))
 
 
 def phc_track_many(hs, opts, x_outs, cls_outs, stats_outs=None, stream=None):

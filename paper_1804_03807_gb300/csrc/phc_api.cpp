@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -54,6 +55,7 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->corr_tol = 1e-9;
     o->corr_contract = 0.5;
     o->max_steps = 20000;
+    o->max_steps_decade = 300;
     o->diverge_norm = 1e6;
     o->endpoint_inf_norm = 1e4;
     o->end_zone = 0.9;
@@ -79,7 +81,7 @@ static int check_opts(const phc_opts &o)
         return fail(PHC_EINVAL, "invalid step control (expand_after >= 1, expand >= 1, 0 < shrink < 1)");
     if (o.max_corr_iters < 1 || o.max_corr_iters > 64 || o.end_iters < 0 || o.end_iters > 64)
         return fail(PHC_EINVAL, "iteration counts out of range");
-    if (o.max_steps < 1) return fail(PHC_EINVAL, "max_steps must be positive");
+    if (o.max_steps < 1 || o.max_steps_decade < 1) return fail(PHC_EINVAL, "step budgets must be positive");
     if (!(o.growth_inf >= 1.0)) return fail(PHC_EINVAL, "growth_inf must be >= 1");
     if (o.precision != PHC_PREC_FP64 && o.precision != PHC_PREC_FP32_INTERIOR)
         return fail(PHC_EINVAL, "unknown precision %d", o.precision);
@@ -160,7 +162,9 @@ struct HostTerms {
     }
 };
 
-static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
+// Uploads go through a private non-blocking stream so that building a
+// homotopy never waits for (or blocks) work the caller runs on its streams.
+static int upload_table(const HostTerms &ht, int n, DeviceTable &out, cudaStream_t ps)
 {
     const size_t T = ht.recs.size(), V = ht.vars.size();
     const size_t C = ht.c0.size();  // T per system
@@ -193,9 +197,10 @@ static int upload_table(const HostTerms &ht, int n, DeviceTable &out)
     }
     void *blob = nullptr;
     if (cudaMalloc(&blob, bytes) != cudaSuccess) return fail(PHC_ENOMEM, "cudaMalloc of %zu table bytes", bytes);
-    if (cudaMemcpy(blob, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpyAsync(blob, host.data(), bytes, cudaMemcpyHostToDevice, ps) != cudaSuccess ||
+        cudaStreamSynchronize(ps) != cudaSuccess) {
         cudaFree(blob);
-        return fail(PHC_ECUDA, "cudaMemcpy of the term table");
+        return fail(PHC_ECUDA, "upload of the term table");
     }
     char *b = static_cast<char *>(blob);
     out.blob = blob;
@@ -308,8 +313,14 @@ extern "C" int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *tpe, 
             }
         }
     }
-    rc = upload_table(ht, n, h->total);
+    cudaStream_t ps = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return fail(PHC_ECUDA, "cudaStreamCreateWithFlags");
+    }
+    rc = upload_table(ht, n, h->total, ps);
     if (rc) {
+        cudaStreamDestroy(ps);
         delete h;
         return rc;
     }
@@ -324,16 +335,19 @@ extern "C" int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *tpe, 
         cudaMalloc(&h->d_root_off, n * sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&h->d_roots, total * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&h->d_qhead, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaStreamDestroy(ps);
         phc_destroy_homotopy(h);
         return fail(PHC_ENOMEM, "cudaMalloc of the start tables");
     }
-    cudaMemcpy(h->d_deg, deg.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(h->d_root_off, roff.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaError_t e = phc::launch_roots(h->d_deg, h->d_root_off, h->d_roots, n, total, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaError_t e = cudaMemcpyAsync(h->d_deg, deg.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_root_off, roff.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess) e = phc::launch_roots(h->d_deg, h->d_root_off, h->d_roots, n, total, ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    cudaStreamDestroy(ps);
     if (e != cudaSuccess) {
         phc_destroy_homotopy(h);
-        return fail(PHC_ECUDA, "roots of unity kernel: %s", cudaGetErrorString(e));
+        return fail(PHC_ECUDA, "start tables: %s", cudaGetErrorString(e));
     }
     *out = h;
     return PHC_OK;
@@ -400,7 +414,7 @@ static int ensure_xfull(phc_homotopy *h, int64_t elems)
 
 static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, const double2 *starts, int64_t first,
                      int64_t n, const phc_opts &o, double2 *x_out, int8_t *cls_out, phc_path_stats *stats,
-                     cudaStream_t s)
+                     cudaStream_t s, const int8_t *sel_cls = nullptr, const uint8_t *sel_sz = nullptr)
 {
     CU(cudaMemsetAsync(h->d_qhead, 0, sizeof(unsigned long long), s));
     phc::TrackLaunch L{};
@@ -410,6 +424,8 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.root_off = h->d_root_off;
     L.roots = h->d_roots;
     L.starts = starts;
+    L.sel_cls = sel_cls;
+    L.sel_sz = sel_sz;
     L.first = first;
     L.n_paths = n;
     L.paths_per_system = h->paths_per_system > 0 ? h->paths_per_system : 1;
@@ -476,7 +492,12 @@ static int ensure_cascade(phc_homotopy *h)
                 ht.add(i, a, n, make_double2(c.re, c.im), make_double2(0.0, 0.0));
         }
     }
-    return upload_table(ht, n, h->cascade);
+    cudaStream_t ps = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(PHC_ECUDA, "cudaStreamCreateWithFlags");
+    const int rc = upload_table(ht, n, h->cascade, ps);
+    cudaStreamDestroy(ps);
+    return rc;
 }
 
 extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *starts, int64_t n, const phc_opts *opts,
@@ -528,6 +549,15 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
         if (!x_out[i] || !cls_out[i]) return fail(PHC_EINVAL, "NULL output array of handle %d", i);
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the launches of different sizes run side by side on helper streams
+    // that fork from and join back into the caller's stream
+    static std::mutex pool_mutex;
+    static std::vector<cudaStream_t> pool;
+    cudaEvent_t fork_ev = nullptr;
+    CU(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    CU(cudaEventRecord(fork_ev, st));
+    std::vector<cudaEvent_t> joins;
+    int used = 0;
     for (int n = 1; n <= PHC_MAX_VARS; n++) {
         std::vector<phc::SysDesc> descs;
         std::vector<int64_t> prefix(1, 0);
@@ -556,17 +586,30 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
             if (b > wtb) wtb = b;
         }
         if (descs.empty()) continue;
+        cudaStream_t hs_st;
+        {
+            std::lock_guard<std::mutex> lock(pool_mutex);
+            while ((int)pool.size() <= used) {
+                cudaStream_t ns;
+                CU(cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
+                pool.push_back(ns);
+            }
+            hs_st = pool[used++];
+        }
+        CU(cudaStreamWaitEvent(hs_st, fork_ev, 0));
         const int m = (int)descs.size();
         const size_t bytes = m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long) + (m + 1) * sizeof(int64_t);
         void *blob = nullptr;
-        CU(cudaMallocAsync(&blob, bytes, st));
+        CU(cudaMallocAsync(&blob, bytes, hs_st));
         char *b = static_cast<char *>(blob);
         phc::SysDesc *d_desc = reinterpret_cast<phc::SysDesc *>(b);
         unsigned long long *d_q = reinterpret_cast<unsigned long long *>(b + m * sizeof(phc::SysDesc));
         int64_t *d_pre = reinterpret_cast<int64_t *>(b + m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long));
-        CU(cudaMemcpyAsync(d_desc, descs.data(), m * sizeof(phc::SysDesc), cudaMemcpyHostToDevice, st));
-        CU(cudaMemsetAsync(d_q, 0, m * sizeof(unsigned long long), st));
-        CU(cudaMemcpyAsync(d_pre, prefix.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(d_desc, descs.data(), m * sizeof(phc::SysDesc), cudaMemcpyHostToDevice, hs_st));
+        CU(cudaMemsetAsync(d_q, 0, m * sizeof(unsigned long long), hs_st));
+        CU(cudaMemcpyAsync(d_pre, prefix.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, hs_st));
+        // the host vectors must outlive the copies from pageable memory
+        CU(cudaStreamSynchronize(hs_st));
         phc::TrackLaunch L{};
         L.n_paths = prefix.back();
         L.o = o;
@@ -575,11 +618,20 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
         L.multi_prefix = d_pre;
         L.n_multi = m;
         L.warp_table_bytes = wtb;
-        cudaError_t e = phc::launch_multi(L, n, o.block_threads, o.max_blocks, st);
-        cudaFreeAsync(blob, st);
+        cudaError_t e = phc::launch_multi(L, n, o.block_threads, o.max_blocks, hs_st);
+        cudaFreeAsync(blob, hs_st);
         if (e != cudaSuccess) return fail(PHC_ECUDA, "multi-system kernel launch (n = %d): %s", n,
                                           cudaGetErrorString(e));
+        cudaEvent_t j;
+        CU(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+        CU(cudaEventRecord(j, hs_st));
+        joins.push_back(j);
     }
+    for (cudaEvent_t j : joins) {
+        CU(cudaStreamWaitEvent(st, j, 0));
+        cudaEventDestroy(j);
+    }
+    cudaEventDestroy(fork_ev);
     return PHC_OK;
 }
 
@@ -649,6 +701,41 @@ extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t
     L.has_next_slack = k > 1 ? 1 : 0;
     cudaError_t e = phc::launch_pipeline(L, o.block_threads, o.max_blocks, s);
     if (e != cudaSuccess) return fail(PHC_ECUDA, "pipeline kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+extern "C" int phc_cascade_from(const phc_homotopy *hc, int k, const phc_cd *x_prev, const int8_t *cls_prev,
+                                const uint8_t *sz_prev, int64_t n, const phc_opts *opts, phc_cd *x_out,
+                                int8_t *cls_out, uint8_t *slack_zero_out, phc_path_stats *stats_out, void *stream)
+{
+    phc_homotopy *h = const_cast<phc_homotopy *>(hc);
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (k < 1 || k >= h->n) return fail(PHC_EINVAL, "cascade stage k = %d outside 1..%d", k, h->n - 1);
+    if (h->n_sys != 1) return fail(PHC_EUNSUPPORTED, "cascade stages need a single-system handle");
+    if (n < 0) return fail(PHC_EINVAL, "n < 0");
+    if (n == 0) return PHC_OK;
+    if (!x_prev || !cls_prev || !x_out || !cls_out || !slack_zero_out) return fail(PHC_EINVAL, "NULL array");
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    rc = ensure_cascade(h);
+    if (rc) return rc;
+    rc = ensure_xfull(h, (int64_t)h->n * n);
+    if (rc) return rc;
+    phc_path_stats *st = stats_out;
+    if (!st) {
+        rc = ensure_stats(h, n);
+        if (rc) return rc;
+        st = h->d_stats;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = run_track(h, h->cascade.view, 2, reinterpret_cast<const double2 *>(x_prev), 0, n, o, h->d_xfull, cls_out, st,
+                   s, cls_prev, sz_prev);
+    if (rc) return rc;
+    cudaError_t e = phc::launch_drop_last(h->d_xfull, h->n, n, reinterpret_cast<double2 *>(x_out), slack_zero_out,
+                                          k > 1 ? 1 : 0, o.slack_tol, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "drop kernel launch: %s", cudaGetErrorString(e));
     return PHC_OK;
 }
 

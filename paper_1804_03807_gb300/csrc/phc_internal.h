@@ -93,7 +93,9 @@ struct TrackLaunch {
     const int32_t *deg;       // [n]
     const int32_t *root_off;  // [n]
     const double2 *roots;     // [sum deg]
-    const double2 *starts;    // SoA [n][n_paths] (mode 1)
+    const double2 *starts;    // SoA [n][n_paths] (modes 1 and 2)
+    const int8_t *sel_cls;    // mode 2: track entry q only if sel_cls[q] is regular
+    const uint8_t *sel_sz;    //         and sel_sz[q] == 0 (NULL: test the last slack of starts)
     int64_t first;
     int64_t n_paths;
     int64_t paths_per_system; // global path p belongs to system p / paths_per_system

@@ -431,6 +431,7 @@ __device__ __forceinline__ int8_t classify_one(const SmTab &tb, const ThreadArra
     }
     int8_t cls = PHC_FAILED;
     double cond = NAN, relres = NAN;
+    if (s.stop == PHC_STOP_SKIPPED) return -1;
     if (fin && s.stop != PHC_STOP_DIVERGED) {
         const double2 *C0 = tb.c0 + (size_t)s.system * tb.n_terms, *C1 = tb.c1 + (size_t)s.system * tb.n_terms;
         evaluate<N, double2, true>(C0, C1, tb, 1.0, false, true, A.xe, A.R, A.J, A.P, A.S, bt);
@@ -558,6 +559,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
     double t = 0.0, h = 0.0, he = 0.0, t1 = 0.0, te = 0.0, prev = 0.0, next_s = 0.0, nx0 = 0.0;
     double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0;  // last five decade checkpoints, r4 newest
     int streak = 0, steps = 0, phase = 0, it = 0, nck = 0;
+    int since_ck = 0;  // steps since the last decade checkpoint (or the start)
     int n_acc = 0, n_rej = 0, n_newt = 0, n_solve = 0, n_f32 = 0;
     bool use32 = false, fp32_off = false;  // fp32_off: the path fell back to double for good
     bool fresh = false;                    // x0 holds a new start point
@@ -644,8 +646,27 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 }
             } else {
                 sys = 0;
+                double nx = 0.0;
 #pragma unroll
-                for (int i = 0; i < N; i++) x0[i] = L.starts[(int64_t)i * np + q];
+                for (int i = 0; i < N; i++) {
+                    x0[i] = L.starts[(int64_t)i * np + q];
+                    const double a = absinf(x0[i]);
+                    if (!(a <= nx)) nx = a;
+                }
+                if (L.start_mode == 2) {
+                    // a start of this stage: a regular endpoint with z_k != 0
+                    bool sel = L.sel_cls[q] == PHC_REGULAR;
+                    if (L.sel_sz) sel = sel && L.sel_sz[q] == 0;
+                    else sel = sel && absinf(x0[N - 1]) > o.slack_tol * (1.0 + nx);
+                    if (!sel) {
+                        phc_path_stats rec = {};
+                        rec.stop = PHC_STOP_SKIPPED;
+                        L.stats[q] = rec;
+                        for (int j = 0; j < N; j++) L.x_out[(int64_t)j * np + q] = make_double2(0.0, 0.0);
+                        q = -1;
+                        continue;
+                    }
+                }
             }
             if constexpr (PIPE) {
                 stage = 0;
@@ -667,6 +688,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             h = o.h_init;
             streak = steps = 0;
             nck = 0;
+            since_ck = 0;
             next_s = 0.1;
             r0 = r1 = r2 = r3 = r4 = 0.0;
             n_acc = n_rej = n_newt = n_solve = n_f32 = 0;
@@ -785,6 +807,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 r3 = r4;
                 r4 = nx;
                 nck++;
+                since_ck = 0;
                 next_s *= 0.1;
                 if (nck >= 40) next_s = 0.0;
             }
@@ -797,6 +820,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                     if (h > o.h_max) h = o.h_max;
                 }
                 if (steps >= o.max_steps) stop = PHC_STOP_BUDGET;
+                else if (++since_ck >= o.max_steps_decade && t < 1.0) stop = PHC_STOP_BUDGET;
                 else if (t >= 1.0) {
                     phase = 5;  // end Newton at t = 1 from x0 (already in xe)
                     it = 0;
@@ -819,6 +843,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 if (h < o.h_min) stop = PHC_STOP_STEP_MIN;
             }
             if (stop < 0 && steps >= o.max_steps) stop = PHC_STOP_BUDGET;
+            if (stop < 0 && ++since_ck >= o.max_steps_decade) stop = PHC_STOP_BUDGET;
             if (stop < 0) begin_step();
         }
         if (stop < 0) continue;
