@@ -237,7 +237,10 @@ def run_gpu(args):
     xlo = torch.empty_like(x)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     opts = P.phc_default_opts(precision=args.precision)
-    launches_per_step = 3  # track, classify, refine
+    if args.tail_drain is not None:
+        opts.tail_drain = args.tail_drain
+    tail_on = opts.tail_drain > 0 and args.precision == 0
+    launches_per_step = 4 if tail_on else 3  # track, (tail,) classify, refine
 
     def step(pair=None):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -279,6 +282,7 @@ def run_gpu(args):
     # roofline of track_kernel: algorithmic flops / duration of the tracking
     # call; units done in single precision count against the FP32 peak
     stn = P.stats_numpy(st)
+    tail_paths = P.phc_tail_paths(h, main)
     units = int(stn["n_solve"].sum())
     units32 = int(stn["n_fp32"].sum())
     f64 = (units - units32) * uf
@@ -288,7 +292,10 @@ def run_gpu(args):
     frac = (f64 / secs / 1e12) / FP64_PEAK_TFLOPS + (f32 / secs / 1e12) / FP32_PEAK_TFLOPS
     roofline = {"bound": "alu", "achieved": f64 / secs / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": frac, "traffic": args.traffic,
-                "kernel": "track_kernel<7> (+classify_kernel<7>, <0.1 %)", "fp64_flops_per_step": f64,
+                "kernel": ("track_kernel<7> + tail_kernel<7,8>" if tail_on else "track_kernel<7>") +
+                          " (+classify_kernel<7>, <0.1 %)",
+                "tail_paths_per_step": tail_paths, "tail_drain": opts.tail_drain if tail_on else 0.0,
+                "fp64_flops_per_step": f64,
                 "fp32_flops_per_step": f32, "fp32_peak": FP32_PEAK_TFLOPS, "units_per_step": units,
                 "fp32_units_per_step": units32, "kernel_ms": kern_ms,
                 "peak_source": "derived: 152 SMs x 2 FP64 (128 FP32) FMA/clk x 2 flops x 2.07 GHz",
@@ -331,6 +338,8 @@ def end_to_end(P, systems, gammas, dev, args):
     xh = torch.empty((systems[0].n_var, total), dtype=torch.complex128, pin_memory=True)
     ch = torch.empty(total, dtype=torch.int8, pin_memory=True)
     opts = P.phc_default_opts(precision=args.precision)
+    if args.tail_drain is not None:
+        opts.tail_drain = args.tail_drain
 
     def one():
         h = P.phc_make_homotopy_batch(systems, gammas)
@@ -398,11 +407,21 @@ def run_serving(args):
     return 0
 
 
-def profile_case():
-    """One random-coefficient cyclic 7 system (5040 paths), tracked twice."""
+def profile_case(which: str = "cyclic7"):
+    """A small case of a bench kernel, run twice: one random-coefficient
+    cyclic 7 system (5040 paths, track_kernel single mode) or 40 systems of
+    the sparse batch (track_kernel multi-system mode)."""
     import torch
     import paper_1804_03807_gb300 as P
     from workloads import configs
+    if which == "sparse":
+        w = configs.sparse_batch(count=40, seed=4)
+        hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
+        for _ in range(2):
+            rs = P.track_many(hs)
+            torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "sparse40", "paths": sum(P.phc_num_paths(h) for h in hs)}))
+        return 0
     w = configs.cyclic7_batch()
     h = P.phc_make_homotopy(w.systems[1], w.gammas[1])
     for _ in range(2):
@@ -423,15 +442,18 @@ def main(argv=None):
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per track launch, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=0, help="0 = FP64, 1 = FP32 interior")
+    ap.add_argument("--tail-drain", type=float, default=None,
+                    help="fraction of idle tracker threads that moves running paths to the tail kernel "
+                         "(default: the library's; 0 = off)")
     ap.add_argument("--workload", choices=["cyclic7_batch", "serving"], default="cyclic7_batch")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of Poisson requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: batches of requests on the GPU at once")
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the cyclic 9 request")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="track one system of the batch twice (a small case for ncu) and exit")
+    ap.add_argument("--profile-case", nargs="?", const="cyclic7", default=None, choices=["cyclic7", "sparse"],
+                    help="run a small case of a bench kernel twice (for ncu) and exit")
     args = ap.parse_args(argv)
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":

@@ -113,6 +113,12 @@ typedef struct {
     double fp32_pivot_ratio; /* FP32_INTERIOR: largest pivot spread accepted */
     int32_t block_threads;   /* threads per block; 0 = chosen by the library */
     int32_t max_blocks;      /* grid size cap; 0 = one wave of resident blocks */
+    double tail_drain;       /* FP64, phc_track_paths / phc_cascade_stage / phc_cascade_from: once
+                                this fraction of the tracker's threads has found no path left to
+                                claim, every path that starts a new step moves to a kernel that
+                                gives each path a group of threads (one per equation); the
+                                arithmetic is the same, operation for operation, so the results do
+                                not change.  0 = never. */
 } phc_opts;
 
 /* Per-path statistics (device array of these, optional). */
@@ -168,6 +174,13 @@ int phc_make_homotopy(int n_eq, int n_var, const int32_t *terms_per_eq, const ui
  * of a path names its system.  Errors as phc_make_homotopy. */
 int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps, int n_systems,
                             const phc_cd *coefs, const phc_cd *gammas, phc_homotopy **out);
+
+/* Paths that the last tracking call on h (phc_track_paths, phc_cascade_stage,
+ * phc_cascade_from) moved to the row-parallel tail kernel (opts.tail_drain);
+ * 0 when no such call ran or the option was 0.  Host call: waits for
+ * cuda_stream (the stream of that call) before reading the device counter.
+ * Errors: PHC_EINVAL for a NULL argument; PHC_ECUDA. */
+int phc_tail_paths(const phc_homotopy *h, void *cuda_stream, int64_t *out);
 
 /* Number of paths of the total-degree homotopy, prod d_i (host call); for a
  * batch handle, n_systems * prod d_i. */

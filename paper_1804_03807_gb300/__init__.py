@@ -16,7 +16,7 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    load, phc_cascade_stage, phc_default_opts, phc_embed, phc_last_error, phc_make_homotopy,
                    phc_make_homotopy_batch,
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
-                   phc_track_many, phc_track_paths_noalloc, phc_track_pipeline)
+                   phc_tail_paths, phc_track_many, phc_track_paths_noalloc, phc_track_pipeline)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -26,7 +26,7 @@ __all__ = [
     "phc_opts", "phc_refine_endpoints", "phc_track_many", "phc_track_paths", "phc_track_paths_noalloc",
     "phc_track_pipeline", "track_many", "phc_cascade_from", "PHC_STOP_SKIPPED", "cascade_from",
     "Tracked", "pipeline", "track", "cascade", "refine",
-    "stats_numpy",
+    "stats_numpy", "phc_tail_paths",
 ]
 
 

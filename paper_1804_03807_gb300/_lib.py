@@ -27,7 +27,7 @@ EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
     "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch", "phc_track_pipeline",
-    "phc_track_many", "phc_cascade_from",
+    "phc_track_many", "phc_cascade_from", "phc_tail_paths",
 ]
 
 
@@ -52,7 +52,7 @@ class phc_opts(ctypes.Structure):
         ("end_iters", ctypes.c_int32), ("end_tol", ctypes.c_double),
         ("cond_regular", ctypes.c_double), ("res_regular", ctypes.c_double), ("slack_tol", ctypes.c_double),
         ("precision", ctypes.c_int32), ("fp32_t_max", ctypes.c_double), ("fp32_pivot_ratio", ctypes.c_double),
-        ("block_threads", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32), ("max_blocks", ctypes.c_int32), ("tail_drain", ctypes.c_double),
     ]
 
 
@@ -96,6 +96,7 @@ def load() -> ctypes.CDLL:
     L.phc_track_many.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_track_pipeline.argtypes = [vp, i32, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp, vp, vp, vp]
     L.phc_refine_endpoints.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]
+    L.phc_tail_paths.argtypes = [vp, vp, ctypes.POINTER(i64)]
     L.phc_last_error.restype = ctypes.c_char_p
     L.phc_destroy_homotopy.argtypes = [vp]
     L.phc_destroy_homotopy.restype = None
@@ -105,7 +106,8 @@ def load() -> ctypes.CDLL:
                  "phc_track_paths",
                  "phc_track_paths_noalloc", "phc_track_pipeline", "phc_track_many", "phc_cascade_from",
                  "phc_embed",
-                 "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats"):
+                 "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats",
+                 "phc_tail_paths"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
         raise ImportError("phc_opts layout mismatch between phc.h and the binding")
@@ -189,6 +191,13 @@ def phc_make_homotopy_batch(systems, gammas) -> Homotopy:
 def phc_num_paths(h: Homotopy) -> int:
     v = ctypes.c_int64()
     _check(load().phc_num_paths(ctypes.c_void_p(h.ptr), ctypes.byref(v)))
+    return int(v.value)
+
+
+def phc_tail_paths(h: Homotopy, stream=None) -> int:
+    """Paths the last tracking call on h handed to the row-parallel tail kernel."""
+    v = ctypes.c_int64()
+    _check(load().phc_tail_paths(ctypes.c_void_p(h.ptr), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(v)))
     return int(v.value)
 
 

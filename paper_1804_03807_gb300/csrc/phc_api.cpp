@@ -70,6 +70,7 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->fp32_pivot_ratio = 1e4;
     o->block_threads = 0;
     o->max_blocks = 0;
+    o->tail_drain = 0.7;
     return PHC_OK;
 }
 
@@ -87,6 +88,7 @@ static int check_opts(const phc_opts &o)
         return fail(PHC_EINVAL, "unknown precision %d", o.precision);
     if (!(o.fp32_pivot_ratio >= 1.0)) return fail(PHC_EINVAL, "fp32_pivot_ratio must be >= 1");
     if (o.block_threads < 0 || o.block_threads % 32) return fail(PHC_EINVAL, "block_threads must be a multiple of 32");
+    if (!(o.tail_drain >= 0.0 && o.tail_drain <= 1.0)) return fail(PHC_EINVAL, "tail_drain must be in [0, 1]");
     return PHC_OK;
 }
 
@@ -122,6 +124,9 @@ struct phc_homotopy {
     int64_t stats2_cap = 0;
     double2 *d_xfull = nullptr;
     int64_t xfull_cap = 0;
+    phc::Handoff *d_handoff = nullptr;  // paths moved to the tail kernel
+    int64_t handoff_cap = 0;
+    unsigned long long *d_tailc = nullptr;  // hand-off, idle and tail queue counters
 };
 
 static void free_table(DeviceTable &t)
@@ -170,6 +175,8 @@ static int upload_table(const HostTerms &ht, int n, DeviceTable &out, cudaStream
     const size_t C = ht.c0.size();  // T per system
     const int n_sys = (int)(C / T);
     if (V > 65535) return fail(PHC_EUNSUPPORTED, "system too large (%zu exponent entries)", V);
+    for (size_t q = 1; q < T; q++)
+        if (ht.recs[q].eq < ht.recs[q - 1].eq) return fail(PHC_EINVAL, "internal: terms not grouped by equation");
     const size_t o_terms = 0;
     const size_t o_vars = o_terms + T * sizeof(TermRec);
     const size_t o_exps = o_vars + V;
@@ -371,7 +378,22 @@ extern "C" void phc_destroy_homotopy(phc_homotopy *h)
     if (h->d_stats) cudaFree(h->d_stats);
     if (h->d_stats2) cudaFree(h->d_stats2);
     if (h->d_xfull) cudaFree(h->d_xfull);
+    if (h->d_handoff) cudaFree(h->d_handoff);
+    if (h->d_tailc) cudaFree(h->d_tailc);
     delete h;
+}
+
+extern "C" int phc_tail_paths(const phc_homotopy *h, void *stream, int64_t *out)
+{
+    if (!h || !out) return fail(PHC_EINVAL, "NULL argument");
+    *out = 0;
+    if (!h->d_tailc) return PHC_OK;
+    unsigned long long v = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CU(cudaMemcpyAsync(&v, h->d_tailc, sizeof v, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *out = (int64_t)v;
+    return PHC_OK;
 }
 
 extern "C" int phc_num_paths(const phc_homotopy *h, int64_t *out)
@@ -395,6 +417,20 @@ static int ensure_stats(phc_homotopy *h, int64_t n)
     if (cudaMalloc(&h->d_stats, n * sizeof(phc_path_stats)) != cudaSuccess)
         return fail(PHC_ENOMEM, "cudaMalloc of %lld path records", (long long)n);
     h->stats_cap = n;
+    return PHC_OK;
+}
+
+static int ensure_handoff(phc_homotopy *h, int64_t lanes)
+{
+    if (!h->d_tailc && cudaMalloc(&h->d_tailc, 4 * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(PHC_ENOMEM, "cudaMalloc of the tail counters");
+    if (h->handoff_cap >= lanes) return PHC_OK;
+    if (h->d_handoff) cudaFree(h->d_handoff);
+    h->d_handoff = nullptr;
+    h->handoff_cap = 0;
+    if (cudaMalloc(&h->d_handoff, lanes * sizeof(phc::Handoff)) != cudaSuccess)
+        return fail(PHC_ENOMEM, "cudaMalloc of %lld hand-off records", (long long)lanes);
+    h->handoff_cap = lanes;
     return PHC_OK;
 }
 
@@ -433,8 +469,27 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.stats = stats;
     L.qhead = h->d_qhead;
     L.o = o;
+    const bool tail = o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64;
+    if (tail) {
+        const int64_t lanes = phc::track_lanes(L, o.block_threads, o.max_blocks);
+        if (lanes < 1) return fail(PHC_EUNSUPPORTED, "no launch configuration for %d unknowns", tab.n);
+        int rc = ensure_handoff(h, lanes);
+        if (rc) return rc;
+        CU(cudaMemsetAsync(h->d_tailc, 0, 3 * sizeof(unsigned long long), s));
+        L.handoff = h->d_handoff;
+        L.handoff_n = h->d_tailc;
+        L.idle_n = h->d_tailc + 1;
+        L.tail_q = h->d_tailc + 2;
+        L.drain_frac = o.tail_drain;
+    } else if (h->d_tailc) {
+        CU(cudaMemsetAsync(h->d_tailc, 0, sizeof(unsigned long long), s));  // phc_tail_paths reports 0
+    }
     cudaError_t e = phc::launch_track(L, o.block_threads, o.max_blocks, s);
     if (e != cudaSuccess) return fail(PHC_ECUDA, "track kernel launch: %s", cudaGetErrorString(e));
+    if (tail) {
+        e = phc::launch_tail(L, o.max_blocks, s);
+        if (e != cudaSuccess) return fail(PHC_ECUDA, "tail kernel launch: %s", cudaGetErrorString(e));
+    }
     phc::ClassifyLaunch C{};
     C.tab = tab;
     C.n_paths = n;

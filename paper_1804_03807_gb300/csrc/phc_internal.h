@@ -29,7 +29,9 @@ enum : uint8_t { TERM_POWERS = 1 };
 // Device tables of one homotopy (global memory; staged into shared memory
 // by the kernels).
 // A batch of n_sys homotopies shares terms/vars/exps; system s has the
-// coefficients c0[s * n_terms + q], c1[s * n_terms + q].
+// coefficients c0[s * n_terms + q], c1[s * n_terms + q].  Terms are grouped
+// by equation in ascending order (upload_table checks it; the tail kernel
+// relies on it).
 struct DevTables {
     int n;        // unknowns = equations
     int n_terms;  // terms
@@ -86,6 +88,15 @@ struct SysDesc {
     phc_path_stats *stats;    // [n_paths]
 };
 
+// The state of a path at the start of a step, handed from the tracker to
+// the row-parallel tail kernel when most lanes have run out of paths.
+struct Handoff {
+    double2 x0[PHC_MAX_VARS];
+    double t, h, next_s, nx0, r0, r1, r2, r3, r4;
+    int64_t q;
+    int32_t sys, streak, steps, since_ck, nck, n_acc, n_rej, n_newt, n_solve, n_f32;
+};
+
 struct TrackLaunch {
     DevTables tab;
     // starts: mode 0 = total-degree roots of unity, mode 1 = explicit SoA
@@ -118,6 +129,14 @@ struct TrackLaunch {
     const int64_t *multi_prefix;   // [n_multi + 1] prefix sums of path counts
     int n_multi;
     int warp_table_bytes;     // shared memory per warp for one system's table
+    // tail hand-off (mode 0, double precision): when idle_n reaches drain_at,
+    // lanes that start a new step save their path to handoff[] and leave
+    Handoff *handoff;
+    unsigned long long *handoff_n;
+    unsigned long long *idle_n;
+    unsigned long long *tail_q;
+    unsigned long long drain_at;  // set by the launcher from drain_frac
+    double drain_frac;            // fraction of idle lanes that starts the hand-off; 0: never
 };
 
 // Bytes of shared memory one warp needs for a table of T terms and V
@@ -156,6 +175,10 @@ cudaError_t launch_roots(const int32_t *deg, const int32_t *root_off, double2 *r
 cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_multi(const TrackLaunch &L, int n, int block_threads, int max_blocks, cudaStream_t s);
+// Lanes the tracker launches for L (grid x block), for sizing the hand-off buffer.
+int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks);
+// The paths handed off by launch_track (L.handoff), G threads per path.
+cudaError_t launch_tail(const TrackLaunch &L, int max_blocks, cudaStream_t s);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,

@@ -204,9 +204,78 @@ static __device__ SmTab stage_table_warp(const DevTables &g, char *region)
 
 // ------------------------------------------------------------------ evaluation
 
+// Adds one term (support size k >= 1) to its equation's row:
+//   Jrow[v_j] += d/dx_{v_j} ct x^a   (slot stride bt)
+//   *Rrow     += cr x^a              (when want_rhs)
+// and returns x^a.  Prefix products go to P[0..k).  Every derivative is
+// accumulated with one complex fused multiply-add, (a_j P_j) suf_j + J.
+// A term whose exponents are all 1 (the TERM_POWERS flag is clear; the flag
+// is the same for every lane, so the branch does not diverge) takes a path
+// with no common factor and no exponent scaling: written as selects, those
+// would cost FP64 multiplications on every term.  In a term with powers
+// every derivative is scaled by a_j (exact for a_j = 1).
+// The one-thread tracker and the row-parallel tail kernel both evaluate
+// through this function, so their rounding is the same.
+template <typename C>
+__device__ __forceinline__ C add_term(const TermRec r, const uint8_t *v, const uint8_t *e, C ct, C cr, bool want_rhs,
+                                      const double2 *X, double2 *Jrow, double2 *Rrow, double2 *P, int bt)
+{
+    typedef typename real_of<C>::type Real;
+    const int k = r.k;
+    C mono;
+    if (!(r.flags & TERM_POWERS)) {
+        // prefix products: P[j] = ct prod_{i<j} x_{v_i}
+        C pre = ct;
+        st(P, 0, bt, pre);
+        for (int j = 1; j < k; j++) {
+            pre = cmul(pre, ld<C>(X, v[j - 1], bt));
+            st(P, j, bt, pre);
+        }
+        // suffix products and the derivatives
+        C suf = ld<C>(X, v[k - 1], bt);
+        st(Jrow, v[k - 1], bt, cadd(ld<C>(Jrow, v[k - 1], bt), pre));
+        for (int j = k - 2; j >= 0; j--) {
+            st(Jrow, v[j], bt, cfma(ld<C>(P, j, bt), suf, ld<C>(Jrow, v[j], bt)));
+            suf = cmul(suf, ld<C>(X, v[j], bt));
+        }
+        mono = suf;
+    } else {
+        // common factor cf = prod_j x_{v_j}^{a_j - 1}
+        C cf = {Real(1), Real(0)};
+        for (int j = 0; j < k; j++) {
+            const int a = e[j];
+            if (a > 1) {
+                const C xv = ld<C>(X, v[j], bt);
+                C pw = xv;
+                for (int m = 2; m < a; m++) pw = cmul(pw, xv);
+                cf = cmul(cf, pw);
+            }
+        }
+        // prefix products: P[j] = ct cf prod_{i<j} x_{v_i}
+        C pre = cmul(ct, cf);
+        st(P, 0, bt, pre);
+        for (int j = 1; j < k; j++) {
+            pre = cmul(pre, ld<C>(X, v[j - 1], bt));
+            st(P, j, bt, pre);
+        }
+        C suf = ld<C>(X, v[k - 1], bt);
+        st(Jrow, v[k - 1], bt, cadd(ld<C>(Jrow, v[k - 1], bt), cscale((Real)e[k - 1], pre)));
+        for (int j = k - 2; j >= 0; j--) {
+            const C pj = cscale((Real)e[j], ld<C>(P, j, bt));
+            st(Jrow, v[j], bt, cfma(pj, suf, ld<C>(Jrow, v[j], bt)));
+            suf = cmul(suf, ld<C>(X, v[j], bt));
+        }
+        // suf = prod_j x_{v_j}; the monomial is cf * suf
+        mono = cmul(cf, suf);
+    }
+    if (want_rhs) st(Rrow, 0, bt, cfma(cr, mono, ld<C>(Rrow, 0, bt)));
+    return mono;
+}
+
 // One pass over the terms at the thread's point X (slots of complex C):
-// J = H_x (row-major N x N) and, when want_rhs, R = H_t (dt) or H (!dt).
-// Each term c(t) x^a with support v_0..v_{k-1} is split as
+// J = H_x (row-major N x N) and, when want_rhs, R = H_t (dt) or H (!dt), for
+// the homotopy sum_q (c0_q + t c1_q) x^{a_q}.  Each term c(t) x^a with
+// support v_0..v_{k-1} is split as
 //   x^a = cf * prod_j x_{v_j},  cf = prod_j x_{v_j}^{a_j - 1}   (common factor)
 // and its partial derivatives come from prefix and suffix products of the
 // x_{v_j} (Speelpenning's product rule):
@@ -220,7 +289,6 @@ __device__ __forceinline__ void evaluate(const C *C0, const C *C1, const SmTab &
 {
     typedef typename real_of<C>::type Real;
     const C zero = {Real(0), Real(0)};
-    const C one = {Real(1), Real(0)};
 #pragma unroll
     for (int i = 0; i < N; i++) {
         if (want_rhs) st(R, i, bt, zero);
@@ -234,54 +302,13 @@ __device__ __forceinline__ void evaluate(const C *C0, const C *C1, const SmTab &
         const C c0 = C0[q], c1 = C1[q];
         const C ct = {fmar(t, c1.x, c0.x), fmar(t, c1.y, c0.y)};
         const C cr = dt ? c1 : ct;  // coefficient of the right-hand side
-        const int k = r.k;
-        if (k == 0) {
+        if (r.k == 0) {
             if (want_rhs) st(R, r.eq, bt, cadd(ld<C>(R, r.eq, bt), cr));
             if (SCALE) SL(S, r.eq).x += abs1(ct);
             continue;
         }
-        const uint8_t *v = tb.vars + r.off;
-        const uint8_t *e = tb.exps + r.off;
-        C cf = one;
-        const bool powers = (r.flags & TERM_POWERS) != 0;
-        if (powers) {
-            for (int j = 0; j < k; j++) {
-                const int a = e[j];
-                if (a > 1) {
-                    const C xv = ld<C>(X, v[j], bt);
-                    C pw = xv;
-                    for (int m = 2; m < a; m++) pw = cmul(pw, xv);
-                    cf = cmul(cf, pw);
-                }
-            }
-        }
-        // prefix products: P[j] = ct cf prod_{i<j} x_{v_i}
-        C pre = powers ? cmul(ct, cf) : ct;
-        st(P, 0, bt, pre);
-        for (int j = 1; j < k; j++) {
-            pre = cmul(pre, ld<C>(X, v[j - 1], bt));
-            st(P, j, bt, pre);
-        }
-        // suffix products and the derivatives
-        C suf = ld<C>(X, v[k - 1], bt);
-        {
-            C d = ld<C>(P, k - 1, bt);
-            const int a = e[k - 1];
-            if (a > 1) d = cscale((Real)a, d);
-            const int idx = r.eq * N + v[k - 1];
-            st(J, idx, bt, cadd(ld<C>(J, idx, bt), d));
-        }
-        for (int j = k - 2; j >= 0; j--) {
-            C d = cmul(ld<C>(P, j, bt), suf);
-            const int a = e[j];
-            if (a > 1) d = cscale((Real)a, d);
-            const int idx = r.eq * N + v[j];
-            st(J, idx, bt, cadd(ld<C>(J, idx, bt), d));
-            suf = cmul(suf, ld<C>(X, v[j], bt));
-        }
-        // suf = prod_j x_{v_j}; the monomial is cf * suf
-        const C mono = powers ? cmul(cf, suf) : suf;
-        if (want_rhs) st(R, r.eq, bt, cfma(cr, mono, ld<C>(R, r.eq, bt)));
+        const C mono = add_term<C>(r, tb.vars + r.off, tb.exps + r.off, ct, cr, want_rhs, X, J + r.eq * N * bt,
+                                   R + r.eq * bt, P, bt);
         if (SCALE) SL(S, r.eq).x += abs1(ct) * abs1(mono);
     }
 }
@@ -381,11 +408,13 @@ __device__ __forceinline__ void lu_solve(const double2 *J, const int (&perm)[N],
         for (int j = 0; j < i; j++) s = cfms(s, ld<C>(J, i * N + j, bt), ld<C>(b, j, bt));
         st(b, i, bt, s);
     }
+    // back substitution, columns from the last to the first (the order the
+    // row-parallel tail kernel uses, so both produce the same rounding)
 #pragma unroll
     for (int i = N - 1; i >= 0; i--) {
         C s = ld<C>(b, i, bt);
 #pragma unroll
-        for (int j = i + 1; j < N; j++) s = cfms(s, ld<C>(J, i * N + j, bt), ld<C>(b, j, bt));
+        for (int j = N - 1; j > i; j--) s = cfms(s, ld<C>(J, i * N + j, bt), ld<C>(b, j, bt));
         st(b, i, bt, cmul(s, ld<C>(J, i * N + i, bt)));
     }
 }
@@ -631,7 +660,10 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             if (q < 0) continue;
         } else if (q < 0) {
             const unsigned long long c = atomicAdd(L.qhead, 1ull);
-            if (c >= (unsigned long long)np) break;
+            if (c >= (unsigned long long)np) {
+                if (L.drain_at) atomicAdd(L.idle_n, 1ull);
+                break;
+            }
             q = (int64_t)c;
             if (L.start_mode == 0) {
                 const int64_t gid = L.first + q;
@@ -846,6 +878,37 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             if (stop < 0 && ++since_ck >= o.max_steps_decade) stop = PHC_STOP_BUDGET;
             if (stop < 0) begin_step();
         }
+        if constexpr (MODE == MODE_SINGLE) {
+            // most lanes are idle: a path that starts a new step moves to
+            // the row-parallel tail kernel (which repeats this arithmetic
+            // exactly, so where a path is finished does not change it)
+            if (stop < 0 && act != ACT_NONE && phase == 0 && L.drain_at &&
+                *reinterpret_cast<volatile unsigned long long *>(L.idle_n) >= L.drain_at) {
+                Handoff &hd = L.handoff[atomicAdd(L.handoff_n, 1ull)];
+                for (int j = 0; j < N; j++) hd.x0[j] = x0[j];
+                hd.t = t;
+                hd.h = h;
+                hd.next_s = next_s;
+                hd.nx0 = nx0;
+                hd.r0 = r0;
+                hd.r1 = r1;
+                hd.r2 = r2;
+                hd.r3 = r3;
+                hd.r4 = r4;
+                hd.q = q;
+                hd.sys = sys;
+                hd.streak = streak;
+                hd.steps = steps;
+                hd.since_ck = since_ck;
+                hd.nck = nck;
+                hd.n_acc = n_acc;
+                hd.n_rej = n_rej;
+                hd.n_newt = n_newt;
+                hd.n_solve = n_solve;
+                hd.n_f32 = n_f32;
+                break;
+            }
+        }
         if (stop < 0) continue;
 
         // ---------------------------------------------------------- the path ends
@@ -920,9 +983,29 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 
 // ------------------------------------------------------------------ launch helper
 
-template <int N, int MODE>
-static cudaError_t launch_track_n(const TrackLaunch &L, int bt, int max_blocks, int64_t work, cudaStream_t s)
+// Lanes (grid x block) launch_track_n launches in mode 0 for L.
+template <int N>
+static int64_t lanes_n(const TrackLaunch &L, int bt, int max_blocks)
 {
+    const size_t smem = table_smem_bytes(L.tab) + (size_t)bt * thread_smem_bytes(N, false);
+    if (cudaFuncSetAttribute(track_kernel<N, MODE_SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<N, MODE_SINGLE>, bt, smem) != cudaSuccess)
+        return -1;
+    int64_t want = (L.n_paths + bt - 1) / bt;
+    int64_t grid = (int64_t)g_num_sms * per_sm;
+    if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    return grid * bt;
+}
+
+template <int N, int MODE>
+static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_blocks, int64_t work, cudaStream_t s)
+{
+    TrackLaunch L = L_in;
     size_t tb, tb2 = 0;
     if (MODE == MODE_MULTI) {
         tb = (size_t)(bt / 32) * (size_t)L.warp_table_bytes;
@@ -943,6 +1026,11 @@ static cudaError_t launch_track_n(const TrackLaunch &L, int bt, int max_blocks, 
     if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
+    L.drain_at = 0;
+    if (MODE == MODE_SINGLE && L.drain_frac > 0.0 && L.handoff) {
+        const unsigned long long at = (unsigned long long)(L.drain_frac * (double)(grid * bt));
+        L.drain_at = at < 1 ? 1 : at;
+    }
     track_kernel<N, MODE><<<(unsigned)grid, bt, smem, s>>>(L, tb, tb2);
     return cudaGetLastError();
 }

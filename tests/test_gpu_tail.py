@@ -1,0 +1,103 @@
+"""The row-parallel tail kernel changes nothing but where a path is finished.
+
+When most threads of a tracking launch have run out of paths, the paths
+that are still running move, at the start of their next step, to a kernel
+that gives every path one thread per equation (opts.tail_drain).  That
+kernel performs the same floating point operations in the same order, so
+endpoints, classes and every per-path statistic must be identical, bit for
+bit, to a run without the hand-off.  Each case runs three ways: hand-off
+off; the default; and a one-block grid with a drain fraction so small that
+nearly every path is handed off after its first step.
+"""
+import numpy as np
+import pytest
+
+import paper_1804_03807_gb300 as P
+from workloads import configs, cyclic, embedding_constants, multistep_example, random_dense, rng_for, unit_gamma
+
+pytestmark = pytest.mark.gpu
+
+
+def _opts(drain, tiny_grid=False):
+    o = P.phc_default_opts()
+    o.tail_drain = drain
+    if tiny_grid:
+        o.block_threads = 32
+        o.max_blocks = 1
+    return o
+
+
+def _host(r):
+    out = [r.x.cpu().numpy(), r.cls.cpu().numpy(), r.stats.cpu().numpy()]
+    if r.slack_zero is not None:
+        out.append(r.slack_zero.cpu().numpy())
+    return out
+
+
+def _same(a, b, label):
+    for u, v in zip(a, b):
+        assert u.shape == v.shape
+        assert u.tobytes() == v.tobytes(), f"{label}: results differ"
+
+
+def _three_ways(run, h):
+    base = _host(run(_opts(0.0)))
+    assert P.phc_tail_paths(h) == 0
+    dflt = _host(run(_opts(0.7)))
+    forced = _host(run(_opts(1e-9, tiny_grid=True)))
+    moved = P.phc_tail_paths(h)
+    _same(base, dflt, "default drain")
+    _same(base, forced, "forced hand-off")
+    return base, moved
+
+
+@pytest.mark.parametrize("case", ["dense4", "cyclic5", "ragged27", "dense9", "dense10"])
+def test_tail_handoff_bit_identical_total_degree(case):
+    if case == "dense4":
+        w = configs.dense4()
+        sys, g = w.systems[0], w.gammas[0]
+    elif case == "cyclic5":
+        sys, g = cyclic(5), unit_gamma(rng_for(305))
+    elif case == "ragged27":
+        sys, g = random_dense(3, 3, rng_for(400)), unit_gamma(rng_for(401))
+    else:
+        # n = 9 and 10 (16 threads per path): all monomials of degree <= 2
+        n = int(case[5:])
+        rng = rng_for(900 + n)
+        sys, g = random_dense(n, 2, rng), unit_gamma(rng)
+    h = P.phc_make_homotopy(sys, g)
+    (_, cls, _), moved = _three_ways(lambda o: P.track(h, opts=o), h)
+    n_paths = P.phc_num_paths(h)
+    # a 32-thread grid holds at most 32 paths at once: every path tracked
+    # after the queue ran dry and still running moves (most of the last 32)
+    assert moved >= min(n_paths, 32) // 2, moved
+    assert np.isin(cls, [0, 1, 2, 3]).all()
+
+
+def test_tail_handoff_bit_identical_batch_handle():
+    w = configs.cyclic_batch(n=5, copies=3)
+    h = P.phc_make_homotopy_batch(w.systems, w.gammas)
+    _, moved = _three_ways(lambda o: P.track(h, opts=o), h)
+    assert moved > 0
+
+
+def test_tail_handoff_bit_identical_cascade_stages():
+    """Cascade stages (explicit starts, and starts selected from the previous
+    stage's outputs) of Example 3.1 with the top dimension D = 3."""
+    import torch
+    sys = multistep_example()
+    D = 3
+    rng = rng_for(41)
+    g, hy = embedding_constants(rng, sys.n_eq, sys.n_var, D)
+    gamma = unit_gamma(rng)
+    E = P.phc_embed(sys, D, g, hy)
+    h = P.phc_make_homotopy(E, gamma)
+    top = P.track(h, opts=_opts(0.0))
+    x = top.x.cpu().numpy().T
+    cls = top.cls.cpu().numpy()
+    keep = (cls == 0) & (np.abs(x[:, -1]) > 1e-8 * (1 + np.abs(x).max(axis=1)))
+    starts = torch.from_numpy(np.ascontiguousarray(x[keep].T)).cuda()
+    (xs, cs, _, _), moved = _three_ways(lambda o: P.cascade(h, D, starts, opts=o), h)
+    assert moved > 0
+    _, moved = _three_ways(lambda o: P.cascade_from(h, D, top, opts=o), h)
+    assert moved > 0
