@@ -215,6 +215,8 @@ static int upload_table(const HostTerms &ht, int n, DeviceTable &out, cudaStream
     out.view.n_terms = (int)T;
     out.view.n_ve = (int)V;
     out.view.n_sys = n_sys;
+    out.view.f32 = 1;  // launchers of double precision work clear it
+    out.view.coef_smem = 1;
     out.view.terms = reinterpret_cast<const TermRec *>(b + o_terms);
     out.view.vars = reinterpret_cast<const uint8_t *>(b + o_vars);
     out.view.exps = reinterpret_cast<const uint8_t *>(b + o_exps);
@@ -455,6 +457,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     CU(cudaMemsetAsync(h->d_qhead, 0, sizeof(unsigned long long), s));
     phc::TrackLaunch L{};
     L.tab = tab;
+    L.tab.f32 = o.precision == PHC_PREC_FP32_INTERIOR;
     L.start_mode = start_mode;
     L.deg = h->d_deg;
     L.root_off = h->d_root_off;
@@ -469,6 +472,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.stats = stats;
     L.qhead = h->d_qhead;
     L.o = o;
+    phc::plan_track(L, o.block_threads);
     const bool tail = o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64;
     if (tail) {
         const int64_t lanes = phc::track_lanes(L, o.block_threads, o.max_blocks);
@@ -492,6 +496,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     }
     phc::ClassifyLaunch C{};
     C.tab = tab;
+    C.tab.f32 = 0;
     C.n_paths = n;
     C.x = x_out;
     C.stats = stats;
@@ -622,6 +627,7 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
             if (h->n != n || h->num_paths == 0) continue;
             phc::SysDesc d{};
             d.tab = h->total.view;
+            d.tab.f32 = o.precision == PHC_PREC_FP32_INTERIOR;
             d.deg = h->d_deg;
             d.root_off = h->d_root_off;
             d.roots = h->d_roots;
@@ -637,7 +643,7 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
             d.stats = sp;
             descs.push_back(d);
             prefix.push_back(prefix.back() + h->num_paths);
-            const int b = (int)phc::warp_table_bytes(h->total.view.n_terms, h->total.view.n_ve);
+            const int b = (int)phc::warp_table_bytes(d.tab.n_terms, d.tab.n_ve, d.tab.f32);
             if (b > wtb) wtb = b;
         }
         if (descs.empty()) continue;
@@ -748,6 +754,7 @@ extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t
     L.qhead = h->d_qhead;
     L.o = o;
     L.tab2 = h->cascade.view;
+    L.tab.f32 = L.tab2.f32 = o.precision == PHC_PREC_FP32_INTERIOR;
     L.cls_out = cls_top;
     L.x_out2 = reinterpret_cast<double2 *>(x_next);
     L.cls_out2 = cls_next;

@@ -37,6 +37,11 @@ struct DevTables {
     int n_terms;  // terms
     int n_ve;     // entries of vars / exps
     int n_sys;    // systems sharing the structure
+    int f32;      // the single precision copies are staged and used (FP32 interior); the
+                  // launchers clear it for double precision work
+    int coef_smem;  // stage the coefficients into shared memory (when within
+                    // COEF_SMEM_LIMIT); plan_track clears it when that would
+                    // cost the tracker a warp per block
     const TermRec *terms;
     const uint8_t *vars;
     const uint8_t *exps;
@@ -46,15 +51,16 @@ struct DevTables {
     const float2 *c1f;
 };
 
-// Bytes of coefficients per term and system: c0, c1 in double, c0, c1 in float.
-constexpr size_t COEF_BYTES = 2 * 16 + 2 * 8;
+// Bytes of coefficients per term and system: c0, c1 in double and, with
+// f32, c0, c1 in float.
+__host__ __device__ inline size_t coef_bytes(bool f32) { return f32 ? 2 * 16 + 2 * 8 : 2 * 16; }
 // Coefficients of all systems are staged into shared memory up to this size;
 // larger batches read them through L1.
 constexpr size_t COEF_SMEM_LIMIT = 48 * 1024;
 
 __host__ __device__ inline bool coefs_in_smem(const DevTables &t)
 {
-    return (size_t)t.n_terms * (size_t)t.n_sys * COEF_BYTES <= COEF_SMEM_LIMIT;
+    return t.coef_smem && (size_t)t.n_terms * (size_t)t.n_sys * coef_bytes(t.f32) <= COEF_SMEM_LIMIT;
 }
 
 // Bytes the staged copy of a table takes in shared memory (16-byte aligned).
@@ -62,17 +68,19 @@ __host__ __device__ inline size_t table_smem_bytes(const DevTables &t)
 {
     size_t b = (size_t)t.n_terms * sizeof(TermRec) + 2 * (size_t)t.n_ve;
     b = (b + 15) & ~(size_t)15;
-    if (coefs_in_smem(t)) b += (size_t)t.n_terms * (size_t)t.n_sys * COEF_BYTES;
+    if (coefs_in_smem(t)) b += (size_t)t.n_terms * (size_t)t.n_sys * coef_bytes(t.f32);
     return b;
 }
 
 // Per-thread shared memory: the evaluation point xe, the right-hand side R,
-// prefix products P, the single precision point X (N slots each), the
-// Jacobian J (N*N slots) and, for classification, the scales S (N slots);
-// one slot is a complex double (single precision values use its first half).
-inline size_t thread_smem_bytes(int n, bool scale = false)
+// prefix products P (N slots each), with f32 the single precision point X
+// (N slots), the Jacobian J (N*N slots) and, for classification, the scales
+// S (N slots); one slot is a complex double (single precision values use its
+// first half).  Without X a 160-thread block of the 7-unknown tracker grows
+// to 192 threads.
+inline size_t thread_smem_bytes(int n, bool scale = false, bool f32 = true)
 {
-    return (size_t)(n * n + 4 * n + (scale ? n : 0)) * sizeof(double2);
+    return (size_t)(n * n + 3 * n + (f32 ? n : 0) + (scale ? n : 0)) * sizeof(double2);
 }
 
 // One system of a multi-system launch (systems of different structure and
@@ -141,11 +149,11 @@ struct TrackLaunch {
 
 // Bytes of shared memory one warp needs for a table of T terms and V
 // exponent entries (single system, 16-byte aligned).
-__host__ __device__ inline size_t warp_table_bytes(int T, int V)
+__host__ __device__ inline size_t warp_table_bytes(int T, int V, bool f32)
 {
     size_t b = (size_t)T * sizeof(TermRec) + 2 * (size_t)V;
     b = (b + 15) & ~(size_t)15;
-    return b + (size_t)T * COEF_BYTES;
+    return b + (size_t)T * coef_bytes(f32);
 }
 
 struct ClassifyLaunch {
@@ -175,6 +183,10 @@ cudaError_t launch_roots(const int32_t *deg, const int32_t *root_off, double2 *r
 cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_multi(const TrackLaunch &L, int n, int block_threads, int max_blocks, cudaStream_t s);
+// Chooses where the mode-0 tracker keeps the coefficients of L.tab (sets
+// L.tab.coef_smem): in shared memory unless reading them through L1 lets a
+// block hold more threads.  Call before track_lanes and launch_track.
+void plan_track(TrackLaunch &L, int block_threads);
 // Lanes the tracker launches for L (grid x block), for sizing the hand-off buffer.
 int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks);
 // The paths handed off by launch_track (L.handoff), G threads per path.
@@ -186,6 +198,6 @@ cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths,
 
 // Threads per block the tracker uses for n unknowns and a table of the given
 // size (fills up to the opt-in shared memory of one block).
-int track_block_threads(int n, size_t table_bytes, int requested, bool scale = false);
+int track_block_threads(int n, size_t table_bytes, int requested, bool scale = false, bool f32 = true);
 
 }  // namespace phc

@@ -49,10 +49,10 @@ void device_limits()
     cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 }
 
-int track_block_threads(int n, size_t table_bytes, int requested, bool scale)
+int track_block_threads(int n, size_t table_bytes, int requested, bool scale, bool f32)
 {
     device_limits();
-    const size_t per = thread_smem_bytes(n, scale);
+    const size_t per = thread_smem_bytes(n, scale, f32);
     long fit = ((long)g_smem_optin - (long)table_bytes) / (long)per;
     int bt = (int)((fit / 32) * 32);
     if (bt > 256) bt = 256;
@@ -65,9 +65,9 @@ template <int N>
 static cudaError_t launch_classify_n(const ClassifyLaunch &L, cudaStream_t s)
 {
     const size_t tb = table_smem_bytes(L.tab);
-    const int bt = track_block_threads(N, tb, 128, true);
+    const int bt = track_block_threads(N, tb, 128, true, false);
     if (bt == 0) return cudaErrorInvalidConfiguration;
-    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, true);
+    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, true, false);
     cudaError_t e = cudaFuncSetAttribute(classify_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t grid = (L.n_paths + bt - 1) / bt;
@@ -82,18 +82,30 @@ cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks
     device_limits();
     if (L.n_paths <= 0) return cudaSuccess;
     const size_t tb = table_smem_bytes(L.tab);
-    const int bt = track_block_threads(L.tab.n, tb, block_threads);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
     if (bt == 0) return cudaErrorInvalidConfiguration;
 #define PHC_CALL_TRACK(NN) launch_track_n<NN, MODE_SINGLE>(L, bt, max_blocks, L.n_paths, s)
     PHC_DISPATCH_N(L.tab.n, PHC_CALL_TRACK)
 #undef PHC_CALL_TRACK
 }
 
+void plan_track(TrackLaunch &L, int block_threads)
+{
+    device_limits();
+    const bool f32 = L.o.precision == PHC_PREC_FP32_INTERIOR;
+    L.tab.coef_smem = 1;
+    const int in_smem = track_block_threads(L.tab.n, table_smem_bytes(L.tab), block_threads, false, f32);
+    DevTables t = L.tab;
+    t.coef_smem = 0;
+    const int in_l1 = track_block_threads(L.tab.n, table_smem_bytes(t), block_threads, false, f32);
+    if (in_l1 > in_smem) L.tab.coef_smem = 0;
+}
+
 int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks)
 {
     device_limits();
     const size_t tb = table_smem_bytes(L.tab);
-    const int bt = track_block_threads(L.tab.n, tb, block_threads);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
     if (bt == 0) return -1;
     switch (L.tab.n) {
     case 1: return lanes_n<1>(L, bt, max_blocks);

@@ -138,18 +138,24 @@ static __device__ SmTab stage_table(const DevTables &g, char *smem)
         const int nc = g.n_terms * g.n_sys;
         double2 *c0 = reinterpret_cast<double2 *>(smem + b);
         double2 *c1 = c0 + nc;
-        float2 *c0f = reinterpret_cast<float2 *>(c1 + nc);
-        float2 *c1f = c0f + nc;
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             c0[i] = g.c0[i];
             c1[i] = g.c1[i];
-            c0f[i] = g.c0f[i];
-            c1f[i] = g.c1f[i];
         }
         s.c0 = c0;
         s.c1 = c1;
-        s.c0f = c0f;
-        s.c1f = c1f;
+        s.c0f = g.c0f;
+        s.c1f = g.c1f;
+        if (g.f32) {
+            float2 *c0f = reinterpret_cast<float2 *>(c1 + nc);
+            float2 *c1f = c0f + nc;
+            for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+                c0f[i] = g.c0f[i];
+                c1f[i] = g.c1f[i];
+            }
+            s.c0f = c0f;
+            s.c1f = c1f;
+        }
     } else {
         s.c0 = g.c0;
         s.c1 = g.c1;
@@ -183,8 +189,10 @@ static __device__ SmTab stage_table_warp(const DevTables &g, char *region)
         terms[i] = g.terms[i];
         c0[i] = g.c0[i];
         c1[i] = g.c1[i];
-        c0f[i] = g.c0f[i];
-        c1f[i] = g.c1f[i];
+        if (g.f32) {
+            c0f[i] = g.c0f[i];
+            c1f[i] = g.c1f[i];
+        }
     }
     for (int i = lane; i < g.n_ve; i += 32) {
         vars[i] = g.vars[i];
@@ -425,15 +433,17 @@ struct ThreadArrays {
     double2 *xe, *R, *P, *X, *J, *S;
 };
 
+// The layout of thread_smem_bytes; without f32 there is no X (it aliases P
+// and is never touched).
 template <int N>
-__device__ __forceinline__ ThreadArrays thread_arrays(char *smem, size_t table_bytes, int bt)
+__device__ __forceinline__ ThreadArrays thread_arrays(char *smem, size_t table_bytes, int bt, bool f32)
 {
     ThreadArrays a;
     a.xe = reinterpret_cast<double2 *>(smem + table_bytes) + threadIdx.x;
     a.R = a.xe + N * bt;
     a.P = a.R + N * bt;
-    a.X = a.P + N * bt;
-    a.J = a.X + N * bt;
+    a.X = f32 ? a.P + N * bt : a.P;
+    a.J = f32 ? a.X + N * bt : a.P + N * bt;
     a.S = a.J + N * N * bt;  // classification only
     return a;
 }
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const ClassifyLaunch L, s
     extern __shared__ __align__(16) char smem[];
     const SmTab tb = stage_table(L.tab, smem);
     const int bt = blockDim.x;
-    const ThreadArrays A = thread_arrays<N>(smem, table_bytes, bt);
+    const ThreadArrays A = thread_arrays<N>(smem, table_bytes, bt, false);
     const int64_t np = L.n_paths;
     for (int64_t q = (int64_t)blockIdx.x * bt + threadIdx.x; q < np; q += (int64_t)gridDim.x * bt) {
         phc_path_stats s = L.stats[q];
@@ -557,7 +567,8 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
         if constexpr (PIPE) tb2 = stage_table(L.tab2, smem + table_bytes);
     }
     const int bt = blockDim.x;
-    const ThreadArrays A = thread_arrays<N>(smem, table_bytes + table2_bytes, bt);
+    const bool f32 = L.o.precision == PHC_PREC_FP32_INTERIOR;
+    const ThreadArrays A = thread_arrays<N>(smem, table_bytes + table2_bytes, bt, f32);
     const phc_opts &o = L.o;
     const int64_t np = L.n_paths;
     const bool interior32 = o.precision == PHC_PREC_FP32_INTERIOR;
@@ -987,7 +998,8 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 template <int N>
 static int64_t lanes_n(const TrackLaunch &L, int bt, int max_blocks)
 {
-    const size_t smem = table_smem_bytes(L.tab) + (size_t)bt * thread_smem_bytes(N, false);
+    const size_t smem = table_smem_bytes(L.tab) +
+                        (size_t)bt * thread_smem_bytes(N, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
     if (cudaFuncSetAttribute(track_kernel<N, MODE_SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
@@ -1013,7 +1025,8 @@ static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_block
         tb = table_smem_bytes(L.tab);
         if (MODE == MODE_PIPE) tb2 = table_smem_bytes(L.tab2);
     }
-    const size_t smem = tb + tb2 + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE);
+    const size_t smem =
+        tb + tb2 + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, L.o.precision == PHC_PREC_FP32_INTERIOR);
     cudaError_t e =
         cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

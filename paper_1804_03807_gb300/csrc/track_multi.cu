@@ -10,7 +10,8 @@ cudaError_t launch_multi(const TrackLaunch &L, int n, int block_threads, int max
     device_limits();
     if (L.n_multi <= 0) return cudaSuccess;
     // shared memory per thread plus a table region per warp
-    const size_t per = thread_smem_bytes(n, true) + (size_t)L.warp_table_bytes / 32;
+    const size_t per =
+        thread_smem_bytes(n, true, L.o.precision == PHC_PREC_FP32_INTERIOR) + (size_t)L.warp_table_bytes / 32;
     long fit = (long)g_smem_optin / (long)per;
     int bt = (int)((fit / 32) * 32);
     if (bt > 256) bt = 256;

@@ -337,8 +337,10 @@ __global__ void __launch_bounds__(128) tail_kernel(const TrackLaunch L, size_t t
 }
 
 template <int N, int G>
-static cudaError_t launch_tail_n(const TrackLaunch &L, int max_blocks, cudaStream_t s)
+static cudaError_t launch_tail_n(const TrackLaunch &L_in, int max_blocks, cudaStream_t s)
 {
+    TrackLaunch L = L_in;
+    L.tab.coef_smem = 1;  // this kernel's shared memory is small
     const size_t tb = table_smem_bytes(L.tab);
     const int bt = 128;
     const size_t smem = tb + (size_t)(bt / G) * (2 * N + N * N + G * N) * sizeof(double2);
