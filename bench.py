@@ -239,6 +239,10 @@ def run_gpu(args):
     opts = P.phc_default_opts(precision=args.precision)
     if args.tail_drain is not None:
         opts.tail_drain = args.tail_drain
+    if args.block_threads:
+        opts.block_threads = args.block_threads
+    if args.tail_threads:
+        opts.tail_threads = args.tail_threads
     tail_on = opts.tail_drain > 0 and args.precision == 0
     launches_per_step = 4 if tail_on else 3  # track, (tail,) classify, refine
 
@@ -282,19 +286,27 @@ def run_gpu(args):
     # roofline of track_kernel: algorithmic flops / duration of the tracking
     # call; units done in single precision count against the FP32 peak
     stn = P.stats_numpy(st)
-    tail_paths = P.phc_tail_paths(h, main)
+    tail_paths, tail_units = P.phc_tail_paths(h, main, units=True)
     units = int(stn["n_solve"].sum())
     units32 = int(stn["n_fp32"].sum())
     f64 = (units - units32) * uf
     f32 = units32 * uf
     kern_ms = float(np.mean([p0.elapsed_time(p1) for p0, p1 in pairs]))
+    # DRAM bytes (read + write) per tracking call: ncu counters of track_kernel<7,0>
+    # (202,752 B) and tail_kernel<7,32> (454,656 B) tracking one system of this
+    # batch (5040 paths, 3,969,533 units), scaled by the units of this step.
+    # Only meaningful for the default FP64 configuration those kernels ran in.
+    traffic = args.traffic
+    if traffic is None and args.precision == 0 and tail_on and (opts.tail_threads or 32) == 32:
+        traffic = (202_752 + 454_656) * units / 3_969_533
     secs = kern_ms / 1e3
     frac = (f64 / secs / 1e12) / FP64_PEAK_TFLOPS + (f32 / secs / 1e12) / FP32_PEAK_TFLOPS
     roofline = {"bound": "alu", "achieved": f64 / secs / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": frac, "traffic": args.traffic,
-                "kernel": ("track_kernel<7> + tail_kernel<7,8>" if tail_on else "track_kernel<7>") +
+                "frac": frac, "traffic": traffic,
+                "kernel": (f"track_kernel<7> + tail_kernel<7,{opts.tail_threads or 32}>" if tail_on else "track_kernel<7>") +
                           " (+classify_kernel<7>, <0.1 %)",
-                "tail_paths_per_step": tail_paths, "tail_drain": opts.tail_drain if tail_on else 0.0,
+                "tail_paths_per_step": tail_paths, "tail_units_per_step": tail_units,
+                "tail_drain": opts.tail_drain if tail_on else 0.0,
                 "fp64_flops_per_step": f64,
                 "fp32_flops_per_step": f32, "fp32_peak": FP32_PEAK_TFLOPS, "units_per_step": units,
                 "fp32_units_per_step": units32, "kernel_ms": kern_ms,
@@ -340,6 +352,10 @@ def end_to_end(P, systems, gammas, dev, args):
     opts = P.phc_default_opts(precision=args.precision)
     if args.tail_drain is not None:
         opts.tail_drain = args.tail_drain
+    if args.block_threads:
+        opts.block_threads = args.block_threads
+    if args.tail_threads:
+        opts.tail_threads = args.tail_threads
 
     def one():
         h = P.phc_make_homotopy_batch(systems, gammas)
@@ -442,6 +458,9 @@ def main(argv=None):
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per track launch, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=0, help="0 = FP64, 1 = FP32 interior")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="tracker threads per block (multiple of 32; default: as many as shared memory holds)")
+    ap.add_argument("--tail-threads", type=int, default=0, help="threads per path in the tail kernel (8, 16, 32)")
     ap.add_argument("--tail-drain", type=float, default=None,
                     help="fraction of idle tracker threads that moves running paths to the tail kernel "
                          "(default: the library's; 0 = off)")

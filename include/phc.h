@@ -119,6 +119,7 @@ typedef struct {
                                 gives each path a group of threads (one per equation); the
                                 arithmetic is the same, operation for operation, so the results do
                                 not change.  0 = never. */
+    int32_t tail_threads;    /* threads per path in that kernel: 8 (N <= 8), 16 or 32; 0 = 32 */
 } phc_opts;
 
 /* Per-path statistics (device array of these, optional). */
@@ -176,11 +177,12 @@ int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *terms_per_eq, co
                             const phc_cd *coefs, const phc_cd *gammas, phc_homotopy **out);
 
 /* Paths that the last tracking call on h (phc_track_paths, phc_cascade_stage,
- * phc_cascade_from) moved to the row-parallel tail kernel (opts.tail_drain);
- * 0 when no such call ran or the option was 0.  Host call: waits for
- * cuda_stream (the stream of that call) before reading the device counter.
- * Errors: PHC_EINVAL for a NULL argument; PHC_ECUDA. */
-int phc_tail_paths(const phc_homotopy *h, void *cuda_stream, int64_t *out);
+ * phc_cascade_from) moved to the row-parallel tail kernel (opts.tail_drain),
+ * and the evaluate+solve units those paths ran there (units_out may be
+ * NULL); 0 when no such call ran or the option was 0.  Host call: waits for
+ * cuda_stream (the stream of that call) before reading the device counters.
+ * Errors: PHC_EINVAL for a NULL handle or paths_out; PHC_ECUDA. */
+int phc_tail_paths(const phc_homotopy *h, void *cuda_stream, int64_t *paths_out, int64_t *units_out);
 
 /* Number of paths of the total-degree homotopy, prod d_i (host call); for a
  * batch handle, n_systems * prod d_i. */

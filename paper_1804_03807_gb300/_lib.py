@@ -53,6 +53,7 @@ class phc_opts(ctypes.Structure):
         ("cond_regular", ctypes.c_double), ("res_regular", ctypes.c_double), ("slack_tol", ctypes.c_double),
         ("precision", ctypes.c_int32), ("fp32_t_max", ctypes.c_double), ("fp32_pivot_ratio", ctypes.c_double),
         ("block_threads", ctypes.c_int32), ("max_blocks", ctypes.c_int32), ("tail_drain", ctypes.c_double),
+        ("tail_threads", ctypes.c_int32),
     ]
 
 
@@ -96,7 +97,7 @@ def load() -> ctypes.CDLL:
     L.phc_track_many.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_track_pipeline.argtypes = [vp, i32, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp, vp, vp, vp]
     L.phc_refine_endpoints.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]
-    L.phc_tail_paths.argtypes = [vp, vp, ctypes.POINTER(i64)]
+    L.phc_tail_paths.argtypes = [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.phc_last_error.restype = ctypes.c_char_p
     L.phc_destroy_homotopy.argtypes = [vp]
     L.phc_destroy_homotopy.restype = None
@@ -194,11 +195,14 @@ def phc_num_paths(h: Homotopy) -> int:
     return int(v.value)
 
 
-def phc_tail_paths(h: Homotopy, stream=None) -> int:
-    """Paths the last tracking call on h handed to the row-parallel tail kernel."""
+def phc_tail_paths(h: Homotopy, stream=None, units: bool = False):
+    """Paths the last tracking call on h handed to the row-parallel tail
+    kernel (with units=True: (paths, units run in the tail kernel))."""
     v = ctypes.c_int64()
-    _check(load().phc_tail_paths(ctypes.c_void_p(h.ptr), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(v)))
-    return int(v.value)
+    u = ctypes.c_int64()
+    _check(load().phc_tail_paths(ctypes.c_void_p(h.ptr), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(v),
+                                 ctypes.byref(u)))
+    return (int(v.value), int(u.value)) if units else int(v.value)
 
 
 def phc_track_paths(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls_out, stats_out=None, stream=None):

@@ -70,7 +70,8 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->fp32_pivot_ratio = 1e4;
     o->block_threads = 0;
     o->max_blocks = 0;
-    o->tail_drain = 0.7;
+    o->tail_drain = 0.85;
+    o->tail_threads = 0;
     return PHC_OK;
 }
 
@@ -89,6 +90,8 @@ static int check_opts(const phc_opts &o)
     if (!(o.fp32_pivot_ratio >= 1.0)) return fail(PHC_EINVAL, "fp32_pivot_ratio must be >= 1");
     if (o.block_threads < 0 || o.block_threads % 32) return fail(PHC_EINVAL, "block_threads must be a multiple of 32");
     if (!(o.tail_drain >= 0.0 && o.tail_drain <= 1.0)) return fail(PHC_EINVAL, "tail_drain must be in [0, 1]");
+    if (o.tail_threads != 0 && o.tail_threads != 8 && o.tail_threads != 16 && o.tail_threads != 32)
+        return fail(PHC_EINVAL, "tail_threads must be 0, 8, 16 or 32");
     return PHC_OK;
 }
 
@@ -385,16 +388,18 @@ extern "C" void phc_destroy_homotopy(phc_homotopy *h)
     delete h;
 }
 
-extern "C" int phc_tail_paths(const phc_homotopy *h, void *stream, int64_t *out)
+extern "C" int phc_tail_paths(const phc_homotopy *h, void *stream, int64_t *out, int64_t *units_out)
 {
     if (!h || !out) return fail(PHC_EINVAL, "NULL argument");
     *out = 0;
+    if (units_out) *units_out = 0;
     if (!h->d_tailc) return PHC_OK;
-    unsigned long long v = 0;
+    unsigned long long v[4] = {0, 0, 0, 0};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CU(cudaMemcpyAsync(&v, h->d_tailc, sizeof v, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(v, h->d_tailc, sizeof v, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    *out = (int64_t)v;
+    *out = (int64_t)v[0];
+    if (units_out) *units_out = (int64_t)v[3];
     return PHC_OK;
 }
 
@@ -472,21 +477,21 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.stats = stats;
     L.qhead = h->d_qhead;
     L.o = o;
-    phc::plan_track(L, o.block_threads);
-    const bool tail = o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64;
+    const bool tail = o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64 && phc::tail_supported(L.tab);
     if (tail) {
         const int64_t lanes = phc::track_lanes(L, o.block_threads, o.max_blocks);
         if (lanes < 1) return fail(PHC_EUNSUPPORTED, "no launch configuration for %d unknowns", tab.n);
         int rc = ensure_handoff(h, lanes);
         if (rc) return rc;
-        CU(cudaMemsetAsync(h->d_tailc, 0, 3 * sizeof(unsigned long long), s));
+        CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));
         L.handoff = h->d_handoff;
         L.handoff_n = h->d_tailc;
         L.idle_n = h->d_tailc + 1;
         L.tail_q = h->d_tailc + 2;
+        L.tail_units = h->d_tailc + 3;
         L.drain_frac = o.tail_drain;
     } else if (h->d_tailc) {
-        CU(cudaMemsetAsync(h->d_tailc, 0, sizeof(unsigned long long), s));  // phc_tail_paths reports 0
+        CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));  // phc_tail_paths reports 0
     }
     cudaError_t e = phc::launch_track(L, o.block_threads, o.max_blocks, s);
     if (e != cudaSuccess) return fail(PHC_ECUDA, "track kernel launch: %s", cudaGetErrorString(e));

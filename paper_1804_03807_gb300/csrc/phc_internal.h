@@ -40,8 +40,8 @@ struct DevTables {
     int f32;      // the single precision copies are staged and used (FP32 interior); the
                   // launchers clear it for double precision work
     int coef_smem;  // stage the coefficients into shared memory (when within
-                    // COEF_SMEM_LIMIT); plan_track clears it when that would
-                    // cost the tracker a warp per block
+                    // COEF_SMEM_LIMIT); the tail launcher clears it when its
+                    // term store would not fit otherwise
     const TermRec *terms;
     const uint8_t *vars;
     const uint8_t *exps;
@@ -143,6 +143,7 @@ struct TrackLaunch {
     unsigned long long *handoff_n;
     unsigned long long *idle_n;
     unsigned long long *tail_q;
+    unsigned long long *tail_units;  // units the tail kernel ran (diagnostic)
     unsigned long long drain_at;  // set by the launcher from drain_frac
     double drain_frac;            // fraction of idle lanes that starts the hand-off; 0: never
 };
@@ -183,14 +184,12 @@ cudaError_t launch_roots(const int32_t *deg, const int32_t *root_off, double2 *r
 cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_multi(const TrackLaunch &L, int n, int block_threads, int max_blocks, cudaStream_t s);
-// Chooses where the mode-0 tracker keeps the coefficients of L.tab (sets
-// L.tab.coef_smem): in shared memory unless reading them through L1 lets a
-// block hold more threads.  Call before track_lanes and launch_track.
-void plan_track(TrackLaunch &L, int block_threads);
 // Lanes the tracker launches for L (grid x block), for sizing the hand-off buffer.
 int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks);
-// The paths handed off by launch_track (L.handoff), G threads per path.
+// The paths handed off by launch_track (L.handoff), L.o.tail_threads threads
+// per path; tail_supported: the tail kernel can hold one path of this table.
 cudaError_t launch_tail(const TrackLaunch &L, int max_blocks, cudaStream_t s);
+bool tail_supported(const DevTables &t);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,

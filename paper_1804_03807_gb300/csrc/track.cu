@@ -89,18 +89,6 @@ cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks
 #undef PHC_CALL_TRACK
 }
 
-void plan_track(TrackLaunch &L, int block_threads)
-{
-    device_limits();
-    const bool f32 = L.o.precision == PHC_PREC_FP32_INTERIOR;
-    L.tab.coef_smem = 1;
-    const int in_smem = track_block_threads(L.tab.n, table_smem_bytes(L.tab), block_threads, false, f32);
-    DevTables t = L.tab;
-    t.coef_smem = 0;
-    const int in_l1 = track_block_threads(L.tab.n, table_smem_bytes(t), block_threads, false, f32);
-    if (in_l1 > in_smem) L.tab.coef_smem = 0;
-}
-
 int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks)
 {
     device_limits();

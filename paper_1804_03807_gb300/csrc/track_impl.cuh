@@ -61,7 +61,10 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c)
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+// __dmul_rn: the product is rounded on its own and never merged into a
+// following addition, so a scaled derivative rounds the same whether it is
+// added at once (one-thread tracker) or stored and added later (tail kernel).
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(__dmul_rn(s, a.x), __dmul_rn(s, a.y)); }
 __device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
 // a + s b
 __device__ __forceinline__ double2 caxpy(double2 a, double s, double2 b)
@@ -212,43 +215,44 @@ static __device__ SmTab stage_table_warp(const DevTables &g, char *region)
 
 // ------------------------------------------------------------------ evaluation
 
-// Adds one term (support size k >= 1) to its equation's row:
-//   Jrow[v_j] += d/dx_{v_j} ct x^a   (slot stride bt)
-//   *Rrow     += cr x^a              (when want_rhs)
-// and returns x^a.  Prefix products go to P[0..k).  Every derivative is
-// accumulated with one complex fused multiply-add, (a_j P_j) suf_j + J.
+// One term (support size k >= 1) of an equation, c x^a with coefficient ct
+// in the Jacobian and cr in the right-hand side.  Produces, in this order,
+//   sink.last(v_{k-1}, d)           d = a_{k-1} P_{k-1}
+//   sink.deriv(j, v_j, p_j, s_j)    p_j = a_j P_j, s_j = prod_{i>j} x_{v_i}, j = k-2..0
+//   sink.rhs(cr, x^a)
+// where P_j = ct cf prod_{i<j} x_{v_i} are the prefix products (kept through
+// sink.put_prefix / get_prefix) and cf = prod_j x_{v_j}^{a_j - 1} the common
+// factor; the partial derivative d/dx_{v_j} of ct x^a is p_j s_j.  Returns x^a.
 // A term whose exponents are all 1 (the TERM_POWERS flag is clear; the flag
 // is the same for every lane, so the branch does not diverge) takes a path
 // with no common factor and no exponent scaling: written as selects, those
-// would cost FP64 multiplications on every term.  In a term with powers
-// every derivative is scaled by a_j (exact for a_j = 1).
-// The one-thread tracker and the row-parallel tail kernel both evaluate
-// through this function, so their rounding is the same.
-template <typename C>
-__device__ __forceinline__ C add_term(const TermRec r, const uint8_t *v, const uint8_t *e, C ct, C cr, bool want_rhs,
-                                      const double2 *X, double2 *Jrow, double2 *Rrow, double2 *P, int bt)
+// would cost FP64 multiplications on every term.
+// AccumSink adds every piece into the thread's row at once (J += p_j s_j as
+// one complex fused multiply-add); the tail kernel's StoreSink keeps the
+// pieces and adds them later with the same operations in the same order, so
+// both round alike.
+template <typename C, typename Sink>
+__device__ __forceinline__ C add_term(const TermRec r, const uint8_t *v, const uint8_t *e, C ct, C cr,
+                                      const double2 *X, int bt, Sink &sink)
 {
     typedef typename real_of<C>::type Real;
     const int k = r.k;
     C mono;
     if (!(r.flags & TERM_POWERS)) {
-        // prefix products: P[j] = ct prod_{i<j} x_{v_i}
         C pre = ct;
-        st(P, 0, bt, pre);
+        if (k > 1) sink.put_prefix(0, pre);
         for (int j = 1; j < k; j++) {
             pre = cmul(pre, ld<C>(X, v[j - 1], bt));
-            st(P, j, bt, pre);
+            if (j < k - 1) sink.put_prefix(j, pre);
         }
-        // suffix products and the derivatives
         C suf = ld<C>(X, v[k - 1], bt);
-        st(Jrow, v[k - 1], bt, cadd(ld<C>(Jrow, v[k - 1], bt), pre));
+        sink.last(v[k - 1], pre);
         for (int j = k - 2; j >= 0; j--) {
-            st(Jrow, v[j], bt, cfma(ld<C>(P, j, bt), suf, ld<C>(Jrow, v[j], bt)));
+            sink.deriv(j, v[j], sink.get_prefix(j), suf);
             suf = cmul(suf, ld<C>(X, v[j], bt));
         }
         mono = suf;
     } else {
-        // common factor cf = prod_j x_{v_j}^{a_j - 1}
         C cf = {Real(1), Real(0)};
         for (int j = 0; j < k; j++) {
             const int a = e[j];
@@ -259,26 +263,43 @@ __device__ __forceinline__ C add_term(const TermRec r, const uint8_t *v, const u
                 cf = cmul(cf, pw);
             }
         }
-        // prefix products: P[j] = ct cf prod_{i<j} x_{v_i}
         C pre = cmul(ct, cf);
-        st(P, 0, bt, pre);
+        if (k > 1) sink.put_prefix(0, pre);
         for (int j = 1; j < k; j++) {
             pre = cmul(pre, ld<C>(X, v[j - 1], bt));
-            st(P, j, bt, pre);
+            if (j < k - 1) sink.put_prefix(j, pre);
         }
         C suf = ld<C>(X, v[k - 1], bt);
-        st(Jrow, v[k - 1], bt, cadd(ld<C>(Jrow, v[k - 1], bt), cscale((Real)e[k - 1], pre)));
+        sink.last(v[k - 1], cscale((Real)e[k - 1], pre));
         for (int j = k - 2; j >= 0; j--) {
-            const C pj = cscale((Real)e[j], ld<C>(P, j, bt));
-            st(Jrow, v[j], bt, cfma(pj, suf, ld<C>(Jrow, v[j], bt)));
+            sink.deriv(j, v[j], cscale((Real)e[j], sink.get_prefix(j)), suf);
             suf = cmul(suf, ld<C>(X, v[j], bt));
         }
-        // suf = prod_j x_{v_j}; the monomial is cf * suf
         mono = cmul(cf, suf);
     }
-    if (want_rhs) st(Rrow, 0, bt, cfma(cr, mono, ld<C>(Rrow, 0, bt)));
+    sink.rhs(cr, mono);
     return mono;
 }
+
+// Adds a term's pieces into row Jrow / Rrow of the thread (slot stride bt);
+// prefix products in P.
+template <typename C>
+struct AccumSink {
+    double2 *Jrow, *Rrow, *P;
+    int bt;
+    bool want_rhs;
+    __device__ __forceinline__ void put_prefix(int j, C p) { st(P, j, bt, p); }
+    __device__ __forceinline__ C get_prefix(int j) const { return ld<C>(P, j, bt); }
+    __device__ __forceinline__ void last(int col, C d) { st(Jrow, col, bt, cadd(ld<C>(Jrow, col, bt), d)); }
+    __device__ __forceinline__ void deriv(int, int col, C pj, C suf)
+    {
+        st(Jrow, col, bt, cfma(pj, suf, ld<C>(Jrow, col, bt)));
+    }
+    __device__ __forceinline__ void rhs(C cr, C mono)
+    {
+        if (want_rhs) st(Rrow, 0, bt, cfma(cr, mono, ld<C>(Rrow, 0, bt)));
+    }
+};
 
 // One pass over the terms at the thread's point X (slots of complex C):
 // J = H_x (row-major N x N) and, when want_rhs, R = H_t (dt) or H (!dt), for
@@ -315,8 +336,8 @@ __device__ __forceinline__ void evaluate(const C *C0, const C *C1, const SmTab &
             if (SCALE) SL(S, r.eq).x += abs1(ct);
             continue;
         }
-        const C mono = add_term<C>(r, tb.vars + r.off, tb.exps + r.off, ct, cr, want_rhs, X, J + r.eq * N * bt,
-                                   R + r.eq * bt, P, bt);
+        AccumSink<C> sink{J + r.eq * N * bt, R + r.eq * bt, P, bt, want_rhs};
+        const C mono = add_term<C>(r, tb.vars + r.off, tb.exps + r.off, ct, cr, X, bt, sink);
         if (SCALE) SL(S, r.eq).x += abs1(ct) * abs1(mono);
     }
 }

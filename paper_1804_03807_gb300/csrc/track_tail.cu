@@ -1,18 +1,26 @@
-// track_tail.cu -- the row-parallel tail kernel.
+// track_tail.cu -- the tail kernel: G threads per path.
 //
 // When most lanes of a tracking launch have run out of paths, the remaining
 // paths leave the one-thread-per-path kernel at the start of a step (see the
-// hand-off in track_impl.cuh) and continue here with G lanes per path: lane
-// r owns equation r -- its terms in the evaluation, row r of the Jacobian in
-// the LU and in the triangular solves.  A long path then no longer runs at the
-// speed of one thread sharing an FP64 pipe with a partly empty warp.
-//
+// hand-off in track_impl.cuh) and continue here with a group of G lanes per
+// path, so that a long path no longer runs at the speed of one thread that
+// shares an FP64 pipe with a mostly empty warp.  One evaluate+factor+solve
+// unit of a path:
+//   evaluation, phase A: the lanes take the terms (heaviest first) and run
+//     add_term into a StoreSink -- the prefix and suffix products and the
+//     coefficient of the right-hand side, kept in the group's term store;
+//   evaluation, phase B: the lanes take the entries of H_x and of the
+//     right-hand side (longest first) and add up each entry's pieces in the
+//     order of the table, with the operations AccumSink would have used;
+//   LU: one column at a time; pivot search by a butterfly arg-max (first row
+//     on ties, as the one-thread loop), the row swap by columns, the trailing
+//     update spread over all lanes;
+//   solves: lane r owns row r (forward over ascending, back substitution over
+//     descending columns, as lu_solve).
 // Every value is computed by exactly the operations, in exactly the order,
-// of the one-thread kernel (terms of a row in table order, one column
-// elimination at a time, forward substitution over ascending and back
-// substitution over descending columns), and the scalars of the step logic
-// are reduced with exact operations (max, and), so a path ends with the same
-// bits whichever kernel finishes it.
+// of the one-thread kernel, and the scalars of the step logic are reduced
+// with exact operations (max, and), so a path ends with the same bits
+// whichever kernel finishes it.
 #include "track_impl.cuh"
 
 namespace phc {
@@ -28,35 +36,134 @@ __device__ __forceinline__ double gmax(double v, unsigned mask)
     return v;
 }
 
+// add_term's pieces of one term, kept in the term's slots of the group's
+// store: (p_j, s_j) pairs for j = 0..k-2, then d, x^a and cr (2k + 1 slots).
+struct StoreSink {
+    double2 *s;
+    int k;
+    __device__ __forceinline__ void put_prefix(int j, double2 p) { s[2 * j] = p; }
+    __device__ __forceinline__ double2 get_prefix(int j) const { return s[2 * j]; }
+    __device__ __forceinline__ void last(int, double2 d) { s[2 * (k - 1)] = d; }
+    __device__ __forceinline__ void deriv(int j, int, double2 pj, double2 suf)
+    {
+        s[2 * j] = pj;
+        s[2 * j + 1] = suf;
+    }
+    __device__ __forceinline__ void rhs(double2 cr, double2 mono)
+    {
+        s[2 * k - 1] = mono;
+        s[2 * k] = cr;
+    }
+};
+
+// Contributions to an entry of H_x or of the right-hand side: slot | kind << 14.
+enum : uint16_t { PIECE_FMA = 0, PIECE_ADD = 1, PIECE_RHS = 2 };
+
+// Per-block plan of the two evaluation phases, built from the staged table:
+// the term store layout, the order in which lanes take terms and entries,
+// and each entry's pieces in table order.  Sizes in tail_plan_bytes.
+struct TailPlan {
+    uint16_t *tslot;   // [T] first store slot of term q
+    uint16_t *torder;  // [T] terms, largest support first
+    uint16_t *eoff;    // [E + 1] pieces of entry e: elist[eoff[e] .. eoff[e + 1])
+    uint16_t *elist;   // [n_ve + T]
+    uint16_t *eorder;  // [E] entries, most pieces first
+};
+
+__host__ __device__ inline size_t tail_plan_bytes(int n, int T, int n_ve)
+{
+    const int E = n * n + n;
+    const size_t b = 2 * ((size_t)T + T + (E + 1) + (n_ve + T) + E);
+    return (b + 15) & ~(size_t)15;
+}
+
+// Store slots of one path: 2k + 1 per term with k >= 1, 1 per constant.
+__host__ __device__ inline int tail_store_slots(int T, int n_ve) { return 2 * n_ve + T; }
+
+template <int N>
+static __device__ TailPlan build_plan(const SmTab &tb, char *region)
+{
+    constexpr int E = N * N + N;
+    const int T = tb.n_terms;
+    TailPlan p;
+    p.tslot = reinterpret_cast<uint16_t *>(region);
+    p.torder = p.tslot + T;
+    p.eoff = p.torder + T;
+    p.elist = p.eoff + (E + 1);
+    int n_pieces = 0;
+    for (int q = 0; q < T; q++) n_pieces += tb.terms[q].k + 1;
+    p.eorder = p.elist + n_pieces;
+    if (threadIdx.x == 0) {
+        uint16_t *cnt = p.eorder;  // scratch: E counters, then the entry order
+        int slot = 0, kmax = 0;
+        for (int e = 0; e < E; e++) cnt[e] = 0;
+        for (int q = 0; q < T; q++) {
+            const TermRec r = tb.terms[q];
+            p.tslot[q] = (uint16_t)slot;
+            slot += r.k ? 2 * r.k + 1 : 1;
+            kmax = r.k > kmax ? r.k : kmax;
+            for (int j = 0; j < r.k; j++) cnt[r.eq * N + tb.vars[r.off + j]]++;
+            cnt[N * N + r.eq]++;
+        }
+        // terms by decreasing support size (stable)
+        int w = 0;
+        for (int k = kmax; k >= 0; k--)
+            for (int q = 0; q < T; q++)
+                if (tb.terms[q].k == k) p.torder[w++] = (uint16_t)q;
+        int acc = 0, lmax = 0;
+        for (int e = 0; e < E; e++) {
+            p.eoff[e] = (uint16_t)acc;
+            acc += cnt[e];
+            lmax = cnt[e] > lmax ? cnt[e] : lmax;
+            cnt[e] = 0;
+        }
+        p.eoff[E] = (uint16_t)acc;
+        // pieces in table order; within a term the columns in the order add_term emits them
+        for (int q = 0; q < T; q++) {
+            const TermRec r = tb.terms[q];
+            const int b = p.tslot[q], k = r.k;
+            if (k) {
+                for (int j = k - 1; j >= 0; j--) {
+                    const int e = r.eq * N + tb.vars[r.off + j];
+                    const uint16_t v = (j == k - 1) ? (uint16_t)((b + 2 * (k - 1)) | (PIECE_ADD << 14))
+                                                    : (uint16_t)((b + 2 * j) | (PIECE_FMA << 14));
+                    p.elist[p.eoff[e] + cnt[e]++] = v;
+                }
+                const int e = N * N + r.eq;
+                p.elist[p.eoff[e] + cnt[e]++] = (uint16_t)((b + 2 * k - 1) | (PIECE_RHS << 14));
+            } else {
+                const int e = N * N + r.eq;
+                p.elist[p.eoff[e] + cnt[e]++] = (uint16_t)(b | (PIECE_ADD << 14));
+            }
+        }
+        // entries by decreasing number of pieces (overwrites the counters)
+        w = 0;
+        for (int l = lmax; l >= 0; l--)
+            for (int e = 0; e < E; e++)
+                if (p.eoff[e + 1] - p.eoff[e] == l) p.eorder[w++] = (uint16_t)e;
+    }
+    __syncthreads();
+    return p;
+}
+
 template <int N, int G>
-__global__ void __launch_bounds__(128) tail_kernel(const TrackLaunch L, size_t table_bytes)
+__global__ void __launch_bounds__(128) tail_kernel(const TrackLaunch L, size_t table_bytes, size_t plan_bytes)
 {
     extern __shared__ __align__(16) char smem[];
     const SmTab tb = stage_table(L.tab, smem);
-    // The terms of equation i are tb.terms[rs[i] .. rs[i + 1]) (tables are
-    // grouped by equation in ascending order); mt = most terms of one row.
-    __shared__ int rs[PHC_MAX_VARS + 1], mt;
-    if (threadIdx.x == 0) {
-        int q = 0, m = 0;
-        for (int i = 0; i < N; i++) {
-            rs[i] = q;
-            while (q < tb.n_terms && tb.terms[q].eq == i) q++;
-            m = (q - rs[i] > m) ? q - rs[i] : m;
-        }
-        rs[N] = q;
-        mt = m;
-    }
-    __syncthreads();
+    const TailPlan plan = build_plan<N>(tb, smem + table_bytes);
+    constexpr int E = N * N + N;
+    const int T = tb.n_terms;
+    const int S = tail_store_slots(T, L.tab.n_ve);
     const int lane = threadIdx.x & 31;
-    const int r = lane % G;  // the equation / row this lane owns (r < N)
+    const int r = lane % G;  // the row this lane owns in the LU and the solves (r < N)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - r));
     const int group = threadIdx.x / G;
-    constexpr int SLOTS = 2 * N + N * N + G * N;
-    double2 *base = reinterpret_cast<double2 *>(smem + table_bytes) + (size_t)group * SLOTS;
+    double2 *base = reinterpret_cast<double2 *>(smem + table_bytes + plan_bytes) + (size_t)group * (2 * N + N * N + S);
     double2 *xe = base;          // [N]
     double2 *R = base + N;       // [N]
     double2 *J = base + 2 * N;   // [N][N]
-    double2 *P = base + 2 * N + N * N + r * N;  // this lane's prefix products
+    double2 *store = base + 2 * N + N * N;  // [S] add_term pieces of every term
     const phc_opts &o = L.o;
     const int64_t np = L.n_paths;
     const bool own = r < N;
@@ -97,30 +204,37 @@ __global__ void __launch_bounds__(128) tail_kernel(const TrackLaunch L, size_t t
         int stop = -1;
         for (;;) {
             __syncwarp(gmask);
-            // ---------------------------------------------- evaluate row r (as evaluate<N, double2>, same add_term)
+            // ---------------------------------------------- evaluation, phase A: the terms' pieces
             const bool dt = phase < 4;
-            if (own) {
-                const double2 zero = make_double2(0.0, 0.0);
-                R[r] = zero;
-#pragma unroll
-                for (int j = 0; j < N; j++) J[r * N + j] = zero;
-                // the terms of equation r, in table order; the lanes of a
-                // group step through their rows together (term i of every row)
-                const int q0 = rs[r], q1 = rs[r + 1];
-                for (int i = 0; i < mt; i++) {
-                    const int qq = q0 + i;
-                    if (qq >= q1) continue;
-                    const TermRec rec = tb.terms[qq];
-                    const double2 c0 = C0[qq], c1 = C1[qq];
-                    const double2 ct = make_double2(fma(te, c1.x, c0.x), fma(te, c1.y, c0.y));
-                    const double2 cr = dt ? c1 : ct;
-                    if (rec.k == 0) {
-                        R[r] = cadd(R[r], cr);
-                        continue;
-                    }
-                    add_term<double2>(rec, tb.vars + rec.off, tb.exps + rec.off, ct, cr, true, xe, J + r * N, R + r,
-                                      P, 1);
+            for (int i = r; i < T; i += G) {
+                const int qq = plan.torder[i];
+                const TermRec rec = tb.terms[qq];
+                const double2 c0 = C0[qq], c1 = C1[qq];
+                const double2 ct = make_double2(fma(te, c1.x, c0.x), fma(te, c1.y, c0.y));
+                const double2 cr = dt ? c1 : ct;
+                double2 *ts = store + plan.tslot[qq];
+                if (rec.k == 0) {
+                    ts[0] = cr;
+                } else {
+                    StoreSink sink{ts, rec.k};
+                    add_term<double2>(rec, tb.vars + rec.off, tb.exps + rec.off, ct, cr, xe, 1, sink);
                 }
+            }
+            __syncwarp(gmask);
+            // ---------------------------------------------- evaluation, phase B: the entries, pieces in table order
+            for (int i = r; i < E; i += G) {
+                const int e = plan.eorder[i];
+                double2 a = make_double2(0.0, 0.0);
+                for (int m = plan.eoff[e]; m < plan.eoff[e + 1]; m++) {
+                    const uint16_t w = plan.elist[m];
+                    const double2 *pc = store + (w & 0x3fff);
+                    const int kind = w >> 14;
+                    if (kind == PIECE_FMA) a = cfma(pc[0], pc[1], a);
+                    else if (kind == PIECE_ADD) a = cadd(a, pc[0]);
+                    else a = cfma(pc[1], pc[0], a);
+                }
+                if (e < N * N) J[e] = a;
+                else R[e - N * N] = a;
             }
             __syncwarp(gmask);
             // ---------------------------------------------- LU (as lu_factor<N, double2>)
@@ -163,11 +277,15 @@ __global__ void __launch_bounds__(128) tail_kernel(const TrackLaunch L, size_t t
                 const double2 inv = recip(J[k * N + k]);
                 __syncwarp(gmask);
                 if (r == k) J[k * N + k] = inv;
-                if (own && r > k) {
-                    const double2 l = cmul(J[r * N + k], inv);
-                    J[r * N + k] = l;
-#pragma unroll
-                    for (int j = k + 1; j < N; j++) J[r * N + j] = cfms(J[r * N + j], l, J[k * N + j]);
+                if (own && r > k) J[r * N + k] = cmul(J[r * N + k], inv);
+                __syncwarp(gmask);
+                // trailing update J[i][j] -= l_i J[k][j], i, j > k, spread over the group
+                const int M = N - 1 - k;
+                if (M > 0) {
+                    for (int m = r; m < M * M; m += G) {
+                        const int i = k + 1 + m / M, j = k + 1 + m % M;
+                        J[i * N + j] = cfms(J[i * N + j], J[i * N + k], J[k * N + j]);
+                    }
                 }
                 __syncwarp(gmask);
             }
@@ -331,6 +449,7 @@ __global__ void __launch_bounds__(128) tail_kernel(const TrackLaunch L, size_t t
             rec.grew = grew;
             rec.system = sys;
             L.stats[q] = rec;
+            atomicAdd(L.tail_units, (unsigned long long)(n_solve - hd.n_solve));
         }
         __syncwarp(gmask);
     }
@@ -340,10 +459,19 @@ template <int N, int G>
 static cudaError_t launch_tail_n(const TrackLaunch &L_in, int max_blocks, cudaStream_t s)
 {
     TrackLaunch L = L_in;
-    L.tab.coef_smem = 1;  // this kernel's shared memory is small
-    const size_t tb = table_smem_bytes(L.tab);
-    const int bt = 128;
-    const size_t smem = tb + (size_t)(bt / G) * (2 * N + N * N + G * N) * sizeof(double2);
+    L.tab.coef_smem = 1;
+    size_t tb = table_smem_bytes(L.tab);
+    const size_t pb = tail_plan_bytes(N, L.tab.n_terms, L.tab.n_ve);
+    const size_t per_group = (size_t)(2 * N + N * N + tail_store_slots(L.tab.n_terms, L.tab.n_ve)) * sizeof(double2);
+    int groups = 128 / G;
+    if (tb + pb + groups * per_group > (size_t)g_smem_optin) {
+        L.tab.coef_smem = 0;  // coefficients through L1
+        tb = table_smem_bytes(L.tab);
+    }
+    while (groups > 1 && tb + pb + groups * per_group > (size_t)g_smem_optin) groups /= 2;
+    const size_t smem = tb + pb + groups * per_group;
+    if (smem > (size_t)g_smem_optin) return cudaErrorInvalidConfiguration;
+    const int bt = groups * G;
     cudaError_t e = cudaFuncSetAttribute(tail_kernel<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -352,28 +480,51 @@ static cudaError_t launch_tail_n(const TrackLaunch &L_in, int max_blocks, cudaSt
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = g_num_sms * per_sm;
     if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
-    tail_kernel<N, G><<<grid, bt, smem, s>>>(L, tb);
+    tail_kernel<N, G><<<grid, bt, smem, s>>>(L, tb, pb);
     return cudaGetLastError();
 }
+
+bool tail_supported(const DevTables &t)
+{
+    device_limits();
+    const int n = t.n;
+    if (n < 1 || n > PHC_MAX_VARS) return false;
+    const int S = tail_store_slots(t.n_terms, t.n_ve);
+    if (S >= (1 << 14)) return false;  // slot numbers are 14-bit
+    DevTables u = t;
+    u.coef_smem = 0;
+    const size_t need = table_smem_bytes(u) + tail_plan_bytes(n, t.n_terms, t.n_ve) +
+                        (size_t)(2 * n + n * n + S) * sizeof(double2);
+    return need <= (size_t)g_smem_optin;
+}
+
+// opts.tail_threads picks G: 8 (N <= 8 only), 16 or 32; 0 = 32.
+#define PHC_TAIL_CASE(NN)                                                                                             \
+    case NN:                                                                                                          \
+        if (group == 8 && (NN) <= 8) return launch_tail_n<NN, ((NN) <= 8 ? 8 : 16)>(L, max_blocks, s);              \
+        if (group == 16) return launch_tail_n<NN, 16>(L, max_blocks, s);                                             \
+        return launch_tail_n<NN, 32>(L, max_blocks, s);
 
 cudaError_t launch_tail(const TrackLaunch &L, int max_blocks, cudaStream_t s)
 {
     device_limits();
+    const int group = L.o.tail_threads;
     switch (L.tab.n) {
-    case 1: return launch_tail_n<1, 8>(L, max_blocks, s);
-    case 2: return launch_tail_n<2, 8>(L, max_blocks, s);
-    case 3: return launch_tail_n<3, 8>(L, max_blocks, s);
-    case 4: return launch_tail_n<4, 8>(L, max_blocks, s);
-    case 5: return launch_tail_n<5, 8>(L, max_blocks, s);
-    case 6: return launch_tail_n<6, 8>(L, max_blocks, s);
-    case 7: return launch_tail_n<7, 8>(L, max_blocks, s);
-    case 8: return launch_tail_n<8, 8>(L, max_blocks, s);
-    case 9: return launch_tail_n<9, 16>(L, max_blocks, s);
-    case 10: return launch_tail_n<10, 16>(L, max_blocks, s);
-    case 11: return launch_tail_n<11, 16>(L, max_blocks, s);
-    case 12: return launch_tail_n<12, 16>(L, max_blocks, s);
+        PHC_TAIL_CASE(1)
+        PHC_TAIL_CASE(2)
+        PHC_TAIL_CASE(3)
+        PHC_TAIL_CASE(4)
+        PHC_TAIL_CASE(5)
+        PHC_TAIL_CASE(6)
+        PHC_TAIL_CASE(7)
+        PHC_TAIL_CASE(8)
+        PHC_TAIL_CASE(9)
+        PHC_TAIL_CASE(10)
+        PHC_TAIL_CASE(11)
+        PHC_TAIL_CASE(12)
     default: return cudaErrorInvalidValue;
     }
 }
+#undef PHC_TAIL_CASE
 
 }  // namespace phc

@@ -5,9 +5,10 @@ that are still running move, at the start of their next step, to a kernel
 that gives every path one thread per equation (opts.tail_drain).  That
 kernel performs the same floating point operations in the same order, so
 endpoints, classes and every per-path statistic must be identical, bit for
-bit, to a run without the hand-off.  Each case runs three ways: hand-off
-off; the default; and a one-block grid with a drain fraction so small that
-nearly every path is handed off after its first step.
+bit, to a run without the hand-off.  Each case runs with the hand-off off;
+with the default; and, for every group size of the tail kernel, on a
+one-block grid with a drain fraction so small that nearly every path is
+handed off after its first step.
 """
 import numpy as np
 import pytest
@@ -18,9 +19,10 @@ from workloads import configs, cyclic, embedding_constants, multistep_example, r
 pytestmark = pytest.mark.gpu
 
 
-def _opts(drain, tiny_grid=False):
+def _opts(drain, tiny_grid=False, group=0):
     o = P.phc_default_opts()
     o.tail_drain = drain
+    o.tail_threads = group
     if tiny_grid:
         o.block_threads = 32
         o.max_blocks = 1
@@ -41,14 +43,18 @@ def _same(a, b, label):
 
 
 def _three_ways(run, h):
+    """Hand-off off, default, and forced with each group size the kernel has
+    for this number of unknowns; returns the results and the fewest paths moved."""
     base = _host(run(_opts(0.0)))
     assert P.phc_tail_paths(h) == 0
-    dflt = _host(run(_opts(0.7)))
-    forced = _host(run(_opts(1e-9, tiny_grid=True)))
-    moved = P.phc_tail_paths(h)
+    dflt = _host(run(_opts(0.85)))
     _same(base, dflt, "default drain")
-    _same(base, forced, "forced hand-off")
-    return base, moved
+    moved = []
+    for group in ([8] if h.n <= 8 else []) + [16, 32]:
+        forced = _host(run(_opts(1e-9, tiny_grid=True, group=group)))
+        moved.append(P.phc_tail_paths(h))
+        _same(base, forced, f"forced hand-off, {group} threads per path")
+    return base, min(moved)
 
 
 @pytest.mark.parametrize("case", ["dense4", "cyclic5", "ragged27", "dense9", "dense10"])
