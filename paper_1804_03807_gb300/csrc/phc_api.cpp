@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -627,6 +628,7 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
         std::vector<phc::SysDesc> descs;
         std::vector<int64_t> prefix(1, 0);
         int wtb = 0;
+        phc::TailMultiSizes tz{0, 0, 0, 0};
         for (int i = 0; i < n_h; i++) {
             phc_homotopy *h = hs[i];
             if (h->n != n || h->num_paths == 0) continue;
@@ -650,6 +652,12 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
             prefix.push_back(prefix.back() + h->num_paths);
             const int b = (int)phc::warp_table_bytes(d.tab.n_terms, d.tab.n_ve, d.tab.f32);
             if (b > wtb) wtb = b;
+            // the multi-system tail kernel's per-warp region (double precision tables)
+            const int T = d.tab.n_terms, V = d.tab.n_ve, S = phc::tail_store_slots(T, V);
+            tz.table_cap = std::max(tz.table_cap, phc::warp_table_bytes(T, V, false));
+            tz.plan_cap = std::max(tz.plan_cap, phc::tail_plan_bytes(n, T, V));
+            tz.group_slots = std::max(tz.group_slots, phc::tail_group_slots(n, S));
+            tz.max_store = std::max(tz.max_store, S);
         }
         if (descs.empty()) continue;
         cudaStream_t hs_st;
@@ -664,7 +672,18 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
         }
         CU(cudaStreamWaitEvent(hs_st, fork_ev, 0));
         const int m = (int)descs.size();
-        const size_t bytes = m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long) + (m + 1) * sizeof(int64_t);
+        phc::TrackLaunch L{};
+        L.n_paths = prefix.back();
+        L.o = o;
+        L.n_multi = m;
+        L.warp_table_bytes = wtb;
+        // tail hand-off (double precision): buffer for one record per lane
+        const bool tail =
+            o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64 && phc::tail_multi_supported(tz);
+        const int64_t lanes = tail ? phc::multi_lanes(L, n, o.block_threads, o.max_blocks) : 0;
+        const size_t head = m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long) + (m + 1) * sizeof(int64_t);
+        const size_t hoff = (head + 255) & ~(size_t)255;
+        const size_t bytes = hoff + (lanes > 0 ? 8 * sizeof(unsigned long long) + lanes * sizeof(phc::Handoff) : 0);
         void *blob = nullptr;
         CU(cudaMallocAsync(&blob, bytes, hs_st));
         char *b = static_cast<char *>(blob);
@@ -674,17 +693,24 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
         CU(cudaMemcpyAsync(d_desc, descs.data(), m * sizeof(phc::SysDesc), cudaMemcpyHostToDevice, hs_st));
         CU(cudaMemsetAsync(d_q, 0, m * sizeof(unsigned long long), hs_st));
         CU(cudaMemcpyAsync(d_pre, prefix.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, hs_st));
-        // the host vectors must outlive the copies from pageable memory
-        CU(cudaStreamSynchronize(hs_st));
-        phc::TrackLaunch L{};
-        L.n_paths = prefix.back();
-        L.o = o;
         L.multi = d_desc;
         L.multi_q = d_q;
         L.multi_prefix = d_pre;
-        L.n_multi = m;
-        L.warp_table_bytes = wtb;
+        if (lanes > 0) {
+            unsigned long long *c = reinterpret_cast<unsigned long long *>(b + hoff);
+            CU(cudaMemsetAsync(c, 0, 8 * sizeof(unsigned long long), hs_st));
+            L.handoff_n = c;
+            L.idle_n = c + 1;
+            L.tail_q = c + 2;
+            L.tail_units = c + 3;
+            L.multi_claimed = c + 4;
+            L.handoff = reinterpret_cast<phc::Handoff *>(c + 8);
+            L.drain_frac = o.tail_drain;
+        }
+        // the host vectors must outlive the copies from pageable memory
+        CU(cudaStreamSynchronize(hs_st));
         cudaError_t e = phc::launch_multi(L, n, o.block_threads, o.max_blocks, hs_st);
+        if (e == cudaSuccess && lanes > 0) e = phc::launch_tail_multi(L, n, tz, o.max_blocks, hs_st);
         cudaFreeAsync(blob, hs_st);
         if (e != cudaSuccess) return fail(PHC_ECUDA, "multi-system kernel launch (n = %d): %s", n,
                                           cudaGetErrorString(e));

@@ -144,6 +144,7 @@ struct TrackLaunch {
     unsigned long long *idle_n;
     unsigned long long *tail_q;
     unsigned long long *tail_units;  // units the tail kernel ran (diagnostic)
+    unsigned long long *multi_claimed;  // multi-system: paths claimed over all systems
     unsigned long long drain_at;  // set by the launcher from drain_frac
     double drain_frac;            // fraction of idle lanes that starts the hand-off; 0: never
 };
@@ -190,6 +191,36 @@ int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks);
 // per path; tail_supported: the tail kernel can hold one path of this table.
 cudaError_t launch_tail(const TrackLaunch &L, int max_blocks, cudaStream_t s);
 bool tail_supported(const DevTables &t);
+
+// Shared memory of the tail kernels (see track_tail.cu): the evaluation plan
+// of a table (term slots and orders, each entry's pieces; 16-bit words) ...
+inline size_t tail_plan_bytes(int n, int T, int n_ve)
+{
+    const int E = n * n + n;
+    const size_t b = 2 * ((size_t)T + T + (E + 1) + (n_ve + T) + E);
+    return (b + 15) & ~(size_t)15;
+}
+// ... the term store of one path (2k + 1 slots per term with k >= 1, 1 per
+// constant) ...
+__host__ __device__ inline int tail_store_slots(int T, int n_ve) { return 2 * n_ve + T; }
+// ... and a group's slots: xe, R (N each), J (N^2) and the store, which also
+// holds the one-lane classification arrays of the multi-system tail.
+__host__ __device__ inline int tail_group_slots(int n, int S)
+{
+    const int cls = n * n + 5 * n;
+    return 2 * n + n * n + (S > cls ? S : cls);
+}
+// Per-warp region of the multi-system tail kernel: the largest table, plan
+// and group over the systems of the launch.
+struct TailMultiSizes {
+    size_t table_cap, plan_cap;
+    int group_slots, max_store;
+};
+// The paths handed off by a multi-system launch (one warp per path).
+cudaError_t launch_tail_multi(const TrackLaunch &L, int n, const TailMultiSizes &z, int max_blocks, cudaStream_t s);
+bool tail_multi_supported(const TailMultiSizes &z);
+// Lanes a multi-system launch of L runs (for sizing its hand-off buffer).
+int64_t multi_lanes(const TrackLaunch &L, int n, int block_threads, int max_blocks);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,

@@ -96,18 +96,18 @@ int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks)
     const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
     if (bt == 0) return -1;
     switch (L.tab.n) {
-    case 1: return lanes_n<1>(L, bt, max_blocks);
-    case 2: return lanes_n<2>(L, bt, max_blocks);
-    case 3: return lanes_n<3>(L, bt, max_blocks);
-    case 4: return lanes_n<4>(L, bt, max_blocks);
-    case 5: return lanes_n<5>(L, bt, max_blocks);
-    case 6: return lanes_n<6>(L, bt, max_blocks);
-    case 7: return lanes_n<7>(L, bt, max_blocks);
-    case 8: return lanes_n<8>(L, bt, max_blocks);
-    case 9: return lanes_n<9>(L, bt, max_blocks);
-    case 10: return lanes_n<10>(L, bt, max_blocks);
-    case 11: return lanes_n<11>(L, bt, max_blocks);
-    case 12: return lanes_n<12>(L, bt, max_blocks);
+    case 1: return lanes_n<1, MODE_SINGLE>(L, bt, max_blocks);
+    case 2: return lanes_n<2, MODE_SINGLE>(L, bt, max_blocks);
+    case 3: return lanes_n<3, MODE_SINGLE>(L, bt, max_blocks);
+    case 4: return lanes_n<4, MODE_SINGLE>(L, bt, max_blocks);
+    case 5: return lanes_n<5, MODE_SINGLE>(L, bt, max_blocks);
+    case 6: return lanes_n<6, MODE_SINGLE>(L, bt, max_blocks);
+    case 7: return lanes_n<7, MODE_SINGLE>(L, bt, max_blocks);
+    case 8: return lanes_n<8, MODE_SINGLE>(L, bt, max_blocks);
+    case 9: return lanes_n<9, MODE_SINGLE>(L, bt, max_blocks);
+    case 10: return lanes_n<10, MODE_SINGLE>(L, bt, max_blocks);
+    case 11: return lanes_n<11, MODE_SINGLE>(L, bt, max_blocks);
+    case 12: return lanes_n<12, MODE_SINGLE>(L, bt, max_blocks);
     default: return -1;
     }
 }

@@ -624,6 +624,17 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
     int n_acc = 0, n_rej = 0, n_newt = 0, n_solve = 0, n_f32 = 0;
     bool use32 = false, fp32_off = false;  // fp32_off: the path fell back to double for good
     bool fresh = false;                    // x0 holds a new start point
+    bool counted = false;                  // multi-system: this lane is in idle_n
+    const unsigned long long multi_total = MULTI ? (unsigned long long)L.multi_prefix[L.n_multi] : 0ull;
+    // multi-system: once every path of every system is claimed, an idle lane
+    // stays idle; it counts itself once towards the tail hand-off
+    auto count_idle = [&]() {
+        if (MULTI && L.drain_at && !counted &&
+            *reinterpret_cast<volatile unsigned long long *>(L.multi_claimed) >= multi_total) {
+            atomicAdd(L.idle_n, 1ull);
+            counted = true;
+        }
+    };
 
     // start a new step from the accepted point x0
     auto begin_step = [&]() {
@@ -654,6 +665,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 const SysDesc &d = L.multi[ws];
                 const unsigned long long c = atomicAdd(&L.multi_q[ws], 1ull);
                 if (c < (unsigned long long)d.n_paths) {
+                    if (L.drain_at) atomicAdd(L.multi_claimed, 1ull);
                     q = (int64_t)c;
                     int64_t pid = q;
 #pragma unroll
@@ -669,6 +681,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                     exhausted = true;
                 }
             }
+            if (q < 0) count_idle();
             if (__all_sync(FULL, q < 0)) {
                 int next = -1;
                 if (lane == 0) {
@@ -682,7 +695,10 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                     }
                 }
                 next = __shfl_sync(FULL, next, 0);
-                if (next < 0) break;
+                if (next < 0) {
+                    if (L.drain_at && !counted) atomicAdd(L.idle_n, 1ull);
+                    break;
+                }
                 __syncwarp();
                 ws = next;
                 tb = stage_table_warp(L.multi[ws].tab, wregion);
@@ -910,10 +926,10 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             if (stop < 0 && ++since_ck >= o.max_steps_decade) stop = PHC_STOP_BUDGET;
             if (stop < 0) begin_step();
         }
-        if constexpr (MODE == MODE_SINGLE) {
+        if constexpr (MODE == MODE_SINGLE || MODE == MODE_MULTI) {
             // most lanes are idle: a path that starts a new step moves to
-            // the row-parallel tail kernel (which repeats this arithmetic
-            // exactly, so where a path is finished does not change it)
+            // the tail kernel (which repeats this arithmetic exactly, so
+            // where a path is finished does not change it)
             if (stop < 0 && act != ACT_NONE && phase == 0 && L.drain_at &&
                 *reinterpret_cast<volatile unsigned long long *>(L.idle_n) >= L.drain_at) {
                 Handoff &hd = L.handoff[atomicAdd(L.handoff_n, 1ull)];
@@ -928,7 +944,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 hd.r3 = r3;
                 hd.r4 = r4;
                 hd.q = q;
-                hd.sys = sys;
+                hd.sys = MULTI ? ws : sys;
                 hd.streak = streak;
                 hd.steps = steps;
                 hd.since_ck = since_ck;
@@ -938,7 +954,17 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 hd.n_newt = n_newt;
                 hd.n_solve = n_solve;
                 hd.n_f32 = n_f32;
-                break;
+                if constexpr (MULTI) {
+                    // the lane stays in the warp's claim loop, idle
+                    q = -1;
+                    if (!counted) {
+                        atomicAdd(L.idle_n, 1ull);
+                        counted = true;
+                    }
+                    continue;
+                } else {
+                    break;
+                }
             }
         }
         if (stop < 0) continue;
@@ -1015,17 +1041,19 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 
 // ------------------------------------------------------------------ launch helper
 
-// Lanes (grid x block) launch_track_n launches in mode 0 for L.
-template <int N>
+// Lanes (grid x block) launch_track_n launches in mode MODE for L (with
+// block size bt): the same shared memory and grid arithmetic.
+template <int N, int MODE>
 static int64_t lanes_n(const TrackLaunch &L, int bt, int max_blocks)
 {
-    const size_t smem = table_smem_bytes(L.tab) +
-                        (size_t)bt * thread_smem_bytes(N, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
-    if (cudaFuncSetAttribute(track_kernel<N, MODE_SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    const bool f32 = L.o.precision == PHC_PREC_FP32_INTERIOR;
+    const size_t tb = MODE == MODE_MULTI ? (size_t)(bt / 32) * (size_t)L.warp_table_bytes : table_smem_bytes(L.tab);
+    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32);
+    if (cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<N, MODE_SINGLE>, bt, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<N, MODE>, bt, smem) != cudaSuccess)
         return -1;
     int64_t want = (L.n_paths + bt - 1) / bt;
     int64_t grid = (int64_t)g_num_sms * per_sm;
@@ -1061,7 +1089,7 @@ static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_block
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
     L.drain_at = 0;
-    if (MODE == MODE_SINGLE && L.drain_frac > 0.0 && L.handoff) {
+    if ((MODE == MODE_SINGLE || MODE == MODE_MULTI) && L.drain_frac > 0.0 && L.handoff) {
         const unsigned long long at = (unsigned long long)(L.drain_frac * (double)(grid * bt));
         L.drain_at = at < 1 ? 1 : at;
     }

@@ -70,18 +70,9 @@ struct TailPlan {
     uint16_t *eorder;  // [E] entries, most pieces first
 };
 
-__host__ __device__ inline size_t tail_plan_bytes(int n, int T, int n_ve)
-{
-    const int E = n * n + n;
-    const size_t b = 2 * ((size_t)T + T + (E + 1) + (n_ve + T) + E);
-    return (b + 15) & ~(size_t)15;
-}
-
-// Store slots of one path: 2k + 1 per term with k >= 1, 1 per constant.
-__host__ __device__ inline int tail_store_slots(int T, int n_ve) { return 2 * n_ve + T; }
 
 template <int N>
-static __device__ TailPlan build_plan(const SmTab &tb, char *region)
+static __device__ TailPlan plan_layout(const SmTab &tb, char *region)
 {
     constexpr int E = N * N + N;
     const int T = tb.n_terms;
@@ -93,57 +84,354 @@ static __device__ TailPlan build_plan(const SmTab &tb, char *region)
     int n_pieces = 0;
     for (int q = 0; q < T; q++) n_pieces += tb.terms[q].k + 1;
     p.eorder = p.elist + n_pieces;
-    if (threadIdx.x == 0) {
-        uint16_t *cnt = p.eorder;  // scratch: E counters, then the entry order
-        int slot = 0, kmax = 0;
-        for (int e = 0; e < E; e++) cnt[e] = 0;
-        for (int q = 0; q < T; q++) {
-            const TermRec r = tb.terms[q];
-            p.tslot[q] = (uint16_t)slot;
-            slot += r.k ? 2 * r.k + 1 : 1;
-            kmax = r.k > kmax ? r.k : kmax;
-            for (int j = 0; j < r.k; j++) cnt[r.eq * N + tb.vars[r.off + j]]++;
-            cnt[N * N + r.eq]++;
+    return p;
+}
+
+// Fills the plan (one thread; the caller synchronises).
+template <int N>
+static __device__ void plan_fill(const SmTab &tb, const TailPlan &p)
+{
+    constexpr int E = N * N + N;
+    const int T = tb.n_terms;
+    uint16_t *cnt = p.eorder;  // scratch: E counters, then the entry order
+    int slot = 0, kmax = 0;
+    for (int e = 0; e < E; e++) cnt[e] = 0;
+    for (int q = 0; q < T; q++) {
+        const TermRec r = tb.terms[q];
+        p.tslot[q] = (uint16_t)slot;
+        slot += r.k ? 2 * r.k + 1 : 1;
+        kmax = r.k > kmax ? r.k : kmax;
+        for (int j = 0; j < r.k; j++) cnt[r.eq * N + tb.vars[r.off + j]]++;
+        cnt[N * N + r.eq]++;
+    }
+    // terms by decreasing support size (stable)
+    int w = 0;
+    for (int k = kmax; k >= 0; k--)
+        for (int q = 0; q < T; q++)
+            if (tb.terms[q].k == k) p.torder[w++] = (uint16_t)q;
+    int acc = 0, lmax = 0;
+    for (int e = 0; e < E; e++) {
+        p.eoff[e] = (uint16_t)acc;
+        acc += cnt[e];
+        lmax = cnt[e] > lmax ? cnt[e] : lmax;
+        cnt[e] = 0;
+    }
+    p.eoff[E] = (uint16_t)acc;
+    // pieces in table order; within a term the columns in the order add_term emits them
+    for (int q = 0; q < T; q++) {
+        const TermRec r = tb.terms[q];
+        const int b = p.tslot[q], k = r.k;
+        if (k) {
+            for (int j = k - 1; j >= 0; j--) {
+                const int e = r.eq * N + tb.vars[r.off + j];
+                const uint16_t v = (j == k - 1) ? (uint16_t)((b + 2 * (k - 1)) | (PIECE_ADD << 14))
+                                                : (uint16_t)((b + 2 * j) | (PIECE_FMA << 14));
+                p.elist[p.eoff[e] + cnt[e]++] = v;
+            }
+            const int e = N * N + r.eq;
+            p.elist[p.eoff[e] + cnt[e]++] = (uint16_t)((b + 2 * k - 1) | (PIECE_RHS << 14));
+        } else {
+            const int e = N * N + r.eq;
+            p.elist[p.eoff[e] + cnt[e]++] = (uint16_t)(b | (PIECE_ADD << 14));
         }
-        // terms by decreasing support size (stable)
-        int w = 0;
-        for (int k = kmax; k >= 0; k--)
-            for (int q = 0; q < T; q++)
-                if (tb.terms[q].k == k) p.torder[w++] = (uint16_t)q;
-        int acc = 0, lmax = 0;
-        for (int e = 0; e < E; e++) {
-            p.eoff[e] = (uint16_t)acc;
-            acc += cnt[e];
-            lmax = cnt[e] > lmax ? cnt[e] : lmax;
-            cnt[e] = 0;
+    }
+    // entries by decreasing number of pieces (overwrites the counters)
+    w = 0;
+    for (int l = lmax; l >= 0; l--)
+        for (int e = 0; e < E; e++)
+            if (p.eoff[e + 1] - p.eoff[e] == l) p.eorder[w++] = (uint16_t)e;
+}
+
+
+// Tracks one handed-off path to its end with the G lanes of a group (base:
+// the group's slots; coef_sys: the coefficient set of a batch table).  At
+// the end every lane calls finish(x0r, rec, units): lane r < N holds x_r,
+// lane 0 the statistics record, units = the units run here.
+template <int N, int G, typename Finish>
+__device__ __forceinline__ void tail_path(const Handoff &hd, const SmTab &tb, const TailPlan &plan, int coef_sys,
+                                          double2 *base, const phc_opts &o, int r, unsigned gmask, Finish &&finish)
+{
+    constexpr int E = N * N + N;
+    const int T = tb.n_terms;
+    double2 *xe = base;          // [N]
+    double2 *R = base + N;       // [N]
+    double2 *J = base + 2 * N;   // [N][N]
+    double2 *store = base + 2 * N + N * N;  // add_term pieces of every term
+    const bool own = r < N;
+    double t = hd.t, h = hd.h, next_s = hd.next_s;
+    double r0 = hd.r0, r1 = hd.r1, r2 = hd.r2, r3 = hd.r3, r4 = hd.r4;
+    const int sys = hd.sys;
+    int streak = hd.streak, steps = hd.steps, since_ck = hd.since_ck, nck = hd.nck;
+    int n_acc = hd.n_acc, n_rej = hd.n_rej, n_newt = hd.n_newt, n_solve = hd.n_solve;
+    const int n_f32 = hd.n_f32;
+    double2 x0r = own ? hd.x0[r] : make_double2(0.0, 0.0);
+    double2 accr = make_double2(0.0, 0.0), solr = make_double2(0.0, 0.0);
+    double he = 0.0, t1 = 0.0, te = 0.0, prev = 0.0;
+    int phase = 0, it = 0;
+    const double2 *C0 = tb.c0 + (size_t)coef_sys * tb.n_terms, *C1 = tb.c1 + (size_t)coef_sys * tb.n_terms;
+
+    auto begin_step = [&]() {
+        he = h;
+        t1 = t + he;
+        if (he >= 1.0 - t) {
+            he = 1.0 - t;
+            t1 = 1.0;
         }
-        p.eoff[E] = (uint16_t)acc;
-        // pieces in table order; within a term the columns in the order add_term emits them
-        for (int q = 0; q < T; q++) {
-            const TermRec r = tb.terms[q];
-            const int b = p.tslot[q], k = r.k;
-            if (k) {
-                for (int j = k - 1; j >= 0; j--) {
-                    const int e = r.eq * N + tb.vars[r.off + j];
-                    const uint16_t v = (j == k - 1) ? (uint16_t)((b + 2 * (k - 1)) | (PIECE_ADD << 14))
-                                                    : (uint16_t)((b + 2 * j) | (PIECE_FMA << 14));
-                    p.elist[p.eoff[e] + cnt[e]++] = v;
-                }
-                const int e = N * N + r.eq;
-                p.elist[p.eoff[e] + cnt[e]++] = (uint16_t)((b + 2 * k - 1) | (PIECE_RHS << 14));
+        if (own) xe[r] = x0r;
+        accr = make_double2(0.0, 0.0);
+        te = t;
+        phase = 0;
+    };
+    begin_step();
+    int stop = -1;
+    for (;;) {
+        __syncwarp(gmask);
+        // ---------------------------------------------- evaluation, phase A: the terms' pieces
+        const bool dt = phase < 4;
+        for (int i = r; i < T; i += G) {
+            const int qq = plan.torder[i];
+            const TermRec rec = tb.terms[qq];
+            const double2 c0 = C0[qq], c1 = C1[qq];
+            const double2 ct = make_double2(fma(te, c1.x, c0.x), fma(te, c1.y, c0.y));
+            const double2 cr = dt ? c1 : ct;
+            double2 *ts = store + plan.tslot[qq];
+            if (rec.k == 0) {
+                ts[0] = cr;
             } else {
-                const int e = N * N + r.eq;
-                p.elist[p.eoff[e] + cnt[e]++] = (uint16_t)(b | (PIECE_ADD << 14));
+                StoreSink sink{ts, rec.k};
+                add_term<double2>(rec, tb.vars + rec.off, tb.exps + rec.off, ct, cr, xe, 1, sink);
             }
         }
-        // entries by decreasing number of pieces (overwrites the counters)
-        w = 0;
-        for (int l = lmax; l >= 0; l--)
-            for (int e = 0; e < E; e++)
-                if (p.eoff[e + 1] - p.eoff[e] == l) p.eorder[w++] = (uint16_t)e;
+        __syncwarp(gmask);
+        // ---------------------------------------------- evaluation, phase B: the entries, pieces in table order
+        for (int i = r; i < E; i += G) {
+            const int e = plan.eorder[i];
+            double2 a = make_double2(0.0, 0.0);
+            for (int m = plan.eoff[e]; m < plan.eoff[e + 1]; m++) {
+                const uint16_t w = plan.elist[m];
+                const double2 *pc = store + (w & 0x3fff);
+                const int kind = w >> 14;
+                if (kind == PIECE_FMA) a = cfma(pc[0], pc[1], a);
+                else if (kind == PIECE_ADD) a = cadd(a, pc[0]);
+                else a = cfma(pc[1], pc[0], a);
+            }
+            if (e < N * N) J[e] = a;
+            else R[e - N * N] = a;
+        }
+        __syncwarp(gmask);
+        // ---------------------------------------------- LU (as lu_factor<N, double2>)
+        bool ok = true;
+        int perm[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            const double vk = abs1(J[k * N + k]);
+            // candidates: rows i > k with a larger |.|_1 (the first on ties)
+            double bv = (own && r > k) ? abs1(J[r * N + k]) : -1.0;
+            if (!(bv == bv)) bv = -1.0;
+            int bi = (own && r > k) ? r : N;
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                const double ov = __shfl_xor_sync(gmask, bv, off, G);
+                const int oi = __shfl_xor_sync(gmask, bi, off, G);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            int p = k;
+            double best = vk;
+            if (bi < N && bv > best) {
+                best = bv;
+                p = bi;
+            }
+            perm[k] = p;
+            if (!(best > 0.0)) {
+                ok = false;
+                break;
+            }
+            __syncwarp(gmask);  // every lane has read column k before row k changes
+            if (own && p != k) {
+                const double2 a = J[k * N + r], c = J[p * N + r];
+                J[k * N + r] = c;
+                J[p * N + r] = a;
+            }
+            __syncwarp(gmask);
+            const double2 inv = recip(J[k * N + k]);
+            __syncwarp(gmask);
+            if (r == k) J[k * N + k] = inv;
+            if (own && r > k) J[r * N + k] = cmul(J[r * N + k], inv);
+            __syncwarp(gmask);
+            // trailing update J[i][j] -= l_i J[k][j], i, j > k, spread over the group
+            const int M = N - 1 - k;
+            if (M > 0) {
+                for (int m = r; m < M * M; m += G) {
+                    const int i = k + 1 + m / M, j = k + 1 + m % M;
+                    J[i * N + j] = cfms(J[i * N + j], J[i * N + k], J[k * N + j]);
+                }
+            }
+            __syncwarp(gmask);
+        }
+        // ---------------------------------------------- solve (as lu_solve<N, double2>)
+        if (ok) {
+            if (r == 0) {
+#pragma unroll
+                for (int k = 0; k < N; k++) {
+                    const int p = perm[k];
+                    const double2 a = R[k], c = R[p];
+                    R[k] = c;
+                    R[p] = a;
+                }
+            }
+            __syncwarp(gmask);
+#pragma unroll
+            for (int k = 0; k < N - 1; k++) {
+                if (own && r > k) R[r] = cfms(R[r], J[r * N + k], R[k]);
+                __syncwarp(gmask);
+            }
+#pragma unroll
+            for (int k = N - 1; k >= 0; k--) {
+                if (r == k) R[k] = cmul(R[k], J[k * N + k]);
+                __syncwarp(gmask);
+                if (own && r < k) R[r] = cfms(R[r], J[r * N + k], R[k]);
+                __syncwarp(gmask);
+            }
+        }
+        solr = (own && ok) ? R[r] : make_double2(0.0, 0.0);
+        n_solve++;
+        __syncwarp(gmask);
+
+        // ---------------------------------------------- what the unit was for
+        enum { ACT_NONE = 0, ACT_ACCEPT, ACT_REJECT };
+        int act = ACT_NONE;
+        if (phase < 4) {
+            const bool fin = __all_sync(gmask, !own || (ok && finite2(solr)));
+            if (!ok || !fin) {
+                act = ACT_REJECT;
+            } else {
+                const double wacc = (phase == 0 || phase == 3) ? 1.0 : 2.0;
+                const double hs = (phase < 2) ? 0.5 * he : he;
+                if (own) {
+                    const double2 kj = make_double2(-solr.x, -solr.y);
+                    accr = (phase == 0) ? kj : caxpy(accr, wacc, kj);
+                    xe[r] = (phase < 3) ? caxpy(x0r, hs, kj) : caxpy(x0r, he / 6.0, accr);
+                }
+                te = (phase < 2) ? t + 0.5 * he : t1;
+                if (phase == 3) {
+                    it = 0;
+                    prev = 0.0;
+                }
+                phase++;
+            }
+        } else {
+            n_newt++;
+            double a = 0.0, c = 0.0;
+            bool fl = true;
+            if (ok && own) {
+                const double2 xj = make_double2(xe[r].x - solr.x, xe[r].y - solr.y);
+                xe[r] = xj;
+                if (phase == 5) x0r = xj;
+                a = absinf(solr);
+                c = absinf(xj);
+                fl = finite2(xj);
+            }
+            const bool fin = __all_sync(gmask, fl);
+            const double d = fin ? gmax<G>(a, gmask) : NAN;
+            const double nx = fin ? gmax<G>(c, gmask) : NAN;
+            if (phase == 4) {
+                if (!ok || !(d == d) || !fin) act = ACT_REJECT;
+                else if (d <= o.corr_tol * (1.0 + nx)) act = ACT_ACCEPT;
+                else if (it > 0 && d > o.corr_contract * prev) act = ACT_REJECT;
+                else {
+                    prev = d;
+                    if (++it >= o.max_corr_iters) act = ACT_REJECT;
+                }
+            } else {
+                if (!ok) stop = PHC_STOP_REACHED;
+                else if (!(d == d) || !fin) stop = fin ? PHC_STOP_REACHED : PHC_STOP_NONFINITE;
+                else if (d <= o.end_tol * (1.0 + nx) || ++it >= o.end_iters) stop = PHC_STOP_REACHED;
+            }
+        }
+        __syncwarp(gmask);
+
+        // ---------------------------------------------- step control
+        if (act == ACT_ACCEPT) {
+            t = t1;
+            if (own) x0r = xe[r];
+            const double nx = gmax<G>(own ? absinf(x0r) : 0.0, gmask);
+            n_acc++;
+            steps++;
+            while (1.0 - t <= next_s && next_s > 0.0) {
+                r0 = r1;
+                r1 = r2;
+                r2 = r3;
+                r3 = r4;
+                r4 = nx;
+                nck++;
+                since_ck = 0;
+                next_s *= 0.1;
+                if (nck >= 40) next_s = 0.0;
+            }
+            if (nx > o.diverge_norm) {
+                stop = PHC_STOP_DIVERGED;
+            } else {
+                if (++streak >= o.expand_after) {
+                    streak = 0;
+                    h = h * o.expand;
+                    if (h > o.h_max) h = o.h_max;
+                }
+                if (steps >= o.max_steps) stop = PHC_STOP_BUDGET;
+                else if (++since_ck >= o.max_steps_decade && t < 1.0) stop = PHC_STOP_BUDGET;
+                else if (t >= 1.0) {
+                    phase = 5;
+                    it = 0;
+                    te = 1.0;
+                } else {
+                    begin_step();
+                }
+            }
+        } else if (act == ACT_REJECT) {
+            n_rej++;
+            steps++;
+            streak = 0;
+            h = he * o.shrink;
+            if (h < o.h_min) stop = PHC_STOP_STEP_MIN;
+            if (stop < 0 && steps >= o.max_steps) stop = PHC_STOP_BUDGET;
+            if (stop < 0 && ++since_ck >= o.max_steps_decade) stop = PHC_STOP_BUDGET;
+            if (stop < 0) begin_step();
+        }
+        if (stop >= 0) break;
     }
-    __syncthreads();
-    return p;
+
+    // ---------------------------------------------- the path ends
+    phc_path_stats rec{};
+    if (r == 0) {
+        int grew = 0;
+        double growth = 0.0;
+        if (nck >= 2) {
+            const int l = nck - 1, m = l < 4 ? l : 4;
+            const double a = r4, b = (m == 1) ? r3 : (m == 2) ? r2 : (m == 3) ? r1 : r0;
+            double g = 1.0;
+            for (int k = 0; k < m; k++) g *= o.growth_inf;
+            grew = a > b * g;
+            growth = log10(a / b) / m;
+        }
+        rec.t = t;
+        rec.h = h;
+        rec.cond = 0.0;
+        rec.relres = 0.0;
+        rec.norm_x = 0.0;
+        rec.growth = growth;
+        rec.n_accept = n_acc;
+        rec.n_reject = n_rej;
+        rec.n_newton = n_newt;
+        rec.n_solve = n_solve;
+        rec.stop = stop;
+        rec.n_fp32 = n_f32;
+        rec.grew = grew;
+        rec.system = sys;
+    }
+    finish(x0r, rec, n_solve - hd.n_solve);
+    __syncwarp(gmask);
 }
 
 template <int N, int G>
@@ -151,307 +439,105 @@ __global__ void __launch_bounds__(128) tail_kernel(const TrackLaunch L, size_t t
 {
     extern __shared__ __align__(16) char smem[];
     const SmTab tb = stage_table(L.tab, smem);
-    const TailPlan plan = build_plan<N>(tb, smem + table_bytes);
-    constexpr int E = N * N + N;
-    const int T = tb.n_terms;
-    const int S = tail_store_slots(T, L.tab.n_ve);
+    const TailPlan plan = plan_layout<N>(tb, smem + table_bytes);
+    if (threadIdx.x == 0) plan_fill<N>(tb, plan);
+    __syncthreads();
+    const int S = tail_store_slots(tb.n_terms, L.tab.n_ve);
     const int lane = threadIdx.x & 31;
     const int r = lane % G;  // the row this lane owns in the LU and the solves (r < N)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - r));
     const int group = threadIdx.x / G;
-    double2 *base = reinterpret_cast<double2 *>(smem + table_bytes + plan_bytes) + (size_t)group * (2 * N + N * N + S);
-    double2 *xe = base;          // [N]
-    double2 *R = base + N;       // [N]
-    double2 *J = base + 2 * N;   // [N][N]
-    double2 *store = base + 2 * N + N * N;  // [S] add_term pieces of every term
-    const phc_opts &o = L.o;
+    double2 *base = reinterpret_cast<double2 *>(smem + table_bytes + plan_bytes) +
+                    (size_t)group * tail_group_slots(N, S);
     const int64_t np = L.n_paths;
-    const bool own = r < N;
     const unsigned long long n_hand = *reinterpret_cast<volatile const unsigned long long *>(L.handoff_n);
-
     for (;;) {
         unsigned long long slot = 0;
         if (r == 0) slot = atomicAdd(L.tail_q, 1ull);
         slot = __shfl_sync(gmask, slot, 0, G);
         if (slot >= n_hand) break;
         const Handoff &hd = L.handoff[slot];
-        double t = hd.t, h = hd.h, next_s = hd.next_s;
-        double r0 = hd.r0, r1 = hd.r1, r2 = hd.r2, r3 = hd.r3, r4 = hd.r4;
         const int64_t q = hd.q;
-        const int sys = hd.sys;
-        int streak = hd.streak, steps = hd.steps, since_ck = hd.since_ck, nck = hd.nck;
-        int n_acc = hd.n_acc, n_rej = hd.n_rej, n_newt = hd.n_newt, n_solve = hd.n_solve;
-        const int n_f32 = hd.n_f32;
-        double2 x0r = own ? hd.x0[r] : make_double2(0.0, 0.0);
-        double2 accr = make_double2(0.0, 0.0), solr = make_double2(0.0, 0.0);
-        double he = 0.0, t1 = 0.0, te = 0.0, prev = 0.0;
-        int phase = 0, it = 0;
-        const double2 *C0 = tb.c0 + (size_t)sys * tb.n_terms, *C1 = tb.c1 + (size_t)sys * tb.n_terms;
+        tail_path<N, G>(hd, tb, plan, hd.sys, base, L.o, r, gmask,
+                        [&](double2 x0r, const phc_path_stats &rec, int units) {
+                            if (r < N) L.x_out[(int64_t)r * np + q] = x0r;
+                            if (r == 0) {
+                                L.stats[q] = rec;
+                                atomicAdd(L.tail_units, (unsigned long long)units);
+                            }
+                        });
+    }
+}
 
-        auto begin_step = [&]() {
-            he = h;
-            t1 = t + he;
-            if (he >= 1.0 - t) {
-                he = 1.0 - t;
-                t1 = 1.0;
-            }
-            if (own) xe[r] = x0r;
-            accr = make_double2(0.0, 0.0);
-            te = t;
-            phase = 0;
-        };
-        begin_step();
-        int stop = -1;
-        for (;;) {
-            __syncwarp(gmask);
-            // ---------------------------------------------- evaluation, phase A: the terms' pieces
-            const bool dt = phase < 4;
-            for (int i = r; i < T; i += G) {
-                const int qq = plan.torder[i];
-                const TermRec rec = tb.terms[qq];
-                const double2 c0 = C0[qq], c1 = C1[qq];
-                const double2 ct = make_double2(fma(te, c1.x, c0.x), fma(te, c1.y, c0.y));
-                const double2 cr = dt ? c1 : ct;
-                double2 *ts = store + plan.tslot[qq];
-                if (rec.k == 0) {
-                    ts[0] = cr;
-                } else {
-                    StoreSink sink{ts, rec.k};
-                    add_term<double2>(rec, tb.vars + rec.off, tb.exps + rec.off, ct, cr, xe, 1, sink);
-                }
-            }
-            __syncwarp(gmask);
-            // ---------------------------------------------- evaluation, phase B: the entries, pieces in table order
-            for (int i = r; i < E; i += G) {
-                const int e = plan.eorder[i];
-                double2 a = make_double2(0.0, 0.0);
-                for (int m = plan.eoff[e]; m < plan.eoff[e + 1]; m++) {
-                    const uint16_t w = plan.elist[m];
-                    const double2 *pc = store + (w & 0x3fff);
-                    const int kind = w >> 14;
-                    if (kind == PIECE_FMA) a = cfma(pc[0], pc[1], a);
-                    else if (kind == PIECE_ADD) a = cadd(a, pc[0]);
-                    else a = cfma(pc[1], pc[0], a);
-                }
-                if (e < N * N) J[e] = a;
-                else R[e - N * N] = a;
-            }
-            __syncwarp(gmask);
-            // ---------------------------------------------- LU (as lu_factor<N, double2>)
-            bool ok = true;
-            int perm[N];
-#pragma unroll
-            for (int k = 0; k < N; k++) {
-                const double vk = abs1(J[k * N + k]);
-                // candidates: rows i > k with a larger |.|_1 (the first on ties)
-                double bv = (own && r > k) ? abs1(J[r * N + k]) : -1.0;
-                if (!(bv == bv)) bv = -1.0;
-                int bi = (own && r > k) ? r : N;
-#pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) {
-                    const double ov = __shfl_xor_sync(gmask, bv, off, G);
-                    const int oi = __shfl_xor_sync(gmask, bi, off, G);
-                    if (ov > bv || (ov == bv && oi < bi)) {
-                        bv = ov;
-                        bi = oi;
-                    }
-                }
-                int p = k;
-                double best = vk;
-                if (bi < N && bv > best) {
-                    best = bv;
-                    p = bi;
-                }
-                perm[k] = p;
-                if (!(best > 0.0)) {
-                    ok = false;
-                    break;
-                }
-                __syncwarp(gmask);  // every lane has read column k before row k changes
-                if (own && p != k) {
-                    const double2 a = J[k * N + r], c = J[p * N + r];
-                    J[k * N + r] = c;
-                    J[p * N + r] = a;
-                }
-                __syncwarp(gmask);
-                const double2 inv = recip(J[k * N + k]);
-                __syncwarp(gmask);
-                if (r == k) J[k * N + k] = inv;
-                if (own && r > k) J[r * N + k] = cmul(J[r * N + k], inv);
-                __syncwarp(gmask);
-                // trailing update J[i][j] -= l_i J[k][j], i, j > k, spread over the group
-                const int M = N - 1 - k;
-                if (M > 0) {
-                    for (int m = r; m < M * M; m += G) {
-                        const int i = k + 1 + m / M, j = k + 1 + m % M;
-                        J[i * N + j] = cfms(J[i * N + j], J[i * N + k], J[k * N + j]);
-                    }
-                }
-                __syncwarp(gmask);
-            }
-            // ---------------------------------------------- solve (as lu_solve<N, double2>)
-            if (ok) {
-                if (r == 0) {
-#pragma unroll
-                    for (int k = 0; k < N; k++) {
-                        const int p = perm[k];
-                        const double2 a = R[k], c = R[p];
-                        R[k] = c;
-                        R[p] = a;
-                    }
-                }
-                __syncwarp(gmask);
-#pragma unroll
-                for (int k = 0; k < N - 1; k++) {
-                    if (own && r > k) R[r] = cfms(R[r], J[r * N + k], R[k]);
-                    __syncwarp(gmask);
-                }
-#pragma unroll
-                for (int k = N - 1; k >= 0; k--) {
-                    if (r == k) R[k] = cmul(R[k], J[k * N + k]);
-                    __syncwarp(gmask);
-                    if (own && r < k) R[r] = cfms(R[r], J[r * N + k], R[k]);
-                    __syncwarp(gmask);
-                }
-            }
-            solr = (own && ok) ? R[r] : make_double2(0.0, 0.0);
-            n_solve++;
-            __syncwarp(gmask);
+// classify_one for one lane, out of line: it needs many registers, the
+// tracking loop of the tail kernel does not.
+template <int N>
+__device__ __noinline__ int8_t classify_lane(const SmTab &tb, const ThreadArrays &A, phc_path_stats &rec,
+                                             const phc_opts &o)
+{
+    return classify_one<N>(tb, A, rec, o, 1);
+}
 
-            // ---------------------------------------------- what the unit was for
-            enum { ACT_NONE = 0, ACT_ACCEPT, ACT_REJECT };
-            int act = ACT_NONE;
-            if (phase < 4) {
-                const bool fin = __all_sync(gmask, !own || (ok && finite2(solr)));
-                if (!ok || !fin) {
-                    act = ACT_REJECT;
-                } else {
-                    const double wacc = (phase == 0 || phase == 3) ? 1.0 : 2.0;
-                    const double hs = (phase < 2) ? 0.5 * he : he;
-                    if (own) {
-                        const double2 kj = make_double2(-solr.x, -solr.y);
-                        accr = (phase == 0) ? kj : caxpy(accr, wacc, kj);
-                        xe[r] = (phase < 3) ? caxpy(x0r, hs, kj) : caxpy(x0r, he / 6.0, accr);
-                    }
-                    te = (phase < 2) ? t + 0.5 * he : t1;
-                    if (phase == 3) {
-                        it = 0;
-                        prev = 0.0;
-                    }
-                    phase++;
-                }
-            } else {
-                n_newt++;
-                double a = 0.0, c = 0.0;
-                bool fl = true;
-                if (ok && own) {
-                    const double2 xj = make_double2(xe[r].x - solr.x, xe[r].y - solr.y);
-                    xe[r] = xj;
-                    if (phase == 5) x0r = xj;
-                    a = absinf(solr);
-                    c = absinf(xj);
-                    fl = finite2(xj);
-                }
-                const bool fin = __all_sync(gmask, fl);
-                const double d = fin ? gmax<G>(a, gmask) : NAN;
-                const double nx = fin ? gmax<G>(c, gmask) : NAN;
-                if (phase == 4) {
-                    if (!ok || !(d == d) || !fin) act = ACT_REJECT;
-                    else if (d <= o.corr_tol * (1.0 + nx)) act = ACT_ACCEPT;
-                    else if (it > 0 && d > o.corr_contract * prev) act = ACT_REJECT;
-                    else {
-                        prev = d;
-                        if (++it >= o.max_corr_iters) act = ACT_REJECT;
-                    }
-                } else {
-                    if (!ok) stop = PHC_STOP_REACHED;
-                    else if (!(d == d) || !fin) stop = fin ? PHC_STOP_REACHED : PHC_STOP_NONFINITE;
-                    else if (d <= o.end_tol * (1.0 + nx) || ++it >= o.end_iters) stop = PHC_STOP_REACHED;
-                }
-            }
-            __syncwarp(gmask);
-
-            // ---------------------------------------------- step control
-            if (act == ACT_ACCEPT) {
-                t = t1;
-                if (own) x0r = xe[r];
-                const double nx = gmax<G>(own ? absinf(x0r) : 0.0, gmask);
-                n_acc++;
-                steps++;
-                while (1.0 - t <= next_s && next_s > 0.0) {
-                    r0 = r1;
-                    r1 = r2;
-                    r2 = r3;
-                    r3 = r4;
-                    r4 = nx;
-                    nck++;
-                    since_ck = 0;
-                    next_s *= 0.1;
-                    if (nck >= 40) next_s = 0.0;
-                }
-                if (nx > o.diverge_norm) {
-                    stop = PHC_STOP_DIVERGED;
-                } else {
-                    if (++streak >= o.expand_after) {
-                        streak = 0;
-                        h = h * o.expand;
-                        if (h > o.h_max) h = o.h_max;
-                    }
-                    if (steps >= o.max_steps) stop = PHC_STOP_BUDGET;
-                    else if (++since_ck >= o.max_steps_decade && t < 1.0) stop = PHC_STOP_BUDGET;
-                    else if (t >= 1.0) {
-                        phase = 5;
-                        it = 0;
-                        te = 1.0;
-                    } else {
-                        begin_step();
-                    }
-                }
-            } else if (act == ACT_REJECT) {
-                n_rej++;
-                steps++;
-                streak = 0;
-                h = he * o.shrink;
-                if (h < o.h_min) stop = PHC_STOP_STEP_MIN;
-                if (stop < 0 && steps >= o.max_steps) stop = PHC_STOP_BUDGET;
-                if (stop < 0 && ++since_ck >= o.max_steps_decade) stop = PHC_STOP_BUDGET;
-                if (stop < 0) begin_step();
-            }
-            if (stop >= 0) break;
+// The multi-system tail: one warp per path; each warp stages the table and
+// builds the plan of the path's system in its own region (again only when
+// the system changes), and classifies the endpoint (in lane 0, with
+// classify_one, as the multi-system tracker does inline).
+template <int N>
+__global__ void __launch_bounds__(128) tail_multi_kernel(const TrackLaunch L, size_t region_bytes,
+                                                         size_t table_cap, size_t plan_cap)
+{
+    extern __shared__ __align__(16) char smem[];
+    constexpr int G = 32;
+    const int r = threadIdx.x & 31;
+    char *region = smem + (size_t)(threadIdx.x >> 5) * region_bytes;
+    double2 *base = reinterpret_cast<double2 *>(region + table_cap + plan_cap);
+    const unsigned long long n_hand = *reinterpret_cast<volatile const unsigned long long *>(L.handoff_n);
+    int cur = -1;
+    SmTab tb{};
+    TailPlan plan{};
+    for (;;) {
+        unsigned long long slot = 0;
+        if (r == 0) slot = atomicAdd(L.tail_q, 1ull);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= n_hand) break;
+        const Handoff &hd = L.handoff[slot];
+        const int ws = hd.sys;
+        const SysDesc &d = L.multi[ws];
+        if (ws != cur) {
+            __syncwarp();
+            tb = stage_table_warp(d.tab, region);
+            plan = plan_layout<N>(tb, region + table_cap);
+            if (r == 0) plan_fill<N>(tb, plan);
+            __syncwarp();
+            cur = ws;
         }
-
-        // ---------------------------------------------- the path ends
-        if (own) L.x_out[(int64_t)r * np + q] = x0r;
-        if (r == 0) {
-            int grew = 0;
-            double growth = 0.0;
-            if (nck >= 2) {
-                const int l = nck - 1, m = l < 4 ? l : 4;
-                const double a = r4, b = (m == 1) ? r3 : (m == 2) ? r2 : (m == 3) ? r1 : r0;
-                double g = 1.0;
-                for (int k = 0; k < m; k++) g *= o.growth_inf;
-                grew = a > b * g;
-                growth = log10(a / b) / m;
-            }
-            phc_path_stats rec;
-            rec.t = t;
-            rec.h = h;
-            rec.cond = 0.0;
-            rec.relres = 0.0;
-            rec.norm_x = 0.0;
-            rec.growth = growth;
-            rec.n_accept = n_acc;
-            rec.n_reject = n_rej;
-            rec.n_newton = n_newt;
-            rec.n_solve = n_solve;
-            rec.stop = stop;
-            rec.n_fp32 = n_f32;
-            rec.grew = grew;
-            rec.system = sys;
-            L.stats[q] = rec;
-            atomicAdd(L.tail_units, (unsigned long long)(n_solve - hd.n_solve));
-        }
-        __syncwarp(gmask);
+        const int64_t q = hd.q;
+        tail_path<N, G>(hd, tb, plan, 0, base, L.o, r, 0xffffffffu,
+                        [&](double2 x0r, const phc_path_stats &rec0, int units) {
+                            // classification arrays over the group's slots, stride 1
+                            ThreadArrays A;
+                            A.xe = base;
+                            A.R = A.xe + N;
+                            A.P = A.R + N;
+                            A.X = A.P;
+                            A.J = A.P + N;
+                            A.S = A.J + N * N;
+                            if (r < N) {
+                                A.xe[r] = x0r;
+                                d.x_out[(int64_t)r * d.n_paths + q] = x0r;
+                            }
+                            __syncwarp();
+                            if (r == 0) {
+                                phc_path_stats rec = rec0;
+                                rec.system = 0;
+                                const int8_t c = classify_lane<N>(tb, A, rec, L.o);
+                                rec.system = ws;
+                                d.stats[q] = rec;
+                                d.cls_out[q] = c;
+                                atomicAdd(L.tail_units, (unsigned long long)units);
+                            }
+                            __syncwarp();
+                        });
     }
 }
 
@@ -462,7 +548,7 @@ static cudaError_t launch_tail_n(const TrackLaunch &L_in, int max_blocks, cudaSt
     L.tab.coef_smem = 1;
     size_t tb = table_smem_bytes(L.tab);
     const size_t pb = tail_plan_bytes(N, L.tab.n_terms, L.tab.n_ve);
-    const size_t per_group = (size_t)(2 * N + N * N + tail_store_slots(L.tab.n_terms, L.tab.n_ve)) * sizeof(double2);
+    const size_t per_group = (size_t)tail_group_slots(N, tail_store_slots(L.tab.n_terms, L.tab.n_ve)) * sizeof(double2);
     int groups = 128 / G;
     if (tb + pb + groups * per_group > (size_t)g_smem_optin) {
         L.tab.coef_smem = 0;  // coefficients through L1
@@ -494,7 +580,7 @@ bool tail_supported(const DevTables &t)
     DevTables u = t;
     u.coef_smem = 0;
     const size_t need = table_smem_bytes(u) + tail_plan_bytes(n, t.n_terms, t.n_ve) +
-                        (size_t)(2 * n + n * n + S) * sizeof(double2);
+                        (size_t)tail_group_slots(n, S) * sizeof(double2);
     return need <= (size_t)g_smem_optin;
 }
 
@@ -526,5 +612,41 @@ cudaError_t launch_tail(const TrackLaunch &L, int max_blocks, cudaStream_t s)
     }
 }
 #undef PHC_TAIL_CASE
+
+template <int N>
+static cudaError_t launch_tail_multi_n(const TrackLaunch &L, const TailMultiSizes &z, int max_blocks, cudaStream_t s)
+{
+    const size_t region = z.table_cap + z.plan_cap + (size_t)z.group_slots * sizeof(double2);
+    int warps = 4;
+    while (warps > 1 && warps * region > (size_t)g_smem_optin) warps /= 2;
+    if (warps * region > (size_t)g_smem_optin) return cudaErrorInvalidConfiguration;
+    const size_t smem = warps * region;
+    cudaError_t e =
+        cudaFuncSetAttribute(tail_multi_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tail_multi_kernel<N>, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = g_num_sms * per_sm;
+    if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+    tail_multi_kernel<N><<<grid, warps * 32, smem, s>>>(L, region, z.table_cap, z.plan_cap);
+    return cudaGetLastError();
+}
+
+bool tail_multi_supported(const TailMultiSizes &z)
+{
+    device_limits();
+    return z.max_store < (1 << 14) &&  // slot numbers are 14-bit
+           z.table_cap + z.plan_cap + (size_t)z.group_slots * sizeof(double2) <= (size_t)g_smem_optin;
+}
+
+cudaError_t launch_tail_multi(const TrackLaunch &L, int n, const TailMultiSizes &z, int max_blocks, cudaStream_t s)
+{
+    device_limits();
+#define PHC_CALL_TAILM(NN) launch_tail_multi_n<NN>(L, z, max_blocks, s)
+    PHC_DISPATCH_N(n, PHC_CALL_TAILM)
+#undef PHC_CALL_TAILM
+}
 
 }  // namespace phc

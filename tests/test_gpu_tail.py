@@ -107,3 +107,18 @@ def test_tail_handoff_bit_identical_cascade_stages():
     assert moved > 0
     _, moved = _three_ways(lambda o: P.cascade_from(h, D, top, opts=o), h)
     assert moved > 0
+
+
+def test_tail_handoff_bit_identical_many_systems():
+    """phc_track_many (one launch per number of unknowns, a warp per system):
+    the multi-system tail kernel leaves results byte-identical too."""
+    w = configs.sparse_batch(count=12, seed=1001, bezout_range=(100, 3000))
+    hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
+
+    def run(o):
+        return [_host(r) for r in P.track_many(hs, opts=o)]
+
+    base = run(_opts(0.0))
+    for o in (_opts(0.85), _opts(1e-9, tiny_grid=True)):
+        for a, b in zip(base, run(o)):
+            _same(a, b, "track_many with the tail hand-off")
