@@ -328,6 +328,13 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}", "classes_last_step": counts.tolist()},
         "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
     }
+    if rank == 0 and world == 1 and args.serving_requests > 0:
+        # served latency: Poisson arrivals of small requests (the third figure of the metric)
+        sv, _ = serving_session(args.serving_requests, False, args.slots)
+        line["serving"] = {k: sv[k] for k in ("requests", "rate_per_s", "wall_s", "tracked_paths_per_s",
+                                              "offered_small_paths_per_s", "latency_small")}
+        line["serving"]["workload"] = (f"{args.serving_requests} Poisson (200/s) sparse requests, "
+                                       "Bezout 1e2..1e3, continuous batching (phc_track_many)")
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, n, dt = oracle_sample(systems, gammas, args.ref_sample)
         line["cpu_baseline"] = {"value": v, "unit": "paths/s", "cores": cores, "kind": "oracle",
@@ -378,27 +385,22 @@ def end_to_end(P, systems, gammas, dev, args):
             "steps": reps}
 
 
-def run_serving(args):
-    """Config 5: Poisson arrivals (200/s) of sparse requests plus cyclic 9
-    embedded for top dimension 2 (362,880 paths, two cascade stages)
-    arriving first; continuous batching on one GPU."""
-    import torch
-    from paper_1804_03807_gb300 import build as pbuild
-    pbuild.build()
-    import paper_1804_03807_gb300 as P
+def serving_session(n_requests: int, big: bool, slots: int):
+    """Continuous batching of Poisson arrivals (200/s) of sparse requests,
+    optionally with cyclic 9 embedded for top dimension 2 (362,880 paths, two
+    cascade stages) arriving first; returns the measurement and the requests."""
     from paper_1804_03807_gb300 import serving
     from workloads import configs
-    torch.cuda.set_device(0)
-    w = configs.serving(n_requests=args.requests, rate=200.0, seed=5, bezout_range=(100, 1000),
-                        big=None if args.no_big else (9, 2))
+    w = configs.serving(n_requests=n_requests, rate=200.0, seed=5, bezout_range=(100, 1000),
+                        big=(9, 2) if big else None)
     reqs = [serving.Request(i, s, g, float(a)) for i, (s, g, a) in
             enumerate(zip(w.systems, w.gammas, w.extra["arrivals"]))]
     small = set(r.rid for r in reqs)
-    if not args.no_big:
+    if big:
         b = w.extra["big"]
         reqs.append(serving.Request(len(reqs), b["system"], b["gamma"], b["arrival"], b["top_dim"], b["gammas"],
                                     b["hyper"]))
-    srv = serving.Server(slots=2, max_inflight=args.slots)
+    srv = serving.Server(slots=2, max_inflight=slots)
     srv.run(reqs[:8], realtime=False)  # warm-up: kernels loaded, allocator primed
     with ClockSampler(0) as clk:
         t0 = time.perf_counter()
@@ -406,13 +408,30 @@ def run_serving(args):
         wall = time.perf_counter() - t0
     paths = sum(r.n_paths * len(r.stages) for r in res)
     top_paths = sum(r.n_paths for r in res)
-    lat_small = serving.latency_summary(res, small)
-    lat_big = serving.latency_summary(res, set(r.rid for r in reqs) - small)
-    offered = sum(r.n_paths for r in res if r.rid in small) / max(w.extra["arrivals"][-1], 1e-9)
-    line = {"metric": METRIC, "workload": "serving", "value": top_paths / wall, "unit": "paths/s",
-            "tracked_paths_per_s": paths / wall, "n_requests": len(reqs), "wall_s": wall,
-            "latency_small": lat_small, "latency_cyclic9_d2": lat_big,
-            "offered_small_paths_per_s": offered, "slots": args.slots, "clocks": clk.summary(),
+    out = {"requests": len(reqs), "rate_per_s": 200.0, "wall_s": wall, "paths_per_s": top_paths / wall,
+           "tracked_paths_per_s": paths / wall,
+           "offered_small_paths_per_s": sum(r.n_paths for r in res if r.rid in small) /
+           max(w.extra["arrivals"][-1], 1e-9),
+           "latency_small": serving.latency_summary(res, small), "clocks": clk.summary(), "slots": slots}
+    if big:
+        out["latency_cyclic9_d2"] = serving.latency_summary(res, set(r.rid for r in reqs) - small)
+    return out, reqs
+
+
+def run_serving(args):
+    """Config 5: Poisson arrivals (200/s) of sparse requests plus cyclic 9
+    embedded for top dimension 2 (362,880 paths, two cascade stages)
+    arriving first; continuous batching on one GPU."""
+    import torch
+    from paper_1804_03807_gb300 import build as pbuild
+    pbuild.build()
+    torch.cuda.set_device(0)
+    sv, reqs = serving_session(args.requests, not args.no_big, args.slots)
+    line = {"metric": METRIC, "workload": "serving", "value": sv["paths_per_s"], "unit": "paths/s",
+            "tracked_paths_per_s": sv["tracked_paths_per_s"], "n_requests": sv["requests"], "wall_s": sv["wall_s"],
+            "latency_small": sv["latency_small"], "latency_cyclic9_d2": sv.get("latency_cyclic9_d2", {"count": 0}),
+            "offered_small_paths_per_s": sv["offered_small_paths_per_s"], "slots": args.slots,
+            "clocks": sv["clocks"],
             "config": {"workload": f"{args.requests} Poisson (200/s) sparse requests, Bezout 1e2..1e3"
                        + ("" if args.no_big else " + cyclic 9 D=2 (362,880 paths, 2 cascade stages) at t=0")}}
     if not args.no_cpu_baseline:
@@ -468,6 +487,8 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of Poisson requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: batches of requests on the GPU at once")
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the cyclic 9 request")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--profile-case", nargs="?", const="cyclic7", default=None, choices=["cyclic7", "sparse"],
                     help="run a small case of a bench kernel twice (for ncu) and exit")
     args = ap.parse_args(argv)
