@@ -10,11 +10,12 @@ and their work overlaps on the device:
   unknowns, every warp on one request's system at a time), so small
   requests share launches that fill the GPU;
 * an embedded request runs on a stream of its own as soon as it arrives:
-  the top stage of E_D and the first cascade stage in one launch
-  (phc_track_pipeline), then one phc_cascade_from per lower stage, each fed
-  directly by the previous stage's device outputs (Section 3.1: regular
-  endpoints with a nonzero slack start the next stage); it gets a grid cap
-  (big_share of the SMs) so that batches of small requests keep SMs.
+  the top stage of E_D, then one phc_cascade_from per cascade stage, each
+  fed directly by the previous stage's device outputs (Section 3.1: regular
+  endpoints with a nonzero slack start the next stage); with pipelined=True
+  the top stage and the first cascade stage share one launch
+  (phc_track_pipeline).  It gets a grid cap (big_share of the SMs) so that
+  batches of small requests keep SMs.
 
 Every unit of work ends with an event; the loop polls the events, copies the
 classes and endpoints of finished work to the host, retires it (freeing its
@@ -33,7 +34,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (STATS_DTYPE, phc_cascade_from, phc_default_opts, phc_embed, phc_make_homotopy, phc_num_paths,
-                   phc_track_many, phc_track_pipeline)
+                   phc_track_many, phc_track_paths, phc_track_pipeline)
 
 
 @dataclass
@@ -78,7 +79,7 @@ def _bytes_for(n_var: int, n_paths: int) -> int:
 
 class Server:
     def __init__(self, slots: int = 4, mem_bytes: int = 16 << 30, big_share: float = 0.6, opts=None,
-                 device="cuda", max_inflight: int = 4, batch_paths: int = 60_000):
+                 device="cuda", max_inflight: int = 4, batch_paths: int = 60_000, pipelined: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -87,6 +88,10 @@ class Server:
         self.batch_paths = batch_paths      # paths per batch (bounds a batch's duration)
         self.mem_bytes = mem_bytes
         self.big_share = big_share
+        # embedded requests: the top stage and the first cascade stage in one
+        # pipelined launch, or (default) one launch each, which lets both use
+        # the tail hand-off
+        self.pipelined = pipelined
         self.opts = opts if opts is not None else phc_default_opts()
         self.batch_streams = [torch.cuda.Stream(device=self.device) for _ in range(max_inflight)]
         self.big_streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
@@ -148,7 +153,13 @@ class Server:
 
             xt, ct, stt, _ = buf(N)
             xn, cn, stn, szn = buf(N - 1)
-            phc_track_pipeline(h, D, 0, P, opts, xt, ct, stt, xn, cn, szn, stn, stream)
+            if self.pipelined:
+                phc_track_pipeline(h, D, 0, P, opts, xt, ct, stt, xn, cn, szn, stn, stream)
+            else:
+                # top stage, then the first cascade stage from its device outputs
+                # (each launch with its tail hand-off)
+                phc_track_paths(h, 0, P, opts, xt, ct, stt, stream)
+                phc_cascade_from(h, D, xt, ct, None, P, opts, xn, cn, szn, stn, stream)
             stages += [(xt, ct), (xn, cn)]
             prev = (xn, cn, szn)
             for k in range(D - 1, 0, -1):
