@@ -464,10 +464,11 @@ def _timed(fn, reps: int, warmup: int = 2):
 
 
 def run_configs(args):
-    """Every workload of the benchmark list on one GPU, one JSON line each:
-    paths/s and Newton steps/s (device time), the FP64 fraction of the flop
-    model, the one-launch-per-system (or per-stage) variant where one exists,
-    and the oracle on a bounded sample of the same workload."""
+    """Every workload of the benchmark list on one GPU (or those in
+    --configs), one JSON line each: paths/s and Newton steps/s (device
+    time), the FP64 fraction of the flop model, the one-launch-per-system
+    (or per-stage) variant where one exists, and the oracle on a bounded
+    sample of the same workload."""
     import torch
     from paper_1804_03807_gb300 import build as pbuild
     pbuild.build()
@@ -476,6 +477,7 @@ def run_configs(args):
     from workloads import configs
     torch.cuda.set_device(0)
     peak = FP64_PEAK_TFLOPS * 1e12
+    out = {}
 
     def summary(rs, flops_per_unit, ms):
         units = newton = 0
@@ -489,88 +491,87 @@ def run_configs(args):
         return {"newton_steps_per_s": newton / (ms / 1e3), "fp64_frac": flops / (ms / 1e3) / peak,
                 "units": units}
 
-    def emit(d):
-        print(json.dumps(d), flush=True)
+    def oracle_part(systems, gammas, per_system, what):
+        v, cores, n, dt = oracle_sample(systems, gammas, per_system)
+        return {"paths_per_s": v, "cores": cores, "sample": f"{n} {what} ({dt:.1f} s)"}
 
-    # 1: dense n = 4, 16 paths
-    w = configs.dense4()
-    h = P.phc_make_homotopy(w.systems[0], w.gammas[0])
-    out = {}
-    ms = _timed(lambda: out.__setitem__("r", P.track(h)), 50)
-    d = {"config": 1, "workload": "dense n=4, degree 2, 16 paths", "paths_per_s": 16 / (ms / 1e3), "ms": ms}
-    d.update(summary([out["r"]], [unit_flops(homotopy_terms(w.systems[0]), 4)], ms))
-    v, cores, n, dt = oracle_sample(w.systems * 200, w.gammas * 200, 16)
-    d["oracle"] = {"paths_per_s": v, "cores": cores, "sample": f"{n} paths ({dt:.1f} s)"}
-    emit(d)
+    def config1():
+        w = configs.dense4()
+        h = P.phc_make_homotopy(w.systems[0], w.gammas[0])
+        ms = _timed(lambda: out.__setitem__("r", P.track(h)), 50)
+        d = {"config": 1, "workload": "dense n=4, degree 2, 16 paths", "paths_per_s": 16 / (ms / 1e3), "ms": ms}
+        d.update(summary([out["r"]], [unit_flops(homotopy_terms(w.systems[0]), 4)], ms))
+        d["oracle"] = oracle_part(w.systems * 200, w.gammas * 200, 16, "paths")
+        return d
 
-    # 2: cyclic 7 batch: one batch launch vs one launch per system
-    w = configs.cyclic7_batch()
-    hb = P.phc_make_homotopy_batch(w.systems, w.gammas)
-    hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
-    fpu = unit_flops(homotopy_terms(w.systems[0]), 7)
-    ms = _timed(lambda: out.__setitem__("r", P.track(hb)), 3)
-    d = {"config": 2, "workload": "cyclic 7 + 8 random copies, 45,360 paths, one batch launch",
-         "paths_per_s": 45360 / (ms / 1e3), "ms": ms}
-    d.update(summary([out["r"]], [fpu], ms))
-    ms1 = _timed(lambda: out.__setitem__("rs", [P.track(x) for x in hs]), 3)
-    d["one_launch_per_system"] = {"paths_per_s": 45360 / (ms1 / 1e3), "ms": ms1}
-    v, cores, n, dt = oracle_sample(w.systems, w.gammas, 400)
-    d["oracle"] = {"paths_per_s": v, "cores": cores, "sample": f"{n} paths ({dt:.1f} s)"}
-    emit(d)
+    def config2():
+        w = configs.cyclic7_batch()
+        hb = P.phc_make_homotopy_batch(w.systems, w.gammas)
+        hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
+        ms = _timed(lambda: out.__setitem__("r", P.track(hb)), 3)
+        d = {"config": 2, "workload": "cyclic 7 + 8 random copies, 45,360 paths, one batch launch",
+             "paths_per_s": 45360 / (ms / 1e3), "ms": ms}
+        d.update(summary([out["r"]], [unit_flops(homotopy_terms(w.systems[0]), 7)], ms))
+        ms1 = _timed(lambda: [P.track(x) for x in hs], 3)
+        d["one_launch_per_system"] = {"paths_per_s": 45360 / (ms1 / 1e3), "ms": ms1}
+        d["oracle"] = oracle_part(w.systems, w.gammas, 400, "paths")
+        return d
 
-    # 3: cyclic 8 embedded for dimension 1, top stage + cascade stage (+ dd refinement)
-    w = configs.cyclic8_d1()
-    base, gamma = w.systems[0], w.gammas[0]
-    E = P.phc_embed(base, 1, w.embed["gammas"], w.embed["hyper"])
-    h = P.phc_make_homotopy(E, gamma)
-    fpu = unit_flops(homotopy_terms(E), 9)
+    def config3():
+        w = configs.cyclic8_d1()
+        base, gamma = w.systems[0], w.gammas[0]
+        E = P.phc_embed(base, 1, w.embed["gammas"], w.embed["hyper"])
+        h = P.phc_make_homotopy(E, gamma)
+        fpu = unit_flops(homotopy_terms(E), 9)
 
-    def piped():
-        top, nxt = P.pipeline(h, 1)
-        P.refine(h, top, cond_threshold=1e8)
-        out["r"] = (top, nxt)
+        def piped():
+            top, nxt = P.pipeline(h, 1)
+            P.refine(h, top, cond_threshold=1e8)
+            out["r"] = (top, nxt)
 
-    def staged():
-        top = P.track(h)
-        P.refine(h, top, cond_threshold=1e8)
-        out["s"] = (top, P.cascade_from(h, 1, top))
+        def staged():
+            top = P.track(h)
+            P.refine(h, top, cond_threshold=1e8)
+            out["s"] = (top, P.cascade_from(h, 1, top))
 
-    ms = _timed(piped, 2, 1)
-    d = {"config": 3, "workload": "cyclic 8 embedded D=1: 40,320 paths + cascade stage, pipelined in one launch",
-         "paths_per_s": 40320 / (ms / 1e3), "ms": ms}
-    d.update(summary(list(out["r"]), [fpu, fpu], ms))
-    ms1 = _timed(staged, 2, 1)
-    d["one_launch_per_stage"] = {"paths_per_s": 40320 / (ms1 / 1e3), "ms": ms1}
-    Eo = oracle.embed(base, 1, w.embed["gammas"], w.embed["hyper"])
-    v, cores, n, dt = oracle_sample([Eo], [gamma], 2000)
-    d["oracle"] = {"paths_per_s": v, "cores": cores, "sample": f"{n} top-stage paths ({dt:.1f} s)"}
-    emit(d)
+        ms = _timed(piped, 2, 1)
+        d = {"config": 3, "workload": "cyclic 8 embedded D=1: 40,320 paths + cascade stage, pipelined in one launch",
+             "paths_per_s": 40320 / (ms / 1e3), "ms": ms}
+        d.update(summary(list(out["r"]), [fpu, fpu], ms))
+        ms1 = _timed(staged, 2, 1)
+        d["one_launch_per_stage"] = {"paths_per_s": 40320 / (ms1 / 1e3), "ms": ms1}
+        Eo = oracle.embed(base, 1, w.embed["gammas"], w.embed["hyper"])
+        d["oracle"] = oracle_part([Eo], [gamma], 2000, "top-stage paths")
+        return d
 
-    # 4: 256 sparse systems: phc_track_many vs one launch per system
-    w = configs.sparse_batch()
-    hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
-    npaths = sum(P.phc_num_paths(x) for x in hs)
-    fpus = [unit_flops(homotopy_terms(s), s.n_var) for s in w.systems]
-    ms = _timed(lambda: out.__setitem__("r", P.track_many(hs)), 1, 1)
-    d = {"config": 4, "workload": f"256 sparse systems, n 3..10, {npaths:,} paths, phc_track_many",
-         "paths_per_s": npaths / (ms / 1e3), "ms": ms}
-    d.update(summary(out["r"], fpus, ms))
-    ms1 = _timed(lambda: [P.track(x) for x in hs], 1, 1)
-    d["one_launch_per_system"] = {"paths_per_s": npaths / (ms1 / 1e3), "ms": ms1}
-    v, cores, n, dt = oracle_sample(w.systems[:40], w.gammas[:40], 100)
-    d["oracle"] = {"paths_per_s": v, "cores": cores, "sample": f"{n} paths of 40 systems ({dt:.1f} s)"}
-    emit(d)
+    def config4():
+        w = configs.sparse_batch()
+        hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
+        npaths = sum(P.phc_num_paths(x) for x in hs)
+        fpus = [unit_flops(homotopy_terms(s), s.n_var) for s in w.systems]
+        ms = _timed(lambda: out.__setitem__("r", P.track_many(hs)), 1, 1)
+        d = {"config": 4, "workload": f"256 sparse systems, n 3..10, {npaths:,} paths, phc_track_many",
+             "paths_per_s": npaths / (ms / 1e3), "ms": ms}
+        d.update(summary(out["r"], fpus, ms))
+        ms1 = _timed(lambda: [P.track(x) for x in hs], 1, 1)
+        d["one_launch_per_system"] = {"paths_per_s": npaths / (ms1 / 1e3), "ms": ms1}
+        d["oracle"] = oracle_part(w.systems[:40], w.gammas[:40], 100, "paths of 40 systems")
+        return d
 
-    # 5: serving
-    sv, reqs = serving_session(args.requests, not args.no_big, args.slots)
-    d = {"config": 5, "workload": f"{args.requests} Poisson (200/s) sparse requests"
-         + ("" if args.no_big else " + cyclic 9 D=2 (362,880 paths, two cascade stages)"),
-         "paths_per_s": sv["paths_per_s"], "tracked_paths_per_s": sv["tracked_paths_per_s"], "wall_s": sv["wall_s"],
-         "latency_small": sv["latency_small"], "latency_cyclic9_d2": sv.get("latency_cyclic9_d2"),
-         "clocks": sv["clocks"]}
-    v, cores, n, dt = oracle_sample([r.system for r in reqs[:40]], [r.gamma for r in reqs[:40]], 100)
-    d["oracle"] = {"paths_per_s": v, "cores": cores, "sample": f"{n} paths of 40 requests ({dt:.1f} s)"}
-    emit(d)
+    def config5():
+        sv, reqs = serving_session(args.requests, not args.no_big, args.slots)
+        d = {"config": 5, "workload": f"{args.requests} Poisson (200/s) sparse requests"
+             + ("" if args.no_big else " + cyclic 9 D=2 (362,880 paths, two cascade stages)"),
+             "paths_per_s": sv["paths_per_s"], "tracked_paths_per_s": sv["tracked_paths_per_s"],
+             "wall_s": sv["wall_s"], "latency_small": sv["latency_small"],
+             "latency_cyclic9_d2": sv.get("latency_cyclic9_d2"), "clocks": sv["clocks"]}
+        d["oracle"] = oracle_part([r.system for r in reqs[:40]], [r.gamma for r in reqs[:40]], 100,
+                                  "paths of 40 requests")
+        return d
+
+    want = [int(c) for c in args.configs.split(",")] if args.configs else [1, 2, 3, 4, 5]
+    for c in want:
+        print(json.dumps([config1, config2, config3, config4, config5][c - 1]()), flush=True)
     return 0
 
 
@@ -620,6 +621,7 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of Poisson requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: batches of requests on the GPU at once")
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the cyclic 9 request")
+    ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default all)")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--profile-case", nargs="?", const="cyclic7", default=None, choices=["cyclic7", "sparse"],

@@ -792,8 +792,29 @@ extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t
     L.slack_zero2 = slack_zero_next;
     L.stats2 = st2;
     L.has_next_slack = k > 1 ? 1 : 0;
+    const bool tail =
+        o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64 && phc::tail_pipe_supported(L.tab, L.tab2);
+    if (tail) {
+        const int64_t lanes = phc::pipe_lanes(L, o.block_threads, o.max_blocks);
+        if (lanes < 1) return fail(PHC_EUNSUPPORTED, "no launch configuration for %d unknowns", L.tab.n);
+        rc = ensure_handoff(h, lanes);
+        if (rc) return rc;
+        CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));
+        L.handoff = h->d_handoff;
+        L.handoff_n = h->d_tailc;
+        L.idle_n = h->d_tailc + 1;
+        L.tail_q = h->d_tailc + 2;
+        L.tail_units = h->d_tailc + 3;
+        L.drain_frac = o.tail_drain;
+    } else if (h->d_tailc) {
+        CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));
+    }
     cudaError_t e = phc::launch_pipeline(L, o.block_threads, o.max_blocks, s);
     if (e != cudaSuccess) return fail(PHC_ECUDA, "pipeline kernel launch: %s", cudaGetErrorString(e));
+    if (tail) {
+        e = phc::launch_tail_pipe(L, o.max_blocks, s);
+        if (e != cudaSuccess) return fail(PHC_ECUDA, "pipelined tail kernel launch: %s", cudaGetErrorString(e));
+    }
     return PHC_OK;
 }
 

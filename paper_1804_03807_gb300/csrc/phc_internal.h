@@ -103,6 +103,7 @@ struct Handoff {
     double t, h, next_s, nx0, r0, r1, r2, r3, r4;
     int64_t q;
     int32_t sys, streak, steps, since_ck, nck, n_acc, n_rej, n_newt, n_solve, n_f32;
+    int32_t stage;  // pipelined launch: 0 top homotopy, 1 cascade stage
 };
 
 struct TrackLaunch {
@@ -221,6 +222,11 @@ cudaError_t launch_tail_multi(const TrackLaunch &L, int n, const TailMultiSizes 
 bool tail_multi_supported(const TailMultiSizes &z);
 // Lanes a multi-system launch of L runs (for sizing its hand-off buffer).
 int64_t multi_lanes(const TrackLaunch &L, int n, int block_threads, int max_blocks);
+// The paths handed off by a pipelined launch (top stage and cascade stage),
+// one warp per path; the lanes such a launch runs; whether the tail fits.
+cudaError_t launch_tail_pipe(const TrackLaunch &L, int max_blocks, cudaStream_t s);
+int64_t pipe_lanes(const TrackLaunch &L, int block_threads, int max_blocks);
+bool tail_pipe_supported(const DevTables &t1, const DevTables &t2);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,

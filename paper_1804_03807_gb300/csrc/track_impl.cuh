@@ -926,7 +926,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             if (stop < 0 && ++since_ck >= o.max_steps_decade) stop = PHC_STOP_BUDGET;
             if (stop < 0) begin_step();
         }
-        if constexpr (MODE == MODE_SINGLE || MODE == MODE_MULTI) {
+        {
             // most lanes are idle: a path that starts a new step moves to
             // the tail kernel (which repeats this arithmetic exactly, so
             // where a path is finished does not change it)
@@ -954,6 +954,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 hd.n_newt = n_newt;
                 hd.n_solve = n_solve;
                 hd.n_f32 = n_f32;
+                hd.stage = stage;
                 if constexpr (MULTI) {
                     // the lane stays in the warp's claim loop, idle
                     q = -1;
@@ -1047,7 +1048,9 @@ template <int N, int MODE>
 static int64_t lanes_n(const TrackLaunch &L, int bt, int max_blocks)
 {
     const bool f32 = L.o.precision == PHC_PREC_FP32_INTERIOR;
-    const size_t tb = MODE == MODE_MULTI ? (size_t)(bt / 32) * (size_t)L.warp_table_bytes : table_smem_bytes(L.tab);
+    const size_t tb = MODE == MODE_MULTI  ? (size_t)(bt / 32) * (size_t)L.warp_table_bytes
+                      : MODE == MODE_PIPE ? table_smem_bytes(L.tab) + table_smem_bytes(L.tab2)
+                                          : table_smem_bytes(L.tab);
     const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32);
     if (cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
@@ -1089,7 +1092,7 @@ static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_block
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
     L.drain_at = 0;
-    if ((MODE == MODE_SINGLE || MODE == MODE_MULTI) && L.drain_frac > 0.0 && L.handoff) {
+    if (L.drain_frac > 0.0 && L.handoff) {
         const unsigned long long at = (unsigned long long)(L.drain_frac * (double)(grid * bt));
         L.drain_at = at < 1 ? 1 : at;
     }

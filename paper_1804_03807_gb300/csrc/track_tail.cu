@@ -541,6 +541,160 @@ __global__ void __launch_bounds__(128) tail_multi_kernel(const TrackLaunch L, si
     }
 }
 
+// The pipelined tail: one warp per path of a pipelined launch.  A path
+// handed off in the top stage ends there, is classified (lane 0,
+// classify_one on the top table) and, when regular with z_k != 0, starts
+// the cascade stage from its endpoint in the same warp, exactly as the
+// pipelined tracker continues it in the same lane.
+template <int N>
+__global__ void __launch_bounds__(128) tail_pipe_kernel(const TrackLaunch L, size_t t1_bytes, size_t t2_bytes,
+                                                        size_t p1_bytes, size_t p2_bytes, int group_slots)
+{
+    extern __shared__ __align__(16) char smem[];
+    const SmTab tb1 = stage_table(L.tab, smem);
+    const SmTab tb2 = stage_table(L.tab2, smem + t1_bytes);
+    const TailPlan plan1 = plan_layout<N>(tb1, smem + t1_bytes + t2_bytes);
+    const TailPlan plan2 = plan_layout<N>(tb2, smem + t1_bytes + t2_bytes + p1_bytes);
+    if (threadIdx.x == 0) {
+        plan_fill<N>(tb1, plan1);
+        plan_fill<N>(tb2, plan2);
+    }
+    __syncthreads();
+    constexpr int G = 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int r = threadIdx.x & 31;
+    constexpr int HS = (int)((sizeof(Handoff) + 15) / 16);
+    double2 *base = reinterpret_cast<double2 *>(smem + t1_bytes + t2_bytes + p1_bytes + p2_bytes) +
+                    (size_t)(threadIdx.x >> 5) * (group_slots + HS);
+    Handoff *hs = reinterpret_cast<Handoff *>(base + group_slots);  // the fresh cascade-stage start
+    const phc_opts &o = L.o;
+    const int64_t np = L.n_paths;
+    const unsigned long long n_hand = *reinterpret_cast<volatile const unsigned long long *>(L.handoff_n);
+    ThreadArrays A;  // one-lane classification arrays over the group's slots (stride 1)
+    A.xe = base;
+    A.R = A.xe + N;
+    A.P = A.R + N;
+    A.X = A.P;
+    A.J = A.P + N;
+    A.S = A.J + N * N;
+    for (;;) {
+        unsigned long long slot = 0;
+        if (r == 0) slot = atomicAdd(L.tail_q, 1ull);
+        slot = __shfl_sync(FULL, slot, 0);
+        if (slot >= n_hand) break;
+        const Handoff *cur = &L.handoff[slot];
+        const int64_t q = cur->q;
+        int stage = cur->stage;
+        for (;;) {
+            int cont = 0;
+            const SmTab &tb = stage ? tb2 : tb1;
+            tail_path<N, G>(*cur, tb, stage ? plan2 : plan1, 0, base, o, r, FULL,
+                            [&](double2 x0r, const phc_path_stats &rec0, int units) {
+                                if (r < N) A.xe[r] = x0r;
+                                __syncwarp();
+                                if (r == 0) {
+                                    phc_path_stats rec = rec0;
+                                    const int8_t c = classify_lane<N>(tb, A, rec, o);
+                                    atomicAdd(L.tail_units, (unsigned long long)units);
+                                    if (stage == 0) {
+                                        for (int j = 0; j < N; j++) L.x_out[(int64_t)j * np + q] = A.xe[j];
+                                        L.stats[q] = rec;
+                                        L.cls_out[q] = c;
+                                        if (c == PHC_REGULAR &&
+                                            absinf(A.xe[N - 1]) > o.slack_tol * (1.0 + rec.norm_x)) {
+                                            cont = 1;
+                                        } else {
+                                            L.cls_out2[q] = -1;
+                                        }
+                                    } else {
+                                        double nx = 0.0;
+                                        for (int j = 0; j < N - 1; j++) {
+                                            L.x_out2[(int64_t)j * np + q] = A.xe[j];
+                                            const double a = absinf(A.xe[j]);
+                                            if (!(a <= nx)) nx = a;
+                                        }
+                                        L.stats2[q] = rec;
+                                        L.cls_out2[q] = c;
+                                        L.slack_zero2[q] =
+                                            L.has_next_slack ? (absinf(A.xe[N - 2]) <= o.slack_tol * (1.0 + nx)) : 0;
+                                    }
+                                }
+                                cont = __shfl_sync(FULL, cont, 0);
+                                if (cont) {
+                                    // the state the pipelined tracker gives a fresh path
+                                    if (r < N) hs->x0[r] = x0r;
+                                    if (r == 0) {
+                                        hs->t = 0.0;
+                                        hs->h = o.h_init;
+                                        hs->next_s = 0.1;
+                                        hs->nx0 = 0.0;
+                                        hs->r0 = hs->r1 = hs->r2 = hs->r3 = hs->r4 = 0.0;
+                                        hs->q = q;
+                                        hs->sys = 0;
+                                        hs->streak = hs->steps = hs->since_ck = hs->nck = 0;
+                                        hs->n_acc = hs->n_rej = hs->n_newt = hs->n_solve = hs->n_f32 = 0;
+                                        hs->stage = 1;
+                                    }
+                                }
+                                __syncwarp();
+                            });
+            if (!cont) break;
+            stage = 1;
+            cur = hs;
+        }
+    }
+}
+
+template <int N>
+static cudaError_t launch_tail_pipe_n(const TrackLaunch &L_in, int max_blocks, cudaStream_t s)
+{
+    TrackLaunch L = L_in;
+    L.tab.coef_smem = L.tab2.coef_smem = 1;
+    const size_t t1 = table_smem_bytes(L.tab), t2 = table_smem_bytes(L.tab2);
+    const size_t p1 = tail_plan_bytes(N, L.tab.n_terms, L.tab.n_ve), p2 = tail_plan_bytes(N, L.tab2.n_terms, L.tab2.n_ve);
+    const int S1 = tail_store_slots(L.tab.n_terms, L.tab.n_ve), S2 = tail_store_slots(L.tab2.n_terms, L.tab2.n_ve);
+    const int gs = tail_group_slots(N, S1 > S2 ? S1 : S2);
+    const size_t per_warp = (size_t)(gs + (sizeof(Handoff) + 15) / 16) * sizeof(double2);
+    int warps = 4;
+    while (warps > 1 && t1 + t2 + p1 + p2 + warps * per_warp > (size_t)g_smem_optin) warps /= 2;
+    const size_t smem = t1 + t2 + p1 + p2 + warps * per_warp;
+    if (smem > (size_t)g_smem_optin) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(tail_pipe_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tail_pipe_kernel<N>, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = g_num_sms * per_sm;
+    if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+    tail_pipe_kernel<N><<<grid, warps * 32, smem, s>>>(L, t1, t2, p1, p2, gs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tail_pipe(const TrackLaunch &L, int max_blocks, cudaStream_t s)
+{
+    device_limits();
+#define PHC_CALL_TAILP(NN) launch_tail_pipe_n<NN>(L, max_blocks, s)
+    PHC_DISPATCH_N(L.tab.n, PHC_CALL_TAILP)
+#undef PHC_CALL_TAILP
+}
+
+bool tail_pipe_supported(const DevTables &t1_in, const DevTables &t2_in)
+{
+    device_limits();
+    const int n = t1_in.n;
+    if (n < 2 || n > PHC_MAX_VARS) return false;
+    DevTables t1 = t1_in, t2 = t2_in;
+    t1.coef_smem = t2.coef_smem = 1;
+    const int S1 = tail_store_slots(t1.n_terms, t1.n_ve), S2 = tail_store_slots(t2.n_terms, t2.n_ve);
+    if (S1 >= (1 << 14) || S2 >= (1 << 14)) return false;
+    const size_t need = table_smem_bytes(t1) + table_smem_bytes(t2) + tail_plan_bytes(n, t1.n_terms, t1.n_ve) +
+                        tail_plan_bytes(n, t2.n_terms, t2.n_ve) +
+                        (size_t)(tail_group_slots(n, S1 > S2 ? S1 : S2) + (sizeof(Handoff) + 15) / 16) *
+                            sizeof(double2);
+    return need <= (size_t)g_smem_optin;
+}
+
 template <int N, int G>
 static cudaError_t launch_tail_n(const TrackLaunch &L_in, int max_blocks, cudaStream_t s)
 {

@@ -122,3 +122,29 @@ def test_tail_handoff_bit_identical_many_systems():
     for o in (_opts(0.85), _opts(1e-9, tiny_grid=True)):
         for a, b in zip(base, run(o)):
             _same(a, b, "track_many with the tail hand-off")
+
+
+def _stage_outputs(top, nxt):
+    """Host copies of a pipelined launch: the top stage whole, the cascade
+    stage on the entries it tracked (cls >= 0; the others are not written)."""
+    c2 = nxt.cls.cpu().numpy()
+    ok = c2 >= 0
+    return [top.x.cpu().numpy(), top.cls.cpu().numpy(), top.stats.cpu().numpy(), c2,
+            nxt.x.cpu().numpy()[:, ok], nxt.stats.cpu().numpy()[ok], nxt.slack_zero.cpu().numpy()[ok]]
+
+
+@pytest.mark.parametrize("D", [1, 3])
+def test_tail_handoff_bit_identical_pipeline(D):
+    """phc_track_pipeline (top stage and cascade stage in one launch): paths
+    handed off in either stage finish in the pipelined tail kernel with the
+    same bits, including those that move on to the cascade stage there."""
+    sys = multistep_example() if D == 3 else cyclic(5)
+    rng = rng_for(50 + D)
+    g, hy = embedding_constants(rng, sys.n_eq, sys.n_var, D)
+    gamma = unit_gamma(rng)
+    h = P.phc_make_homotopy(P.phc_embed(sys, D, g, hy), gamma)
+    base = _stage_outputs(*P.pipeline(h, D, opts=_opts(0.0)))
+    assert P.phc_tail_paths(h) == 0
+    for o in (_opts(0.85), _opts(1e-9, tiny_grid=True)):
+        _same(base, _stage_outputs(*P.pipeline(h, D, opts=o)), "pipeline with the tail hand-off")
+    assert P.phc_tail_paths(h) > 0
