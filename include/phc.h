@@ -194,6 +194,9 @@ int phc_num_paths(const phc_homotopy *h, int64_t *out);
  * classify the endpoints.  opts may be NULL (defaults).
  * Outputs (device, caller-owned): x_out SoA [n_var][n_paths] phc_cd,
  * cls_out [n_paths] int8 (PHC_REGULAR ...), stats_out [n_paths] or NULL.
+ * A call with sizes and options that an earlier call on h already had
+ * allocates nothing and does not synchronise with the host (stream-ordered
+ * memsets and kernel launches only), so it can be captured in a CUDA graph.
  * Errors: PHC_EINVAL for a NULL handle or output, a range outside
  * [0, num_paths), or invalid options; PHC_ECUDA. */
 int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_out,

@@ -148,3 +148,31 @@ def test_tail_handoff_bit_identical_pipeline(D):
     for o in (_opts(0.85), _opts(1e-9, tiny_grid=True)):
         _same(base, _stage_outputs(*P.pipeline(h, D, opts=o)), "pipeline with the tail hand-off")
     assert P.phc_tail_paths(h) > 0
+
+
+def test_track_paths_replays_in_a_cuda_graph():
+    """After one call with the same sizes (which allocates the handle's
+    scratch), phc_track_paths issues no allocation and no host
+    synchronisation: its launches (counters, tracker, tail, classification)
+    capture into a CUDA graph, and each replay gives the same bytes."""
+    import torch
+    w = configs.cyclic_batch(n=5, copies=3)
+    h = P.phc_make_homotopy_batch(w.systems, w.gammas)
+    n = P.phc_num_paths(h)
+    x = torch.empty((h.n, n), dtype=torch.complex128, device="cuda")
+    cls = torch.empty(n, dtype=torch.int8, device="cuda")
+    st = torch.empty((n, P.STATS_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+    P.phc_track_paths(h, 0, n, None, x, cls, st)
+    torch.cuda.synchronize()
+    ref = [x.cpu().numpy(), cls.cpu().numpy(), st.cpu().numpy()]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        P.phc_track_paths(h, 0, n, None, x, cls, st)
+    for _ in range(2):
+        x.zero_()
+        cls.fill_(-7)
+        st.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        _same(ref, [x.cpu().numpy(), cls.cpu().numpy(), st.cpu().numpy()], "graph replay")
+    assert P.phc_tail_paths(h) > 0
