@@ -555,6 +555,16 @@ def run_configs(args):
         d.update(summary(out["r"], fpus, ms))
         ms1 = _timed(lambda: [P.track(x) for x in hs], 1, 1)
         d["one_launch_per_system"] = {"paths_per_s": npaths / (ms1 / 1e3), "ms": ms1}
+        # launch parameters chosen by the project's tuner on a sample of the systems
+        from paper_1804_03807_gb300 import autotune
+        t0 = time.perf_counter()
+        o = autotune.tune_many(hs, sample_systems=16,
+                               grid={"tail_threads": (16, 32), "tail_drain": (0.85, 0.95), "block_threads": (0, 128)})
+        tune_s = time.perf_counter() - t0
+        ms2 = _timed(lambda: P.track_many(hs, opts=o), 1, 1)
+        d["autotuned"] = {"paths_per_s": npaths / (ms2 / 1e3), "ms": ms2, "tuning_s": tune_s,
+                          "opts": {"tail_threads": o.tail_threads, "tail_drain": o.tail_drain,
+                                   "block_threads": o.block_threads}}
         d["oracle"] = oracle_part(w.systems[:40], w.gammas[:40], 100, "paths of 40 systems")
         return d
 
