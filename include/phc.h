@@ -113,12 +113,12 @@ typedef struct {
     double fp32_pivot_ratio; /* FP32_INTERIOR: largest pivot spread accepted */
     int32_t block_threads;   /* threads per block; 0 = chosen by the library */
     int32_t max_blocks;      /* grid size cap; 0 = one wave of resident blocks */
-    double tail_drain;       /* FP64, phc_track_paths / phc_cascade_stage / phc_cascade_from: once
-                                this fraction of the tracker's threads has found no path left to
-                                claim, every path that starts a new step moves to a kernel that
-                                gives each path a group of threads (one per equation); the
-                                arithmetic is the same, operation for operation, so the results do
-                                not change.  0 = never. */
+    double tail_drain;       /* every tracking call: once this fraction of the tracker's threads
+                                has found no path left to claim, every path that starts a new step
+                                moves to a tail kernel that gives each path a group of threads
+                                (FP32_INTERIOR: only paths whose remaining steps are all double);
+                                the arithmetic is the same, operation for operation, so the
+                                results do not change.  0 = never. */
     int32_t tail_threads;    /* threads per path in that kernel: 8 (N <= 8), 16 or 32; 0 = 32 */
 } phc_opts;
 

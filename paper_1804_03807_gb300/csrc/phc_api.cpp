@@ -478,7 +478,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.stats = stats;
     L.qhead = h->d_qhead;
     L.o = o;
-    const bool tail = o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64 && phc::tail_supported(L.tab);
+    const bool tail = o.tail_drain > 0.0 && phc::tail_supported(L.tab);
     if (tail) {
         const int64_t lanes = phc::track_lanes(L, o.block_threads, o.max_blocks);
         if (lanes < 1) return fail(PHC_EUNSUPPORTED, "no launch configuration for %d unknowns", tab.n);
@@ -679,7 +679,7 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
         L.warp_table_bytes = wtb;
         // tail hand-off (double precision): buffer for one record per lane
         const bool tail =
-            o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64 && phc::tail_multi_supported(tz);
+            o.tail_drain > 0.0 && phc::tail_multi_supported(tz);
         const int64_t lanes = tail ? phc::multi_lanes(L, n, o.block_threads, o.max_blocks) : 0;
         const size_t head = m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long) + (m + 1) * sizeof(int64_t);
         const size_t hoff = (head + 255) & ~(size_t)255;
@@ -793,7 +793,7 @@ extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t
     L.stats2 = st2;
     L.has_next_slack = k > 1 ? 1 : 0;
     const bool tail =
-        o.tail_drain > 0.0 && o.precision == PHC_PREC_FP64 && phc::tail_pipe_supported(L.tab, L.tab2);
+        o.tail_drain > 0.0 && phc::tail_pipe_supported(L.tab, L.tab2);
     if (tail) {
         const int64_t lanes = phc::pipe_lanes(L, o.block_threads, o.max_blocks);
         if (lanes < 1) return fail(PHC_EUNSUPPORTED, "no launch configuration for %d unknowns", L.tab.n);

@@ -930,7 +930,12 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             // most lanes are idle: a path that starts a new step moves to
             // the tail kernel (which repeats this arithmetic exactly, so
             // where a path is finished does not change it)
+            // (FP32 interior: only a path whose remaining steps are all double
+            // precision -- t already at fp32_t_max, so every later step ends
+            // beyond it even after rejections, or fallen back for good --
+            // since the tail kernel computes in double only)
             if (stop < 0 && act != ACT_NONE && phase == 0 && L.drain_at &&
+                (!interior32 || fp32_off || t >= o.fp32_t_max) &&
                 *reinterpret_cast<volatile unsigned long long *>(L.idle_n) >= L.drain_at) {
                 Handoff &hd = L.handoff[atomicAdd(L.handoff_n, 1ull)];
                 for (int j = 0; j < N; j++) hd.x0[j] = x0[j];

@@ -176,3 +176,20 @@ def test_track_paths_replays_in_a_cuda_graph():
         torch.cuda.synchronize()
         _same(ref, [x.cpu().numpy(), cls.cpu().numpy(), st.cpu().numpy()], "graph replay")
     assert P.phc_tail_paths(h) > 0
+
+
+def test_tail_handoff_bit_identical_fp32_interior():
+    """FP32 interior: only paths whose remaining steps are all double move to
+    the tail kernel; the results stay byte-identical."""
+    w = configs.cyclic_batch(n=5, copies=3)
+    h = P.phc_make_homotopy_batch(w.systems, w.gammas)
+
+    def run(o):
+        o.precision = P.PHC_PREC_FP32_INTERIOR
+        return P.track(h, opts=o)
+
+    base = _host(run(_opts(0.0)))
+    assert P.stats_numpy(run(_opts(0.0)).stats)["n_fp32"].sum() > 0
+    for o in (_opts(0.85), _opts(1e-9, tiny_grid=True)):
+        _same(base, _host(run(o)), "FP32 interior with the tail hand-off")
+    assert P.phc_tail_paths(h) > 0
