@@ -25,15 +25,27 @@
 
 namespace phc {
 
-template <int G>
+// Smallest power of two >= N: the lanes that hold rows of the group.
+template <int N>
+__host__ __device__ constexpr int rows_pow2()
+{
+    return N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16;
+}
+
+// Maximum over the group of non-negative, non-NaN doubles held by its first
+// P2 lanes, in every lane.  The bit pattern of a non-negative double orders
+// like its value, so the comparisons are integer ones (the FP64 pipe, which
+// bounds these kernels, is spared); the result is the same maximum.
+template <int G, int P2>
 __device__ __forceinline__ double gmax(double v, unsigned mask)
 {
+    unsigned long long k = (unsigned long long)__double_as_longlong(v);
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        const double w = __shfl_xor_sync(mask, v, o, G);
-        v = (w > v) ? w : v;
+    for (int o = P2 / 2; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(mask, k, o, G);
+        k = (w > k) ? w : k;
     }
-    return v;
+    return __longlong_as_double((long long)__shfl_sync(mask, k, 0, G));
 }
 
 // add_term's pieces of one term, kept in the term's slots of the group's
@@ -152,6 +164,7 @@ __device__ __forceinline__ void tail_path(const Handoff &hd, const SmTab &tb, co
                                           double2 *base, const phc_opts &o, int r, unsigned gmask, Finish &&finish)
 {
     constexpr int E = N * N + N;
+    constexpr int P2 = rows_pow2<N>();
     const int T = tb.n_terms;
     double2 *xe = base;          // [N]
     double2 *R = base + N;       // [N]
@@ -225,19 +238,30 @@ __device__ __forceinline__ void tail_path(const Handoff &hd, const SmTab &tb, co
 #pragma unroll
         for (int k = 0; k < N; k++) {
             const double vk = abs1(J[k * N + k]);
-            // candidates: rows i > k with a larger |.|_1 (the first on ties)
-            double bv = (own && r > k) ? abs1(J[r * N + k]) : -1.0;
-            if (!(bv == bv)) bv = -1.0;
-            int bi = (own && r > k) ? r : N;
+            // candidates: rows i > k with a larger |.|_1 (the first on ties);
+            // keyed by the bit pattern of |.|_1 (integer compares), a row
+            // without a candidate (or with a NaN) by 0 and the index N
+            unsigned long long key = 0ull;
+            int bi = N;
+            if (own && r > k) {
+                const double a = abs1(J[r * N + k]);
+                if (a == a) {
+                    key = (unsigned long long)__double_as_longlong(a);
+                    bi = r;
+                }
+            }
 #pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) {
-                const double ov = __shfl_xor_sync(gmask, bv, off, G);
+            for (int off = P2 / 2; off > 0; off >>= 1) {
+                const unsigned long long ok2 = __shfl_xor_sync(gmask, key, off, G);
                 const int oi = __shfl_xor_sync(gmask, bi, off, G);
-                if (ov > bv || (ov == bv && oi < bi)) {
-                    bv = ov;
+                if (ok2 > key || (ok2 == key && oi < bi)) {
+                    key = ok2;
                     bi = oi;
                 }
             }
+            key = __shfl_sync(gmask, key, 0, G);
+            bi = __shfl_sync(gmask, bi, 0, G);
+            const double bv = __longlong_as_double((long long)key);
             int p = k;
             double best = vk;
             if (bi < N && bv > best) {
@@ -335,8 +359,8 @@ __device__ __forceinline__ void tail_path(const Handoff &hd, const SmTab &tb, co
                 fl = finite2(xj);
             }
             const bool fin = __all_sync(gmask, fl);
-            const double d = fin ? gmax<G>(a, gmask) : NAN;
-            const double nx = fin ? gmax<G>(c, gmask) : NAN;
+            const double d = fin ? gmax<G, P2>(a, gmask) : NAN;
+            const double nx = fin ? gmax<G, P2>(c, gmask) : NAN;
             if (phase == 4) {
                 if (!ok || !(d == d) || !fin) act = ACT_REJECT;
                 else if (d <= o.corr_tol * (1.0 + nx)) act = ACT_ACCEPT;
@@ -357,7 +381,7 @@ __device__ __forceinline__ void tail_path(const Handoff &hd, const SmTab &tb, co
         if (act == ACT_ACCEPT) {
             t = t1;
             if (own) x0r = xe[r];
-            const double nx = gmax<G>(own ? absinf(x0r) : 0.0, gmask);
+            const double nx = gmax<G, P2>(own ? absinf(x0r) : 0.0, gmask);
             n_acc++;
             steps++;
             while (1.0 - t <= next_s && next_s > 0.0) {
