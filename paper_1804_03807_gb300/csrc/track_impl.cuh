@@ -1006,7 +1006,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             L.stats[q] = rec;
             q = -1;
             continue;
-        }
+        } else {
         // modes 1 and 2 classify here
 #pragma unroll
         for (int j = 0; j < N; j++) SL(A.xe, j) = x0[j];
@@ -1042,6 +1042,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             L.slack_zero2[q] = L.has_next_slack ? (absinf(x0[N - 2]) <= o.slack_tol * (1.0 + nx)) : 0;
         }
         q = -1;
+        }
     }
 }
 

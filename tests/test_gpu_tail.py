@@ -1,9 +1,9 @@
-"""The row-parallel tail kernel changes nothing but where a path is finished.
+"""The tail kernels change nothing but where a path is finished.
 
 When most threads of a tracking launch have run out of paths, the paths
 that are still running move, at the start of their next step, to a kernel
-that gives every path one thread per equation (opts.tail_drain).  That
-kernel performs the same floating point operations in the same order, so
+that gives every path a group of threads (opts.tail_drain, opts.tail_threads).
+That kernel performs the same floating point operations in the same order, so
 endpoints, classes and every per-path statistic must be identical, bit for
 bit, to a run without the hand-off.  Each case runs with the hand-off off;
 with the default; and, for every group size of the tail kernel, on a
