@@ -559,7 +559,7 @@ def run_configs(args):
         from paper_1804_03807_gb300 import autotune
         t0 = time.perf_counter()
         o = autotune.tune_many(hs, sample_systems=16,
-                               grid={"tail_threads": (16, 32), "tail_drain": (0.85, 0.95), "block_threads": (0, 128)})
+                               grid={"tail_threads": (16, 32), "tail_drain": (0.8, 0.9), "block_threads": (0, 128)})
         tune_s = time.perf_counter() - t0
         ms2 = _timed(lambda: P.track_many(hs, opts=o), 1, 1)
         d["autotuned"] = {"paths_per_s": npaths / (ms2 / 1e3), "ms": ms2, "tuning_s": tune_s,

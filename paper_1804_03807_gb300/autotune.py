@@ -21,7 +21,7 @@ from ._lib import phc_default_opts, phc_num_paths, phc_opts
 GRID = {
     "block_threads": (0, 128),
     "tail_threads": (16, 32),
-    "tail_drain": (0.7, 0.85, 0.95),
+    "tail_drain": (0.7, 0.8, 0.9),
 }
 
 _cache: dict = {}

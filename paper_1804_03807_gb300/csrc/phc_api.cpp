@@ -71,7 +71,7 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->fp32_pivot_ratio = 1e4;
     o->block_threads = 0;
     o->max_blocks = 0;
-    o->tail_drain = 0.85;
+    o->tail_drain = 0.8;
     o->tail_threads = 0;
     return PHC_OK;
 }

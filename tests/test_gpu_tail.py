@@ -47,7 +47,7 @@ def _three_ways(run, h):
     for this number of unknowns; returns the results and the fewest paths moved."""
     base = _host(run(_opts(0.0)))
     assert P.phc_tail_paths(h) == 0
-    dflt = _host(run(_opts(0.85)))
+    dflt = _host(run(_opts(0.8)))
     _same(base, dflt, "default drain")
     moved = []
     for group in ([8] if h.n <= 8 else []) + [16, 32]:
