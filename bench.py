@@ -154,6 +154,12 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def replica_value(world: int, paths_per_rank: int, steps: int, max_total_ms: float) -> float:
+    """Whole-job paths/s of N independent replicas: every rank tracks the same
+    workload, timed by the slowest rank (weak scaling)."""
+    return world * paths_per_rank * steps / (max_total_ms / 1e3)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -285,7 +291,7 @@ def run_gpu(args):
     barrier(world)
     clocks = clk.summary()
     total_ms = max_over_ranks(float(np.sum(times)), world, dev)
-    value = world * total_paths * args.steps / (total_ms / 1e3)
+    value = replica_value(world, total_paths, args.steps, total_ms)
 
     # roofline of track_kernel: algorithmic flops / duration of the tracking
     # call; units done in single precision count against the FP32 peak
