@@ -177,7 +177,7 @@ int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *terms_per_eq, co
                             const phc_cd *coefs, const phc_cd *gammas, phc_homotopy **out);
 
 /* Paths that the last tracking call on h (phc_track_paths, phc_cascade_stage,
- * phc_cascade_from) moved to the row-parallel tail kernel (opts.tail_drain),
+ * phc_cascade_from, phc_track_pipeline) moved to a tail kernel (opts.tail_drain),
  * and the evaluate+solve units those paths ran there (units_out may be
  * NULL); 0 when no such call ran or the option was 0.  Host call: waits for
  * cuda_stream (the stream of that call) before reading the device counters.
@@ -254,8 +254,10 @@ int phc_cascade_from(const phc_homotopy *embedded_k, int k, const phc_cd *x_prev
  * one launch: each warp works on one system at a time with that system's
  * tables in its own shared memory, its lanes refill from the system's path
  * queue, and a warp whose lanes are all idle moves on to a system with
- * unclaimed paths.  hs: host array of n_h single-system handles; x_out,
- * cls_out, stats_out: host arrays of n_h device pointers, each as the
+ * unclaimed paths; once every path is claimed, paths still running move
+ * to a tail kernel (one warp per path, opts.tail_drain).  hs: host array
+ * of n_h single-system handles; x_out, cls_out, stats_out: host arrays of
+ * n_h device pointers, each as the
  * corresponding argument of phc_track_paths for that handle (stats_out or
  * any of its entries may be NULL).  The results equal n_h phc_track_paths
  * calls.  Errors: PHC_EINVAL for NULL or batch handles and NULL outputs,
@@ -270,7 +272,9 @@ int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_c
  * endpoint as its path ends and, when it is regular with z_k != 0
  * (|z_k| > slack_tol (1 + ||x||)), continues the same GPU thread on the
  * cascade homotopy E_k -> E_{k-1} from it, so stage k-1 starts while stage
- * k is still running and no host round trip separates them.
+ * k is still running and no host round trip separates them; paths still
+ * running when most threads are idle finish, in either stage, in a tail
+ * kernel (opts.tail_drain) that continues them the same way.
  * Outputs (device, caller-owned): the top stage as phc_track_paths (x_top
  * SoA [n_var][n_paths], cls_top [n_paths], stats_top or NULL) and, per top
  * path, the stage below: x_next SoA [n_var - 1][n_paths], cls_next (-1 where
