@@ -337,6 +337,8 @@ def run_gpu(args):
                    "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas x{world}", "classes_last_step": counts.tolist()},
         "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+        # Newton corrections (corrector and end game) per second of the same steps, all ranks
+        "newton_steps_per_s": world * int(stn["n_newton"].sum()) * args.steps / (total_ms / 1e3),
     }
     if rank == 0 and world == 1 and args.serving_requests > 0:
         # served latency: Poisson arrivals of small requests (the third figure of the metric)
