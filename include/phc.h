@@ -7,7 +7,10 @@
  * and the cascade of homotopies down to dimension zero (Verschelde, "A
  * Blackbox Polynomial System Solver on Parallel Shared Memory Computers",
  * Sections 2 and 3).  Paths are independent (Section 1), so every path is
- * tracked by one GPU thread; all compute runs in the library's CUDA kernels.
+ * tracked by one GPU thread, and the paths still running when most threads
+ * are idle finish in tail kernels that give each one a warp (with the same
+ * arithmetic, so results do not depend on where a path finishes); all
+ * compute runs in the library's CUDA kernels.
  *
  * Conventions
  *  - Every function returns PHC_OK (0) or a negative PHC_E* code; the message
@@ -22,6 +25,9 @@
  *  - Endpoint arrays are structs of arrays: x[j * n_paths + p] is unknown j
  *    of path p ("SoA [n_var][n_paths]").
  *  - A per-path numerical failure is not an error: it is class PHC_FAILED.
+ *  - A handle keeps per-call scratch (queue and hand-off counters, records):
+ *    tracking calls on one handle must not overlap on the GPU (issue them on
+ *    one stream, or order the streams); different handles are independent.
  *  - The library never exits, aborts or traps on the device.
  */
 #ifndef PHC_H
