@@ -253,7 +253,7 @@ def run_gpu(args):
         opts.block_threads = args.block_threads
     if args.tail_threads:
         opts.tail_threads = args.tail_threads
-    tail_on = opts.tail_drain > 0 and args.precision == 0
+    tail_on = opts.tail_drain > 0  # FP32 interior too: its double-only paths hand off
     launches_per_step = 4 if tail_on else 3  # track, (tail,) classify, refine
 
     def step(pair=None):
