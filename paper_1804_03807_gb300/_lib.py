@@ -196,7 +196,7 @@ def phc_num_paths(h: Homotopy) -> int:
 
 
 def phc_tail_paths(h: Homotopy, stream=None, units: bool = False):
-    """Paths the last tracking call on h handed to the row-parallel tail
+    """Paths the last tracking call on h handed to a tail
     kernel (with units=True: (paths, units run in the tail kernel))."""
     v = ctypes.c_int64()
     u = ctypes.c_int64()

@@ -97,7 +97,7 @@ struct SysDesc {
 };
 
 // The state of a path at the start of a step, handed from the tracker to
-// the row-parallel tail kernel when most lanes have run out of paths.
+// a tail kernel when most lanes have run out of paths.
 struct Handoff {
     double2 x0[PHC_MAX_VARS];
     double t, h, next_s, nx0, r0, r1, r2, r3, r4;

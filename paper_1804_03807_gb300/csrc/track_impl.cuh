@@ -17,7 +17,11 @@
 // so lanes at different points of their paths still execute the same
 // arithmetic together.  A lane whose path ends writes its endpoint and takes
 // the next path index from a global atomic counter (the GPU form of the work
-// crew of Section 1).  Classification runs afterwards in classify_kernel.
+// crew of Section 1).  Classification runs afterwards in classify_kernel
+// (mode 0) or inline (modes 1 and 2).  Once most lanes find the counter
+// exhausted, paths that start a new step save their state and leave for the
+// tail kernels of track_tail.cu, which finish them a warp per path with the
+// same arithmetic (add_term, the LU's operation order, lu_solve's order).
 //
 // The step logic follows the readings documented in include/phc.h; the CPU
 // oracle implements the same readings independently.
@@ -438,7 +442,7 @@ __device__ __forceinline__ void lu_solve(const double2 *J, const int (&perm)[N],
         st(b, i, bt, s);
     }
     // back substitution, columns from the last to the first (the order the
-    // row-parallel tail kernel uses, so both produce the same rounding)
+    // tail kernels use, so both produce the same rounding)
 #pragma unroll
     for (int i = N - 1; i >= 0; i--) {
         C s = ld<C>(b, i, bt);
