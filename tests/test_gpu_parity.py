@@ -175,6 +175,35 @@ def test_cyclic8_embedded_sampled_paths():
     assert (d <= RTOL).mean() >= 0.99
 
 
+def test_cyclic9_d2_top_stage_sampled_paths():
+    """The large request of the serving workload: cyclic 9 embedded for top
+    dimension 2 (11 unknowns, 362,880 paths) tracked whole on the GPU; a
+    seeded sample of 240 paths re-tracked by the oracle path by path."""
+    w = configs.serving(n_requests=1, big=(9, 2))
+    b = w.extra["big"]
+    E = P.phc_embed(b["system"], b["top_dim"], b["gammas"], b["hyper"])
+    h = P.phc_make_homotopy(E, b["gamma"])
+    r = P.track(h)
+    cg = r.cls.cpu().numpy()
+    xg = r.x.cpu().numpy().T
+    assert len(cg) == 362880
+    e = oracle.embed(b["system"], b["top_dim"], b["gammas"], b["hyper"])
+    reg = cg == P.PHC_REGULAR
+    assert reg.any() and relative_residual(e, xg[reg]).max() <= 1e-12
+    idx = np.sort(rng_for(610).choice(362880, 240, replace=False))
+    ho = oracle.total_degree(e, b["gamma"])
+    xo = np.zeros((len(idx), e.n_var), complex)
+    co = np.zeros(len(idx), np.int8)
+    for k, p in enumerate(idx):
+        x1, c1, _ = oracle.track(ho, first=int(p), n_paths=1, threads=1)
+        xo[k], co[k] = x1[0], c1[0]
+    same_cls = cg[idx] == co
+    assert same_cls.mean() >= 0.99, f"{(~same_cls).sum()} of {len(idx)} sampled paths differ in class"
+    both = (cg[idx] == 0) & (co == 0)
+    d = np.max(np.abs(xg[idx][both] - xo[both]), axis=1) / (1 + np.max(np.abs(xo[both]), axis=1))
+    assert (d <= RTOL).mean() >= 0.99
+
+
 def _embedded_top(sys, D, seed):
     rng = rng_for(seed)
     g, hy = embedding_constants(rng, sys.n_eq, sys.n_var, D)
