@@ -342,7 +342,7 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and args.serving_requests > 0:
         # served latency: Poisson arrivals of small requests (the third figure of the metric)
-        sv, _ = serving_session(args.serving_requests, False, args.slots)
+        sv, _ = serving_session(args.serving_requests, False, args.slots, args.batch_paths)
         line["serving"] = {k: sv[k] for k in ("requests", "rate_per_s", "wall_s", "tracked_paths_per_s",
                                               "offered_small_paths_per_s", "latency_small")}
         line["serving"]["workload"] = (f"{args.serving_requests} Poisson (200/s) sparse requests, "
@@ -397,7 +397,7 @@ def end_to_end(P, systems, gammas, dev, args):
             "steps": reps}
 
 
-def serving_session(n_requests: int, big: bool, slots: int):
+def serving_session(n_requests: int, big: bool, slots: int, batch_paths: int = 60_000):
     """Continuous batching of Poisson arrivals (200/s) of sparse requests,
     optionally with cyclic 9 embedded for top dimension 2 (362,880 paths, two
     cascade stages) arriving first; returns the measurement and the requests."""
@@ -412,7 +412,7 @@ def serving_session(n_requests: int, big: bool, slots: int):
         b = w.extra["big"]
         reqs.append(serving.Request(len(reqs), b["system"], b["gamma"], b["arrival"], b["top_dim"], b["gammas"],
                                     b["hyper"]))
-    srv = serving.Server(slots=2, max_inflight=slots)
+    srv = serving.Server(slots=2, max_inflight=slots, batch_paths=batch_paths)
     srv.run(reqs[:8], realtime=False)  # warm-up: kernels loaded, allocator primed
     with ClockSampler(0) as clk:
         t0 = time.perf_counter()
@@ -438,7 +438,7 @@ def run_serving(args):
     from paper_1804_03807_gb300 import build as pbuild
     pbuild.build()
     torch.cuda.set_device(0)
-    sv, reqs = serving_session(args.requests, not args.no_big, args.slots)
+    sv, reqs = serving_session(args.requests, not args.no_big, args.slots, args.batch_paths)
     line = {"metric": METRIC, "workload": "serving", "value": sv["paths_per_s"], "unit": "paths/s",
             "tracked_paths_per_s": sv["tracked_paths_per_s"], "n_requests": sv["requests"], "wall_s": sv["wall_s"],
             "latency_small": sv["latency_small"], "latency_cyclic9_d2": sv.get("latency_cyclic9_d2", {"count": 0}),
@@ -577,7 +577,7 @@ def run_configs(args):
         return d
 
     def config5():
-        sv, reqs = serving_session(args.requests, not args.no_big, args.slots)
+        sv, reqs = serving_session(args.requests, not args.no_big, args.slots, args.batch_paths)
         d = {"config": 5, "workload": f"{args.requests} Poisson (200/s) sparse requests"
              + ("" if args.no_big else " + cyclic 9 D=2 (362,880 paths, two cascade stages)"),
              "paths_per_s": sv["paths_per_s"], "tracked_paths_per_s": sv["tracked_paths_per_s"],
@@ -639,6 +639,7 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of Poisson requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: batches of requests on the GPU at once")
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the cyclic 9 request")
+    ap.add_argument("--batch-paths", type=int, default=60_000, help="serving: most paths per batch of small requests")
     ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default all)")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
