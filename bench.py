@@ -3,19 +3,25 @@
 Workload: cyclic 7-roots plus 8 copies with its supports and random complex
 Gaussian coefficients (seed 2), total-degree homotopies, 9 x 5040 = 45,360
 paths per step.  One step = track every path of the 9 systems (one batch
-handle, one launch), classify the endpoints and refine the ill-conditioned
-ones in double double.  The homotopy tables are resident in HBM before the
-timed region; the L2 is flushed (a 256 MiB write) between steps.
+handle: the tracker launch, the tail launch that finishes the paths still
+running when most threads are idle, and classification), then refine the
+ill-conditioned endpoints in double double.  The homotopy tables are
+resident in HBM before the timed region; the L2 is flushed (a 256 MiB
+write) between steps.
 
-Lines printed (rank 0, one JSON object): the device-timed value, an
-end-to-end value through the C ABI with host buffers (table upload and
-endpoint download inside the timed region), the roofline of the dominant
-kernel (track_kernel, FP64 ALU bound), the oracle timed on the host cores,
-SM clocks sampled during the timed region and the kernel launch count.
+Line printed (rank 0, one JSON object): the device-timed value and Newton
+steps/s, an end-to-end value through the C ABI with host buffers (table
+upload and endpoint download inside the timed region), the roofline of the
+tracking call (track + tail kernels, FP64 ALU bound), the served latency of
+Poisson-arriving small requests (continuous batching), the oracle timed on
+the host cores, SM clocks sampled during the timed region and the kernel
+launch count.
 
 ``--impl reference`` times the CPU oracle (the reference of this project)
 on the same workload instead.  ``--gpus N`` under torchrun runs N
 independent replicas (paths are independent; nothing is exchanged).
+``--workload serving`` runs the serving workload alone; ``--workload
+configs`` measures all five workloads, one line each.
 """
 from __future__ import annotations
 
