@@ -44,6 +44,16 @@ def test_default_opts_match_the_oracle_readings():
         assert getattr(g, name) == getattr(o, name), name
 
 
+def test_default_launch_options():
+    """Options with no counterpart in the oracle (they never change a
+    result): the tail hand-off on by default at 0.8 idle with 32 threads per
+    path, double precision, library-chosen grid."""
+    g = P.phc_default_opts()
+    assert g.tail_drain == 0.8 and g.tail_threads == 0
+    assert g.precision == P.PHC_PREC_FP64 and g.block_threads == 0 and g.max_blocks == 0
+    assert g.fp32_t_max == 0.9 and g.fp32_pivot_ratio == 1e4
+
+
 def _bad(sys_kwargs):
     base = dict(n_eq=2, n_var=2, terms_per_eq=np.array([2, 2]),
                 exps=np.array([[1, 0], [0, 0], [0, 1], [0, 0]], dtype=np.uint8),
