@@ -4,6 +4,20 @@ embedding and cascade of a numerical irreducible decomposition).
 The compute path is libphc.so (CUDA for sm_103a, C ABI in include/phc.h);
 this package only marshals arguments (``_lib``) and allocates the output
 tensors for the convenience helpers below.  Nothing here computes on the CPU.
+
+Typical use (a system is any object with n_eq, n_var, terms_per_eq [n_eq],
+exps [T, n_var] uint8 and coefs [T] complex)::
+
+    import paper_1804_03807_gb300 as P
+    h = P.phc_make_homotopy(system, gamma)          # total-degree homotopy
+    r = P.track(h)                                  # every path, on the GPU
+    P.refine(h, r)                                  # double double where ill-conditioned
+    x, cls = r.x.cpu().numpy().T, r.cls.cpu().numpy()   # endpoints, PHC_REGULAR ...
+
+    E = P.phc_embed(system, 1, gammas, hyper)       # top dimension 1 (eq. (2))
+    hE = P.phc_make_homotopy(E, gamma)
+    top = P.track(hE)
+    stage = P.cascade_from(hE, 1, top)              # dimension 0, from the device outputs
 """
 from __future__ import annotations
 
