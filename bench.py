@@ -52,20 +52,36 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # ------------------------------------------------------------------ flop model
 
 def unit_flops(tab_terms, n: int) -> float:
-    """Algorithmic FP64 flops of one evaluate+factor+solve unit of a homotopy
-    whose terms are (support size k, sum of (a_j - 1)) pairs: per term the
-    powers and common factor (sum (a_j-1) complex multiplications), the value
-    and gradient by prefix/suffix products (3k - 2), c(t) x^a and c1 x^a (2),
-    accumulation into H, H_t and k Jacobian entries (k + 2 complex
-    additions), c(t) = c0 + t c1 (4 flops); complex LU 8n^3/3, one solve 8n^2.
-    A complex multiplication is 6 flops, an addition 2."""
+    """FP64 flops of one evaluate+factor+solve unit as the tracker executes it
+    (a fused multiply-add counts 2, a multiplication, addition or division 1;
+    comparisons and absolute values 0), for a homotopy whose terms are
+    (support size k, sum of (a_j - 1)) pairs.  Per term: c(t) = c0 + t c1
+    (2 FMA); a constant adds c(t) to its row of the right-hand side (2);
+    an exponent-one term (sum 0) runs k - 1 prefix and k - 1 suffix complex
+    multiplications (6 each), k - 1 complex fused multiply-adds into H_x (8
+    each), one complex addition (2) and one into the right-hand side (8):
+    20k - 6; a term with powers adds the common factor (sum (a_j - 1)
+    complex multiplications), c(t) times it (6), the exponent scalings
+    (2 per variable) and x^a = cf * suffix (6): 22k + 6 sum + 6.  Complex LU
+    with partial pivoting: per column the |.|_1 sums of the pivot search (1
+    each), the reciprocal of the pivot (6), m multipliers (6 each) and m^2
+    trailing updates (8 each), m = n - 1 - column; one solve: n(n-1)/2
+    complex fused multiply-adds forward and backward (8 each) and n
+    multiplications by the reciprocal pivots (6).  The step logic between
+    units (Runge-Kutta combinations, norms) is not counted."""
     f = 0.0
     for k, extra in tab_terms:
+        f += 4  # c(t)
         if k == 0:
-            f += 4 + 2 * 2
-            continue
-        f += 6 * (extra + 3 * k - 2 + 2) + 2 * (k + 2) + 4
-    f += 8.0 * n ** 3 / 3.0 + 8.0 * n ** 2
+            f += 2
+        elif extra == 0:
+            f += 20 * k - 10
+        else:
+            f += 22 * k + 6 * extra + 2
+    for col in range(n):
+        m = n - 1 - col
+        f += (m + 1) + 6 + 6 * m + 8 * m * m
+    f += 8 * n * (n - 1) + 6 * n
     return f
 
 
@@ -316,9 +332,10 @@ def run_gpu(args):
     if traffic is None and args.precision == 0 and tail_on and (opts.tail_threads or 32) == 32:
         traffic = (203_264 + 256 + 337_408) * units / 3_969_533
     secs = kern_ms / 1e3
-    frac = (f64 / secs / 1e12) / FP64_PEAK_TFLOPS + (f32 / secs / 1e12) / FP32_PEAK_TFLOPS
+    frac = (f64 / secs / 1e12) / FP64_PEAK_TFLOPS
+    frac32 = (f32 / secs / 1e12) / FP32_PEAK_TFLOPS
     roofline = {"bound": "alu", "achieved": f64 / secs / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": frac, "traffic": traffic,
+                "frac": frac, "fp32_frac": frac32, "traffic": traffic,
                 "kernel": (f"track_kernel<7> + tail_kernel<7,{opts.tail_threads or 32}>" if tail_on else "track_kernel<7>") +
                           " (+classify_kernel<7>, <0.1 %)",
                 "tail_paths_per_step": tail_paths, "tail_units_per_step": tail_units,
@@ -326,8 +343,10 @@ def run_gpu(args):
                 "fp64_flops_per_step": f64,
                 "fp32_flops_per_step": f32, "fp32_peak": FP32_PEAK_TFLOPS, "units_per_step": units,
                 "fp32_units_per_step": units32, "kernel_ms": kern_ms,
+                "flops_per_unit": uf,
                 "peak_source": "derived: 152 SMs x 2 FP64 (128 FP32) FMA/clk x 2 flops x 2.07 GHz",
-                "frac_formula": "fp64_flops/peak/T + fp32_flops/fp32_peak/T"}
+                "frac_formula": "frac = fp64_flops/peak/T; fp32_frac = fp32_flops/fp32_peak/T; "
+                                "flops = units x flops_per_unit (FP64 flops the kernel executes per unit)"}
 
     # end to end through the C ABI with host buffers
     e2e = end_to_end(P, systems, gammas, dev, args)
@@ -515,6 +534,10 @@ def run_configs(args):
         ms = _timed(lambda: out.__setitem__("r", P.track(h)), 50)
         d = {"config": 1, "workload": "dense n=4, degree 2, 16 paths", "paths_per_s": 16 / (ms / 1e3), "ms": ms}
         d.update(summary([out["r"]], [unit_flops(homotopy_terms(w.systems[0]), 4)], ms))
+        for drain in (0.0, 0.8):
+            o = P.phc_default_opts(tail_drain=drain)
+            msd = _timed(lambda: P.track(h, opts=o), 50)
+            d[f"tail_drain_{drain}"] = {"ms": msd, "paths_per_s": 16 / (msd / 1e3)}
         d["oracle"] = oracle_part(w.systems * 200, w.gammas * 200, 16, "paths")
         return d
 
@@ -582,6 +605,36 @@ def run_configs(args):
         d["oracle"] = oracle_part(w.systems[:40], w.gammas[:40], 100, "paths of 40 systems")
         return d
 
+    def config9():
+        """The large request of the serving workload alone: cyclic 9 embedded
+        for top dimension 2 (11 unknowns, 362,880 paths), top stage, then its
+        two cascade stages chained on the device."""
+        w = configs.serving(n_requests=1, big=(9, 2))
+        b = w.extra["big"]
+        E = P.phc_embed(b["system"], b["top_dim"], b["gammas"], b["hyper"])
+        h = P.phc_make_homotopy(E, b["gamma"])
+        E1 = P.phc_embed(b["system"], 1, b["gammas"][:, :1], b["hyper"][:1])
+        h1 = P.phc_make_homotopy(E1, b["gamma"])
+        ms = _timed(lambda: out.__setitem__("r", P.track(h)), 1, 1)
+        top = out["r"]
+        d = {"config": "5-big", "workload": "cyclic 9 embedded D=2: 362,880 paths, top stage alone",
+             "paths_per_s": 362880 / (ms / 1e3), "ms": ms}
+        d.update(summary([top], [unit_flops(homotopy_terms(E), 11)], ms))
+        d["classes_top"] = np.bincount(top.cls.cpu().numpy(), minlength=4).tolist()
+
+        def stages():
+            s2 = P.cascade_from(h, 2, top)
+            s1 = P.cascade_from(h1, 1, s2)
+            out["s"] = (s2, s1)
+        ms2 = _timed(stages, 1, 1)
+        s2, s1 = out["s"]
+        n2 = int((s2.cls.cpu().numpy() >= 0).sum())
+        n1 = int((s1.cls.cpu().numpy() >= 0).sum())
+        d["cascade"] = {"ms": ms2, "paths": [n2, n1], "paths_per_s": (n2 + n1) / (ms2 / 1e3)}
+        d["cascade"].update(summary([s2, s1], [unit_flops(homotopy_terms(E), 11),
+                                              unit_flops(homotopy_terms(E1), 10)], ms2))
+        return d
+
     def config5():
         sv, reqs = serving_session(args.requests, not args.no_big, args.slots, args.batch_paths)
         d = {"config": 5, "workload": f"{args.requests} Poisson (200/s) sparse requests"
@@ -594,8 +647,9 @@ def run_configs(args):
         return d
 
     want = [int(c) for c in args.configs.split(",")] if args.configs else [1, 2, 3, 4, 5]
+    table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9}
     for c in want:
-        print(json.dumps([config1, config2, config3, config4, config5][c - 1]()), flush=True)
+        print(json.dumps(table[c]()), flush=True)
     return 0
 
 
@@ -646,7 +700,8 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=4, help="serving: batches of requests on the GPU at once")
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the cyclic 9 request")
     ap.add_argument("--batch-paths", type=int, default=60_000, help="serving: most paths per batch of small requests")
-    ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default all)")
+    ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default 1-5; 9 = the "
+                    "cyclic 9 D=2 request of the serving workload alone)")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--profile-case", nargs="?", const="cyclic7", default=None, choices=["cyclic7", "sparse"],

@@ -49,7 +49,9 @@ enum {
     PHC_EINVAL = -1,        /* invalid argument or system                 */
     PHC_ENOMEM = -2,        /* host or device allocation failed           */
     PHC_ECUDA = -3,         /* a CUDA call failed (message names it)      */
-    PHC_ETIMEOUT = -4,      /* a bounded device wait ran out              */
+    PHC_ETIMEOUT = -4,      /* a bounded device wait ran out (reserved: no
+                               kernel of this library waits on another, so
+                               no call returns it)                        */
     PHC_EUNSUPPORTED = -5   /* size or option outside what is built       */
 };
 
@@ -213,9 +215,11 @@ int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const 
  * n_eq + k is hyper[k][0] + sum_j hyper[k][j+1] x_j + z_k.  A square f only
  * (the squaring of Section 2.1 is left to the caller).  gammas [n_eq][D] and
  * hyper [D][n_var + 1] are host arrays; when NULL they are drawn from
- * `seed` (standard complex Gaussian from a 64-bit PCG: state advance
- * s = s * 6364136223846793005 + 1442695040888963407, output the top 53 bits
- * of s ^ (s >> 29) as a uniform in [0,1), Box-Muller for the normal).  Host
+ * `seed` (standard complex Gaussian from a 64-bit linear congruential
+ * generator with an xor-shift output: state s = seed ^ 0x9E3779B97F4A7C15,
+ * advance s = s * 6364136223846793005 + 1442695040888963407, output the top
+ * 53 bits of s ^ (s >> 29) as a uniform u in [0,1); two uniforms u1, u2 give
+ * sqrt(-log u1) (cos 2 pi u2 + i sin 2 pi u2), so E|z|^2 = 1).  Host
  * call; *out is library-allocated (phc_free_lists).
  * Errors: PHC_EINVAL for a non-square f, top_dim < 0, or n_var + top_dim
  * above PHC_MAX_VARS; PHC_ENOMEM. */
@@ -311,22 +315,30 @@ int phc_refine_endpoints(const phc_homotopy *h, phc_cd *x_hi_io, phc_cd *x_lo_ou
 
 /* Largest n_paths phc_track_paths_noalloc accepts with stats_out == NULL. */
 #define PHC_NOALLOC_MAX_PATHS 52428
+/* Most paths phc_track_paths_noalloc moves to the tail kernel in one call. */
+#define PHC_NOALLOC_MAX_HANDOFF 4096
 
 /* phc_track_paths without any device allocation during the call (the paper
  * has no counterpart; this is a service to callers that cannot allocate).
- * Same arguments, outputs and errors as phc_track_paths.  Callers whose
- * device memory belongs to another allocator (a framework's caching
- * allocator that reserved the free memory up front) or that must not enter
- * the allocator after start-up (latency-critical serving loops) use it.
- * Its scratch -- the path-queue counter and, when stats_out is NULL, the
- * per-path records -- is one static device array of 256 + 80 *
- * PHC_NOALLOC_MAX_PATHS bytes (about 4 MiB) that every GPU loading the
- * library holds until exit.  The first call on a device (with that device
- * current) looks up the array's address; make it before any stream capture.
- * All calls share the array and it keeps the last call's contents (the
- * counter is cleared at each call): calls that overlap on the GPU race, so
- * serialise them.  With stats_out == NULL, n_paths above
- * PHC_NOALLOC_MAX_PATHS is rejected with PHC_EUNSUPPORTED. */
+ * Same arguments, outputs and errors as phc_track_paths, and the same
+ * results.  Callers whose device memory belongs to another allocator (a
+ * framework's caching allocator that reserved the free memory up front) or
+ * that must not enter the allocator after start-up (latency-critical serving
+ * loops) use it.  Its scratch -- the path-queue and hand-off counters, the
+ * hand-off records of the tail kernel and, when stats_out is NULL, the
+ * per-path records -- is one static device array of about 5.5 MiB
+ * (256 B + 320 B * PHC_NOALLOC_MAX_HANDOFF + 80 B * PHC_NOALLOC_MAX_PATHS)
+ * that every GPU loading the library holds until exit.  The first call on a
+ * device (with that device current) looks up the array's address; make it
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (the counters are cleared at each call): calls that
+ * overlap on the GPU race, so serialise them.  With stats_out == NULL,
+ * n_paths above PHC_NOALLOC_MAX_PATHS is rejected with PHC_EUNSUPPORTED.
+ * The tail hand-off (opts.tail_drain) holds at most PHC_NOALLOC_MAX_HANDOFF
+ * paths, so on launches of more threads it starts once no more than that
+ * many threads still hold a path (a later start than tail_drain alone, the
+ * same results).  The call resets the handle's hand-off counters:
+ * phc_tail_paths reports 0 after it. */
 int phc_track_paths_noalloc(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts,
                             phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
 

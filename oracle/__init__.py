@@ -60,7 +60,7 @@ class _Hom(ctypes.Structure):
         ("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("n_terms", ctypes.c_int32),
         ("terms_per_eq", ctypes.c_void_p), ("exps", ctypes.c_void_p), ("coefs", ctypes.c_void_p),
         ("gamma_re", ctypes.c_double), ("gamma_im", ctypes.c_double),
-        ("row", ctypes.c_int32), ("slack", ctypes.c_int32),
+        ("row", ctypes.c_int32), ("slack", ctypes.c_int32), ("coefs0", ctypes.c_void_p),
     ]
 
 
@@ -107,15 +107,22 @@ def host_threads() -> int:
 class Homotopy:
     """Keeps the numpy buffers alive behind the C struct."""
 
-    def __init__(self, sys: PolySystem, kind: int, gamma: complex = 1.0, row: int = -1, slack: int = -1):
+    def __init__(self, sys: PolySystem, kind: int, gamma: complex = 1.0, row: int = -1, slack: int = -1,
+                 coefs0=None):
         assert sys.n_eq == sys.n_var, "the tracker needs a square system"
         self.sys = sys
         self.n = sys.n_var
         self._tpe = np.ascontiguousarray(sys.terms_per_eq, dtype=np.int32)
         self._exps = np.ascontiguousarray(sys.exps, dtype=np.uint8)
         self._coefs = np.ascontiguousarray(np.stack([sys.coefs.real, sys.coefs.imag], axis=1), dtype=np.float64)
+        self._coefs0 = None
+        if coefs0 is not None:
+            c0 = np.asarray(coefs0, dtype=np.complex128).reshape(-1)
+            assert c0.shape[0] == sys.n_terms, "start coefficients must match the target's terms"
+            self._coefs0 = np.ascontiguousarray(np.stack([c0.real, c0.imag], axis=1), dtype=np.float64)
         self.c = _Hom(kind, self.n, sys.n_terms, self._tpe.ctypes.data, self._exps.ctypes.data,
-                      self._coefs.ctypes.data, float(np.real(gamma)), float(np.imag(gamma)), row, slack)
+                      self._coefs.ctypes.data, float(np.real(gamma)), float(np.imag(gamma)), row, slack,
+                      None if self._coefs0 is None else self._coefs0.ctypes.data)
 
     def ref(self):
         return ctypes.byref(self.c)
@@ -124,6 +131,24 @@ class Homotopy:
 def total_degree(sys: PolySystem, gamma: complex) -> Homotopy:
     """H(x,t) = (1-t) gamma g(x) + t f(x), g_i = x_i^{d_i} - 1."""
     return Homotopy(sys, 0, gamma)
+
+
+def parameter_homotopy(target: PolySystem, start_coefs, gamma: complex) -> Homotopy:
+    """H(x,t) = (1-t) gamma g(x) + t f(x), f = target, g = the target's
+    supports with the coefficients start_coefs (Section 2.3: the solutions
+    of a random coefficient system start the paths to the target).  Paths
+    start from explicit solutions of g (track(..., starts=...))."""
+    return Homotopy(target, 2, gamma, coefs0=start_coefs)
+
+
+def end_measures(h: Homotopy, x: np.ndarray):
+    """(cond, relres) of the endpoint x as a root of H(., 1)."""
+    xb = np.ascontiguousarray(x, dtype=np.complex128)
+    c = ctypes.c_double()
+    r = ctypes.c_double()
+    lib().orc_end_measures(h.ref(), xb.view(np.float64).ctypes.data_as(ctypes.c_void_p), ctypes.byref(c),
+                           ctypes.byref(r))
+    return c.value, r.value
 
 
 def cascade_homotopy(emb: PolySystem, n_eq_orig: int, n_var_orig: int, k: int) -> Homotopy:

@@ -103,7 +103,10 @@ enum { ORC_REGULAR = 0, ORC_SINGULAR = 1, ORC_AT_INFINITY = 2, ORC_FAILED = 3 };
 /* A homotopy on n unknowns.  kind 0: total-degree homotopy with target f,
  * start g_i = x_i^{deg_i} - 1 and constant gamma.  kind 1: cascade stage on
  * the embedded system f = E_k; equation `row` is hyperplane k and variable
- * `slack` is z_k. */
+ * `slack` is z_k.  kind 2: coefficient-parameter homotopy
+ * (1-t) gamma g(x) + t f(x) where g has the supports of f and the
+ * coefficients coefs0 (Section 2.3: the solutions of a random coefficient
+ * system start the paths to the target system). */
 typedef struct {
     int32_t kind;
     int32_t n;
@@ -111,8 +114,9 @@ typedef struct {
     const int32_t *terms_per_eq; /* [n]                  */
     const uint8_t *exps;         /* [n_terms][n]         */
     const double *coefs;         /* [n_terms][2] re, im  */
-    double gamma_re, gamma_im;   /* kind 0               */
+    double gamma_re, gamma_im;   /* kinds 0 and 2        */
     int32_t row, slack;          /* kind 1               */
+    const double *coefs0;        /* kind 2: [n_terms][2] coefficients of g */
 } orc_homotopy;
 
 typedef struct {
@@ -216,6 +220,10 @@ static void eval_homotopy(const orc_homotopy *h, const cplx *x, double t, cplx *
             if (h->kind == 0) {
                 ct = t * c;
                 dct = c;
+            } else if (h->kind == 2) {
+                const cplx c0 = h->coefs0[2 * (off + k)] + I * h->coefs0[2 * (off + k) + 1];
+                ct = (1.0 - t) * gamma * c0 + t * c;
+                dct = c - gamma * c0;
             } else if (i == h->row && !is_unit(a, n, h->slack)) {
                 ct = (1.0 - t) * c;
                 dct = -c;
@@ -387,6 +395,16 @@ static void end_measures(const orc_homotopy *h, const cplx *x, double *cond, dou
         if (!(rowacc[j] <= m)) m = rowacc[j];
     *cond = m / (1.0 + vnorm(n, x));
     if (!isfinite(*cond)) *cond = INFINITY;
+}
+
+/* Exported for tests: cond and relres of end_measures at the point x. */
+int orc_end_measures(const orc_homotopy *h, const double *x_ri, double *cond, double *relres)
+{
+    cplx x[NMAX];
+    if (h->n < 1 || h->n > NMAX) return -2;
+    for (int j = 0; j < h->n; j++) x[j] = x_ri[2 * j] + I * x_ri[2 * j + 1];
+    end_measures(h, x, cond, relres);
+    return 0;
 }
 
 /* Track one path from (x, t=0) to t = 1 and classify its endpoint.
@@ -734,7 +752,7 @@ static void eval_end_dd(const orc_homotopy *h, const cdd *x, cdd *H, cdd *Hx)
         for (int k = 0; k < h->terms_per_eq[i]; k++) {
             const uint8_t *a = h->exps + (size_t)(off + k) * n;
             cplx c = coef_of(h, off + k);
-            /* coefficient at t = 1: kind 0 keeps c; kind 1 zeroes the scaled hyperplane terms */
+            /* coefficient at t = 1: kinds 0 and 2 keep c; kind 1 zeroes the scaled hyperplane terms */
             if (h->kind == 1 && i == h->row && !is_unit(a, n, h->slack)) continue;
             cdd cc = cdd_from(c);
             cdd m = cdd_from(1.0);

@@ -22,6 +22,7 @@ PHC_STOP_SKIPPED = 5
 PHC_PREC_FP64, PHC_PREC_FP32_INTERIOR = 0, 1
 PHC_MAX_VARS = 12
 PHC_NOALLOC_MAX_PATHS = 52428
+PHC_NOALLOC_MAX_HANDOFF = 4096
 
 EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",

@@ -986,15 +986,22 @@ int handle_num_paths(const phc_homotopy *h, int64_t *out)
     return PHC_OK;
 }
 
-// Device view of the handle's total-degree homotopy and start tables.
-int handle_track_view(phc_homotopy *h, TrackLaunch *L)
+// Device view of the handle's total-degree homotopy and start tables, set
+// up for the options' arithmetic as run_track sets it up (the single
+// precision copies staged only for FP32_INTERIOR).
+int handle_track_view(phc_homotopy *h, const phc_opts &o, TrackLaunch *L)
 {
     L->tab = h->total.view;
+    L->tab.f32 = o.precision == PHC_PREC_FP32_INTERIOR;
     L->deg = h->d_deg;
     L->root_off = h->d_root_off;
     L->roots = h->d_roots;
     L->paths_per_system = h->paths_per_system;
     return PHC_OK;
 }
+
+// The handle's hand-off counters (NULL until a call used the hand-off):
+// phc_tail_paths reads them.
+unsigned long long *handle_tail_counters(phc_homotopy *h) { return h->d_tailc; }
 
 }  // namespace phc

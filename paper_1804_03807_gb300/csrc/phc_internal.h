@@ -148,6 +148,9 @@ struct TrackLaunch {
     unsigned long long *multi_claimed;  // multi-system: paths claimed over all systems
     unsigned long long drain_at;  // set by the launcher from drain_frac
     double drain_frac;            // fraction of idle lanes that starts the hand-off; 0: never
+    int64_t handoff_cap;          // records the hand-off buffer holds; 0: one per lane.  With a
+                                  // cap the hand-off starts no earlier than when at most this many
+                                  // lanes still hold a path (each writes one record at most)
 };
 
 // Bytes of shared memory one warp needs for a table of T terms and V

@@ -1103,7 +1103,11 @@ static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_block
     if (grid < 1) grid = 1;
     L.drain_at = 0;
     if (L.drain_frac > 0.0 && L.handoff) {
-        const unsigned long long at = (unsigned long long)(L.drain_frac * (double)(grid * bt));
+        const int64_t lanes = grid * bt;
+        unsigned long long at = (unsigned long long)(L.drain_frac * (double)lanes);
+        // a lane that finds the queue empty stays idle, so when idle_n >= at at most
+        // lanes - at lanes hold a path, and each writes at most one record
+        if (L.handoff_cap > 0 && lanes - L.handoff_cap > (int64_t)at) at = (unsigned long long)(lanes - L.handoff_cap);
         L.drain_at = at < 1 ? 1 : at;
     }
     track_kernel<N, MODE><<<(unsigned)grid, bt, smem, s>>>(L, tb, tb2);

@@ -106,3 +106,41 @@ def exact_residual(sys, x_hi: np.ndarray, x_lo: np.ndarray) -> float:
         worst = max(worst, val / (1.0 + scale))
         off += m
     return worst
+
+
+def jacobian(sys, x: np.ndarray) -> np.ndarray:
+    """J_ij = d f_i / d x_j at one point x [n], from
+    d/dx_j c x^a = c a_j x_j^(a_j - 1) prod_{l != j} x_l^a_l."""
+    x = np.asarray(x, dtype=np.complex128)
+    n = sys.n_var
+    J = np.zeros((sys.n_eq, n), np.complex128)
+    off = 0
+    for i in range(sys.n_eq):
+        m = int(sys.terms_per_eq[i])
+        for k in range(m):
+            a = sys.exps[off + k].astype(np.int64)
+            c = complex(sys.coefs[off + k])
+            for j in range(n):
+                if a[j] == 0:
+                    continue
+                d = a.copy()
+                d[j] -= 1
+                J[i, j] += c * a[j] * np.prod(x ** d)
+        off += m
+    return J
+
+
+def term_scales(sys, x: np.ndarray) -> np.ndarray:
+    """scale_i = sum over the terms of equation i of |c|_1 |x^a|_1, with
+    |z|_1 = |Re z| + |Im z|."""
+    x = np.asarray(x, dtype=np.complex128)
+    out = np.zeros(sys.n_eq)
+    off = 0
+    for i in range(sys.n_eq):
+        m = int(sys.terms_per_eq[i])
+        for k in range(m):
+            c = complex(sys.coefs[off + k])
+            v = np.prod(x ** sys.exps[off + k].astype(np.int64))
+            out[i] += (abs(c.real) + abs(c.imag)) * (abs(v.real) + abs(v.imag))
+        off += m
+    return out
