@@ -213,7 +213,7 @@ int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const 
 /* The embedded system E_D of Section 2.1 (eq. (2) for D = 1): unknowns
  * x_1..x_n, z_1..z_D; equation i is f_i(x) + sum_k gammas[i][k] z_k; equation
  * n_eq + k is hyper[k][0] + sum_j hyper[k][j+1] x_j + z_k.  A square f only
- * (the squaring of Section 2.1 is left to the caller).  gammas [n_eq][D] and
+ * (square a non-square system first with phc_square).  gammas [n_eq][D] and
  * hyper [D][n_var + 1] are host arrays; when NULL they are drawn from
  * `seed` (standard complex Gaussian from a 64-bit linear congruential
  * generator with an xor-shift output: state s = seed ^ 0x9E3779B97F4A7C15,
@@ -225,6 +225,20 @@ int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const 
  * above PHC_MAX_VARS; PHC_ENOMEM. */
 int phc_embed(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps, const phc_cd *coefs,
               int top_dim, const phc_cd *gammas, const phc_cd *hyper, uint64_t seed, phc_system_lists **out);
+
+/* A square system from a non-square one (Section 2.1): an underdetermined f
+ * (n_eq < n_var) gains n_var - n_eq random hyperplanes
+ * consts[k][0] + sum_j consts[k][j+1] x_j = 0 (consts [n_var - n_eq][n_var + 1]);
+ * an overdetermined f (n_eq > n_var) gains n_eq - n_var new unknowns s_k
+ * (after x), and equation i gains sum_k consts[i][k] s_k
+ * (consts [n_eq][n_eq - n_var]).  A square f is returned unchanged.  consts
+ * is a host array or NULL (then drawn from seed as in phc_embed).  The
+ * result is square with max(n_eq, n_var) unknowns (at most PHC_MAX_VARS);
+ * embed it with phc_embed.  Host call; *out is library-allocated
+ * (phc_free_lists).  Errors: PHC_EINVAL for invalid lists or a square
+ * system above PHC_MAX_VARS unknowns; PHC_ENOMEM. */
+int phc_square(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps, const phc_cd *coefs,
+               const phc_cd *consts, uint64_t seed, phc_system_lists **out);
 
 /* One stage of the cascade of homotopies (Section 3.1, Figure 3): embedded_k
  * is a handle made from E_k (k >= 1 slacks, as phc_embed lays it out: z_k is
@@ -274,6 +288,59 @@ int phc_cascade_from(const phc_homotopy *embedded_k, int k, const phc_cd *x_prev
  * PHC_ENOMEM, PHC_ECUDA. */
 int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
                    int8_t *const *cls_out, phc_path_stats *const *stats_out, void *cuda_stream);
+
+/* Coefficient-parameter homotopy H(x,t) = (1-t) gamma g(x) + t f(x)
+ * (Section 2.3: the solutions of a random coefficient system are the start
+ * solutions of the homotopy to the target system): g and f share the
+ * supports terms_per_eq, exps (as in phc_make_homotopy); g has the
+ * coefficients coefs_start [T], and there are n_systems targets
+ * coefs_target [n_systems][T] (host arrays), e.g. one target per test
+ * point of a membership test (phc_membership_test).  The handle has no
+ * total-degree start system: phc_num_paths reports 0 and paths start from
+ * caller-given solutions of g (phc_track_from).  Endpoints are classified
+ * and refined (phc_refine_endpoints) with the exact target coefficients.
+ * Errors: as phc_make_homotopy (the target lists are validated). */
+int phc_make_parameter_homotopy(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps,
+                                int n_systems, const phc_cd *coefs_start, const phc_cd *coefs_target,
+                                phc_cd gamma, phc_homotopy **out);
+
+/* Track n_starts paths of h from explicit points at t = 0 to t = 1 and
+ * classify the endpoints.  starts: device SoA [n_var][n_starts], solutions
+ * of the homotopy at t = 0 (of g for a parameter homotopy, of gamma
+ * (x_i^{d_i} - 1) for a total-degree handle).  Entry q belongs to system
+ * q / starts_per_system of a batch or parameter handle (starts_per_system
+ * 0: every entry to system 0).  Outputs as phc_track_paths, indexed by
+ * entry: x_out SoA [n_var][n_starts], cls_out [n_starts], stats_out or NULL.
+ * Errors: PHC_EINVAL for NULL arrays, negative sizes or entries beyond the
+ * handle's systems; PHC_ECUDA. */
+int phc_track_from(phc_homotopy *h, const phc_cd *starts, int64_t n_starts, int64_t starts_per_system,
+                   const phc_opts *opts, phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out,
+                   void *cuda_stream);
+
+/* Homotopy membership test (Section 4.1, Example 4.1): does a point lie on
+ * a k-dimensional solution set given by witness points?  The embedded
+ * system E_k (host lists as phc_embed lays them out: unknowns x_1..x_n,
+ * z_1..z_k; the last k equations are the hyperplanes, each with one
+ * constant term, linear terms and its slack) has the m witness points
+ * (device SoA [n_var][m]: solutions with every slack zero, the generic
+ * points of the set).  For each test point z_t (host [p][n_var - k], the
+ * x-coordinates), the constant c_j0 of hyperplane j moves to
+ * c_j3 = -sum_i c_ji z_t,i, so that (z_t, 0) satisfies every hyperplane:
+ * the homotopy (1-t) E_k(c_0) + t E_k(c_3) carries the witness points to
+ * the generic points of the set on the moved hyperplanes; z_t lies on the
+ * set when one of the m endpoints (regular or singular) equals (z_t, 0)
+ * within tol (1 + ||z_t||) in every unknown.  p x m paths in one launch.
+ * Outputs (device): on_out [p] (1 on the set, 0 not), and, unless NULL,
+ * the endpoints x_out SoA [n_var][p * m] and their classes cls_out
+ * [p * m] (test point t owns entries t*m .. t*m + m - 1).  The call
+ * allocates its temporaries and returns after the work on cuda_stream has
+ * finished.
+ * Errors: PHC_EINVAL for k outside 1..n_var-1, m < 1, hyperplane rows of
+ * another form, non-finite points, tol <= 0; PHC_ENOMEM; PHC_ECUDA. */
+int phc_membership_test(int n_eq, int n_var, const int32_t *terms_per_eq, const uint8_t *exps,
+                        const phc_cd *coefs, int k, const phc_cd *witness, int64_t m, const phc_cd *points,
+                        int64_t p, double tol, const phc_opts *opts, uint8_t *on_out, phc_cd *x_out,
+                        int8_t *cls_out, void *cuda_stream);
 
 /* The top stage and the cascade stage below it in one launch (Section 3.1,
  * Figure 3; the GPU counterpart of the paper's pipelining, Section 2.2).

@@ -293,6 +293,44 @@ def embed(sys: PolySystem, top_dim: int, gammas: np.ndarray, hyper: np.ndarray) 
                       name=f"{sys.name}-E{D}")
 
 
+def square(sys: PolySystem, consts: np.ndarray) -> PolySystem:
+    """A square system from a non-square one (Section 2.1).  Underdetermined
+    (n_eq < n_var): add the n_var - n_eq hyperplanes
+    consts[k, 0] + sum_j consts[k, j+1] x_j.  Overdetermined (n_eq > n_var):
+    add n_eq - n_var unknowns s_k after x and the term consts[i, k] s_k to
+    every equation i.  Square: unchanged."""
+    n_eq, n = sys.n_eq, sys.n_var
+    N = max(n_eq, n)
+    exps, coefs, tpe = [], [], []
+    off = 0
+    for i in range(n_eq):
+        m = int(sys.terms_per_eq[i])
+        for q in range(m):
+            exps.append(list(sys.exps[off + q]) + [0] * (N - n))
+            coefs.append(sys.coefs[off + q])
+        if n_eq > n:
+            for k in range(N - n):
+                e = [0] * N
+                e[n + k] = 1
+                exps.append(e)
+                coefs.append(consts[i, k])
+            m += N - n
+        tpe.append(m)
+        off += int(sys.terms_per_eq[i])
+    if n_eq < n:
+        for k in range(N - n_eq):
+            exps.append([0] * N)
+            coefs.append(consts[k, 0])
+            for j in range(n):
+                e = [0] * N
+                e[j] = 1
+                exps.append(e)
+                coefs.append(consts[k, j + 1])
+            tpe.append(n + 1)
+    return PolySystem(N, N, np.array(tpe), np.array(exps, dtype=np.uint8).reshape(-1, N), np.array(coefs),
+                      name=f"{sys.name}-sq")
+
+
 def drop_last_slack(emb: PolySystem, n_eq_orig: int, n_var_orig: int, k: int) -> PolySystem:
     """E_k with z_k = 0 and hyperplane k removed, i.e. E_{k-1}."""
     N = emb.n_var
@@ -334,3 +372,93 @@ def cascade_stage(emb: PolySystem, n_eq_orig: int, n_var_orig: int, k: int, star
     s = n_var_orig + k - 1
     x_next = np.delete(x, s, axis=1)
     return drop_last_slack(emb, n_eq_orig, n_var_orig, k), x_next, cls, st
+
+
+# ------------------------------------------------------------------ membership test and filtering (Section 4)
+
+def membership_target(emb: PolySystem, n_var_orig: int, k: int, z: np.ndarray) -> PolySystem:
+    """E_k with the constant c_j0 of every hyperplane j (the last k equations)
+    replaced by c_j3 = -sum_i c_ji z_i, so that (z, 0) satisfies every
+    hyperplane (Section 4.1, Example 4.1: c_3 = -2 c_1 for the point (2, 0))."""
+    coefs = np.array(emb.coefs, dtype=np.complex128).copy()
+    bounds = np.concatenate([[0], np.cumsum(emb.terms_per_eq)])
+    z = np.asarray(z, dtype=np.complex128)
+    for j in range(k):
+        row = emb.n_eq - k + j
+        const, acc = None, 0.0 + 0.0j
+        for q in range(int(bounds[row]), int(bounds[row + 1])):
+            e = np.asarray(emb.exps[q], dtype=np.int64)
+            if e.sum() == 0:
+                const = q
+            elif e[:n_var_orig].sum() == 1 and e.sum() == 1:
+                acc += coefs[q] * z[int(np.argmax(e[:n_var_orig]))]
+        assert const is not None, "a hyperplane without constant term"
+        coefs[const] = -acc
+    return PolySystem(emb.n_eq, emb.n_var, np.array(emb.terms_per_eq), np.array(emb.exps), coefs,
+                      name=f"{emb.name}-moved")
+
+
+def membership(emb: PolySystem, n_var_orig: int, k: int, witness: np.ndarray, points: np.ndarray,
+               tol: float = 1e-3, threads: int | None = None):
+    """Homotopy membership test (Section 4.1, Example 4.1).  witness [m, N]:
+    the generic points of a k-dimensional set, solutions of E_k = emb with
+    zero slacks.  For every test point z (rows of points, the first
+    n_var_orig unknowns) the hyperplane constants move from c_0 to c_3
+    along (1-t) E_k(c_0) + t E_k(c_3); z lies on the set when one endpoint
+    (regular or singular) equals (z, 0) within tol (1 + ||z||) in every
+    unknown.  The tolerance is loose because the points tested are singular
+    endpoints of the cascade (on a higher-dimensional set the Jacobian loses
+    rank and the end Newton steps converge slowly: in Example 3.1 they are
+    accurate to about 1e-4, while the other endpoints are at distance >= 1).
+    Returns (on [p] bool, per point the endpoints and classes)."""
+    witness = np.atleast_2d(np.asarray(witness, dtype=np.complex128))
+    on, ends = [], []
+    for z in np.atleast_2d(np.asarray(points, dtype=np.complex128)):
+        target = membership_target(emb, n_var_orig, k, z)
+        h = parameter_homotopy(target, emb.coefs, 1.0)
+        x, c, st = track(h, starts=witness, threads=threads)
+        zz = np.concatenate([z, np.zeros(emb.n_var - n_var_orig)])
+        nz = np.max(np.maximum(np.abs(z.real), np.abs(z.imag)))
+        d = np.max(np.maximum(np.abs((x - zz).real), np.abs((x - zz).imag)), axis=1)
+        on.append(bool(np.any(((c == REGULAR) | (c == SINGULAR)) & (d <= tol * (1.0 + nz)))))
+        ends.append((x, c))
+    return np.array(on, dtype=bool), ends
+
+
+def filter_candidates(levels: dict, n_var_orig: int, tol: float = 1e-3, threads: int | None = None):
+    """The filters of Section 4.2 (Figures 4 and 5).  levels[k] = (E_k,
+    x [P, n + k], cls [P]) are the endpoints of the cascade at dimension k
+    (top level D first, then D-1, ..., 0; E_0 is the original system), each
+    point's last unknown being z_k for k >= 1.  At every level the finite
+    candidates with z_k = 0 (all endpoints at level 0) that are regular are
+    kept; the singular ones are tested against the witness sets of the
+    higher dimensions, from the top down, and dropped when on one.  The
+    witness set of dimension k is what is kept at level k.
+
+    Returns (witness sets {k: points [m, n + k]}, isolated points at level 0
+    (the kept and the remaining singular candidates), and the filter stages
+    as (level, dimension tested against, paths tracked, points removed))."""
+    D = max(levels)
+    witness, stages = {}, []
+    isolated = None
+    for k in range(D, -1, -1):
+        E, x, cls = levels[k]
+        finite = (cls == REGULAR) | (cls == SINGULAR)
+        cand = finite & (slack_zero(x, n_var_orig + k - 1) if k >= 1 else np.ones(len(cls), bool))
+        keep = x[cand & (cls == REGULAR)]
+        sus = x[cand & (cls == SINGULAR)]
+        for kk in range(D, k, -1):
+            if len(sus) == 0:
+                break
+            Ekk, W = witness[kk]
+            if len(W) == 0:
+                continue
+            on, _ = membership(Ekk, n_var_orig, kk, W, sus[:, :n_var_orig], tol, threads)
+            stages.append((k, kk, len(sus) * len(W), int(on.sum())))
+            sus = sus[~on]
+        kept = np.concatenate([keep, sus]) if len(sus) else keep
+        if k >= 1:
+            witness[k] = (E, kept)
+        else:
+            isolated = kept
+    return {k: w for k, (E, w) in witness.items()}, isolated, stages

@@ -30,7 +30,8 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    load, phc_cascade_stage, phc_default_opts, phc_embed, phc_last_error, phc_make_homotopy,
                    phc_make_homotopy_batch,
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
-                   phc_tail_paths, phc_track_many, phc_track_paths_noalloc, phc_track_pipeline)
+                   phc_tail_paths, phc_track_many, phc_track_paths_noalloc, phc_track_pipeline,
+                   phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -40,7 +41,8 @@ __all__ = [
     "phc_opts", "phc_refine_endpoints", "phc_track_many", "phc_track_paths", "phc_track_paths_noalloc",
     "phc_track_pipeline", "track_many", "phc_cascade_from", "PHC_STOP_SKIPPED", "cascade_from",
     "Tracked", "pipeline", "track", "cascade", "refine",
-    "stats_numpy", "phc_tail_paths",
+    "stats_numpy", "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
+    "track_from", "membership", "phc_square",
 ]
 
 
@@ -76,6 +78,30 @@ def track(h: Homotopy, first: int = 0, n_paths: int | None = None, opts=None, st
     x, cls, st = _alloc(h.n, n_paths, device)
     phc_track_paths(h, first, n_paths, opts, x, cls, st, stream)
     return Tracked(x, cls, st)
+
+
+def track_from(h: Homotopy, starts, starts_per_system: int = 0, opts=None, stream=None) -> Tracked:
+    """Track paths of h from the columns of starts [n_var, n] (device)."""
+    n = int(starts.shape[1])
+    x, cls, st = _alloc(h.n, n, starts.device)
+    phc_track_from(h, starts.contiguous(), n, starts_per_system, opts, x, cls, st, stream)
+    return Tracked(x, cls, st)
+
+
+def membership(emb, k: int, witness, points, tol: float = 1e-3, opts=None, stream=None):
+    """Homotopy membership test (Section 4.1): for every row of points
+    [p, n_var - k] whether it lies on the set whose witness points (device
+    [n_var, m], solutions of E_k = emb with zero slacks) are given.  Returns
+    (on [p] bool numpy array, Tracked endpoints [n_var, p * m])."""
+    import torch
+    pts = np.atleast_2d(np.asarray(points, dtype=np.complex128))
+    p, m = pts.shape[0], int(witness.shape[1])
+    dev = witness.device
+    on = torch.empty(p, dtype=torch.uint8, device=dev)
+    x = torch.empty((int(emb.n_var), p * m), dtype=torch.complex128, device=dev)
+    cls = torch.empty(p * m, dtype=torch.int8, device=dev)
+    phc_membership_test(emb, k, witness.contiguous(), pts, tol, opts, on, x, cls, stream)
+    return on.cpu().numpy().astype(bool), Tracked(x, cls, None)
 
 
 def cascade(h_k: Homotopy, k: int, starts, opts=None, stream=None) -> Tracked:

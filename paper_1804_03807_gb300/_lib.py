@@ -28,7 +28,8 @@ EXPORTED = [
     "phc_default_opts", "phc_make_homotopy", "phc_num_paths", "phc_track_paths", "phc_embed", "phc_cascade_stage",
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
     "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch", "phc_track_pipeline",
-    "phc_track_many", "phc_cascade_from", "phc_tail_paths",
+    "phc_track_many", "phc_cascade_from", "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from",
+    "phc_membership_test", "phc_square",
 ]
 
 
@@ -93,12 +94,18 @@ def load() -> ctypes.CDLL:
     L.phc_track_paths_noalloc.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
+    L.phc_square.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.c_uint64,
+                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_cascade_stage.argtypes = [vp, i32, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
     L.phc_cascade_from.argtypes = [vp, i32, vp, vp, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
     L.phc_track_many.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_track_pipeline.argtypes = [vp, i32, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp, vp, vp, vp]
     L.phc_refine_endpoints.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]
     L.phc_tail_paths.argtypes = [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.phc_make_parameter_homotopy.argtypes = [i32, i32, vp, vp, i32, vp, vp, phc_cd, ctypes.POINTER(vp)]
+    L.phc_track_from.argtypes = [vp, vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
+    L.phc_membership_test.argtypes = [i32, i32, vp, vp, vp, i32, vp, i64, vp, i64, ctypes.c_double,
+                                      ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_last_error.restype = ctypes.c_char_p
     L.phc_destroy_homotopy.argtypes = [vp]
     L.phc_destroy_homotopy.restype = None
@@ -109,7 +116,8 @@ def load() -> ctypes.CDLL:
                  "phc_track_paths_noalloc", "phc_track_pipeline", "phc_track_many", "phc_cascade_from",
                  "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats",
-                 "phc_tail_paths"):
+                 "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
+                 "phc_square"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
         raise ImportError("phc_opts layout mismatch between phc.h and the binding")
@@ -190,6 +198,49 @@ def phc_make_homotopy_batch(systems, gammas) -> Homotopy:
     return Homotopy(out.value, int(systems[0].n_var))
 
 
+def phc_make_parameter_homotopy(target, start_coefs, gamma: complex = 1.0) -> Homotopy:
+    """(1-t) gamma g + t f: f = ``target`` (one system, or a list of systems
+    sharing supports: one per target), g = the supports with the
+    coefficients ``start_coefs``."""
+    L = load()
+    systems = target if isinstance(target, (list, tuple)) else [target]
+    tpe, exps, _ = _lists(systems[0])
+    for t in systems[1:]:
+        if not (np.array_equal(np.asarray(t.terms_per_eq), tpe) and np.array_equal(np.asarray(t.exps), exps)):
+            raise ValueError("targets must share terms_per_eq and exps")
+    ct = np.ascontiguousarray(np.stack([np.asarray(t.coefs, dtype=np.complex128) for t in systems]))
+    cs = np.ascontiguousarray(np.asarray(start_coefs, dtype=np.complex128).reshape(-1))
+    out = ctypes.c_void_p()
+    _check(L.phc_make_parameter_homotopy(int(systems[0].n_eq), int(systems[0].n_var), tpe.ctypes.data,
+                                         exps.ctypes.data, len(systems), cs.ctypes.data, ct.ctypes.data,
+                                         phc_cd(float(np.real(gamma)), float(np.imag(gamma))), ctypes.byref(out)))
+    return Homotopy(out.value, int(systems[0].n_var))
+
+
+def phc_track_from(h: Homotopy, starts, n_starts: int, starts_per_system: int, opts, x_out, cls_out,
+                   stats_out=None, stream=None):
+    """starts: complex128 CUDA tensor [n_var, n_starts] (SoA)."""
+    _check(load().phc_track_from(ctypes.c_void_p(h.ptr), _ptr(starts), int(n_starts), int(starts_per_system),
+                                 ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
+                                 _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_membership_test(emb, k: int, witness, points, tol: float, opts, on_out, x_out=None, cls_out=None,
+                        stream=None):
+    """emb: the embedded system E_k (lists); witness: complex128 CUDA tensor
+    [n_var, m]; points: host array [p, n_var - k]; on_out: uint8 CUDA tensor [p]."""
+    L = load()
+    tpe, exps, coefs = _lists(emb)
+    pts = np.ascontiguousarray(np.atleast_2d(np.asarray(points, dtype=np.complex128)))
+    if 1 <= int(k) < int(emb.n_var) and pts.shape[1] != int(emb.n_var) - int(k):
+        raise ValueError(f"test points need {int(emb.n_var) - int(k)} coordinates, got {pts.shape[1]}")
+    m = int(witness.shape[1])
+    _check(L.phc_membership_test(int(emb.n_eq), int(emb.n_var), tpe.ctypes.data, exps.ctypes.data,
+                                 coefs.ctypes.data, int(k), _ptr(witness), m, pts.ctypes.data, pts.shape[0],
+                                 ctypes.c_double(tol), ctypes.byref(opts) if opts is not None else None,
+                                 _ptr(on_out), _ptr(x_out), _ptr(cls_out), _stream_ptr(stream)))
+
+
 def phc_num_paths(h: Homotopy) -> int:
     v = ctypes.c_int64()
     _check(load().phc_num_paths(ctypes.c_void_p(h.ptr), ctypes.byref(v)))
@@ -250,6 +301,33 @@ def phc_embed(sys, top_dim: int, gammas=None, hyper=None, seed: int = 0) -> Syst
     )
     L.phc_free_lists(out)
     return res
+
+
+def _copy_lists(L, out) -> SystemLists:
+    s = out.contents
+    T, N = s.n_terms, s.n_var
+    res = SystemLists(
+        s.n_eq, N,
+        np.ctypeslib.as_array(s.terms_per_eq, shape=(s.n_eq,)).copy(),
+        np.ctypeslib.as_array(s.exps, shape=(T * N,)).copy().reshape(T, N),
+        np.ctypeslib.as_array(ctypes.cast(s.coefs, ctypes.POINTER(ctypes.c_double)), shape=(2 * T,)).copy()
+        .view(np.complex128),
+    )
+    L.phc_free_lists(out)
+    return res
+
+
+def phc_square(sys, consts=None, seed: int = 0) -> SystemLists:
+    """The square system of Section 2.1 (random hyperplanes for an
+    underdetermined, new unknowns with random multipliers for an
+    overdetermined system)."""
+    L = load()
+    tpe, exps, coefs = _lists(sys)
+    c = None if consts is None else np.ascontiguousarray(consts, dtype=np.complex128)
+    out = ctypes.POINTER(phc_system_lists)()
+    _check(L.phc_square(int(sys.n_eq), int(sys.n_var), tpe.ctypes.data, exps.ctypes.data, coefs.ctypes.data,
+                        None if c is None else c.ctypes.data, ctypes.c_uint64(seed), ctypes.byref(out)))
+    return _copy_lists(L, out)
 
 
 def phc_cascade_stage(h: Homotopy, k: int, starts, n_starts: int, opts, x_out, cls_out, slack_zero_out,

@@ -118,6 +118,12 @@ struct phc_homotopy {
     int device = 0;
     DeviceTable total;    // total-degree homotopy
     DeviceTable cascade;  // cascade stage (last slack), built on first use
+    // coefficient-parameter homotopy (phc_make_parameter_homotopy): no
+    // total-degree start system; `total` holds (gamma c_start, c_target -
+    // gamma c_start) per term and `target` (c_target, 0), the exact target
+    // for the classification and refinement at t = 1
+    int parameter = 0;
+    DeviceTable target;
     int32_t *d_deg = nullptr, *d_root_off = nullptr;
     double2 *d_roots = nullptr;
     // scratch
@@ -372,11 +378,87 @@ extern "C" int phc_make_homotopy(int n_eq, int n_var, const int32_t *tpe, const 
     return phc_make_homotopy_batch(n_eq, n_var, tpe, exps, 1, coefs, &gamma, out);
 }
 
+extern "C" int phc_make_parameter_homotopy(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps,
+                                           int n_sys, const phc_cd *coefs_start, const phc_cd *coefs_target,
+                                           phc_cd gamma, phc_homotopy **out)
+{
+    if (!out) return fail(PHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_sys < 1) return fail(PHC_EINVAL, "n_systems = %d < 1", n_sys);
+    if (!coefs_start || !coefs_target) return fail(PHC_EINVAL, "NULL coefficients");
+    std::vector<int32_t> deg;
+    int rc = validate_lists(n_eq, n_var, tpe, exps, coefs_target, true, &deg);
+    if (rc) return rc;
+    if (!std::isfinite(gamma.re) || !std::isfinite(gamma.im) || (gamma.re == 0.0 && gamma.im == 0.0))
+        return fail(PHC_EINVAL, "gamma must be finite and nonzero");
+    const int n = n_var;
+    int64_t T = 0;
+    for (int i = 0; i < n_eq; i++) T += tpe[i];
+    for (int64_t k = 0; k < T; k++)
+        if (!std::isfinite(coefs_start[k].re) || !std::isfinite(coefs_start[k].im))
+            return fail(PHC_EINVAL, "start coefficient %lld is not finite", (long long)k);
+    for (int64_t k = 0; k < (int64_t)n_sys * T; k++)
+        if (!std::isfinite(coefs_target[k].re) || !std::isfinite(coefs_target[k].im))
+            return fail(PHC_EINVAL, "target coefficient %lld is not finite", (long long)k);
+
+    phc_homotopy *h = new (std::nothrow) phc_homotopy();
+    if (!h) return fail(PHC_ENOMEM, "host allocation");
+    h->n = n;
+    h->n_sys = n_sys;
+    h->parameter = 1;
+    h->tpe.assign(tpe, tpe + n_eq);
+    h->exps.assign(exps, exps + T * n);
+    h->coefs.assign(coefs_target, coefs_target + T);
+    h->gamma = gamma;
+    h->deg = deg;
+    h->paths_per_system = 0;
+    h->num_paths = 0;
+    cudaGetDevice(&h->device);
+    // (1-t) gamma g + t f: per term (gamma c_start, c_target - gamma c_start)
+    HostTerms ht, hf;
+    const double2 g = make_double2(gamma.re, gamma.im);
+    for (int s = 0; s < n_sys; s++) {
+        int64_t off = 0;
+        for (int i = 0; i < n; i++) {
+            for (int k = 0; k < tpe[i]; k++, off++) {
+                const phc_cd cs = coefs_start[off], ct = coefs_target[(int64_t)s * T + off];
+                const double2 c0 = make_double2(g.x * cs.re - g.y * cs.im, g.x * cs.im + g.y * cs.re);
+                const double2 c1 = make_double2(ct.re - c0.x, ct.im - c0.y);
+                const double2 f0 = make_double2(ct.re, ct.im), zero = make_double2(0.0, 0.0);
+                if (s == 0) {
+                    ht.add(i, exps + off * n, n, c0, c1);
+                    hf.add(i, exps + off * n, n, f0, zero);
+                } else {
+                    ht.add_coef(c0, c1);
+                    hf.add_coef(f0, zero);
+                }
+            }
+        }
+    }
+    cudaStream_t ps = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return fail(PHC_ECUDA, "cudaStreamCreateWithFlags");
+    }
+    rc = upload_table(ht, n, h->total, ps);
+    if (!rc) rc = upload_table(hf, n, h->target, ps);
+    cudaStreamDestroy(ps);
+    if (!rc && cudaMalloc(&h->d_qhead, sizeof(unsigned long long)) != cudaSuccess)
+        rc = fail(PHC_ENOMEM, "cudaMalloc of the path counter");
+    if (rc) {
+        phc_destroy_homotopy(h);
+        return rc;
+    }
+    *out = h;
+    return PHC_OK;
+}
+
 extern "C" void phc_destroy_homotopy(phc_homotopy *h)
 {
     if (!h) return;
     free_table(h->total);
     free_table(h->cascade);
+    free_table(h->target);
     if (h->d_deg) cudaFree(h->d_deg);
     if (h->d_root_off) cudaFree(h->d_root_off);
     if (h->d_roots) cudaFree(h->d_roots);
@@ -456,9 +538,17 @@ static int ensure_xfull(phc_homotopy *h, int64_t elems)
 
 // ------------------------------------------------------------------ tracking
 
+// The table the endpoints are classified and refined with: the homotopy at
+// t = 1 (for a parameter homotopy its exact target).
+static const DevTables &end_table(const phc_homotopy *h)
+{
+    return h->parameter ? h->target.view : h->total.view;
+}
+
 static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, const double2 *starts, int64_t first,
                      int64_t n, const phc_opts &o, double2 *x_out, int8_t *cls_out, phc_path_stats *stats,
-                     cudaStream_t s, const int8_t *sel_cls = nullptr, const uint8_t *sel_sz = nullptr)
+                     cudaStream_t s, const int8_t *sel_cls = nullptr, const uint8_t *sel_sz = nullptr,
+                     int64_t starts_per_system = 0, const DevTables *cls_tab = nullptr)
 {
     CU(cudaMemsetAsync(h->d_qhead, 0, sizeof(unsigned long long), s));
     phc::TrackLaunch L{};
@@ -474,6 +564,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.first = first;
     L.n_paths = n;
     L.paths_per_system = h->paths_per_system > 0 ? h->paths_per_system : 1;
+    L.starts_per_system = starts_per_system;
     L.x_out = x_out;
     L.stats = stats;
     L.qhead = h->d_qhead;
@@ -501,7 +592,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
         if (e != cudaSuccess) return fail(PHC_ECUDA, "tail kernel launch: %s", cudaGetErrorString(e));
     }
     phc::ClassifyLaunch C{};
-    C.tab = tab;
+    C.tab = cls_tab ? *cls_tab : tab;
     C.tab.f32 = 0;
     C.n_paths = n;
     C.x = x_out;
@@ -517,6 +608,8 @@ extern "C" int phc_track_paths(phc_homotopy *h, int64_t first, int64_t n, const 
                                int8_t *cls_out, phc_path_stats *stats_out, void *stream)
 {
     if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (h->parameter && n > 0)
+        return fail(PHC_EINVAL, "a parameter homotopy has no total-degree start system (use phc_track_from)");
     if (n < 0 || first < 0 || first + n > h->num_paths)
         return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
                     (long long)(first + n), (long long)h->num_paths);
@@ -534,6 +627,33 @@ extern "C" int phc_track_paths(phc_homotopy *h, int64_t first, int64_t n, const 
     }
     return run_track(h, h->total.view, 0, nullptr, first, n, o, reinterpret_cast<double2 *>(x_out), cls_out, st,
                      static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int phc_track_from(phc_homotopy *h, const phc_cd *starts, int64_t n, int64_t starts_per_system,
+                              const phc_opts *opts, phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out,
+                              void *stream)
+{
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (n < 0 || starts_per_system < 0) return fail(PHC_EINVAL, "n_starts or starts_per_system < 0");
+    if (n == 0) return PHC_OK;
+    if (!starts || !x_out || !cls_out) return fail(PHC_EINVAL, "NULL array");
+    const int64_t systems = starts_per_system > 0 ? (n + starts_per_system - 1) / starts_per_system : 1;
+    if (systems > h->n_sys)
+        return fail(PHC_EINVAL, "%lld starts at %lld per system need %lld systems, the handle has %d", (long long)n,
+                    (long long)starts_per_system, (long long)systems, h->n_sys);
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    phc_path_stats *st = stats_out;
+    if (!st) {
+        rc = ensure_stats(h, n);
+        if (rc) return rc;
+        st = h->d_stats;
+    }
+    return run_track(h, h->total.view, 1, reinterpret_cast<const double2 *>(starts), 0, n, o,
+                     reinterpret_cast<double2 *>(x_out), cls_out, st, static_cast<cudaStream_t>(stream), nullptr,
+                     nullptr, starts_per_system, &end_table(h));
 }
 
 // Cascade homotopy on the handle's system E_k: every term keeps its
@@ -612,6 +732,7 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
     for (int i = 0; i < n_h; i++) {
         if (!hs[i]) return fail(PHC_EINVAL, "handle %d is NULL", i);
         if (hs[i]->n_sys != 1) return fail(PHC_EUNSUPPORTED, "handle %d is a batch handle", i);
+        if (hs[i]->parameter) return fail(PHC_EINVAL, "handle %d is a parameter homotopy", i);
         if (!x_out[i] || !cls_out[i]) return fail(PHC_EINVAL, "NULL output array of handle %d", i);
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -853,6 +974,109 @@ extern "C" int phc_cascade_from(const phc_homotopy *hc, int k, const phc_cd *x_p
     return PHC_OK;
 }
 
+extern "C" int phc_membership_test(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps,
+                                   const phc_cd *coefs, int k, const phc_cd *witness, int64_t m,
+                                   const phc_cd *points, int64_t p, double tol, const phc_opts *opts,
+                                   uint8_t *on_out, phc_cd *x_out, int8_t *cls_out, void *stream)
+{
+    if (k < 1 || k >= n_var) return fail(PHC_EINVAL, "k = %d outside 1..n_var-1", k);
+    if (m < 1 || p < 0) return fail(PHC_EINVAL, "need m >= 1 witness points and p >= 0 test points");
+    if (p == 0) return PHC_OK;
+    if (!witness || !points || !on_out) return fail(PHC_EINVAL, "NULL array");
+    if (!(tol > 0.0)) return fail(PHC_EINVAL, "tol must be positive");
+    if (p > 0x7fffffff) return fail(PHC_EUNSUPPORTED, "more than 2^31 - 1 test points in one call");
+    int rc = validate_lists(n_eq, n_var, tpe, exps, coefs, true, nullptr);
+    if (rc) return rc;
+    const int n = n_var, nx = n_var - k;
+    int64_t T = 0;
+    for (int i = 0; i < n_eq; i++) T += tpe[i];
+    // the hyperplanes are the last k equations: one constant term, linear
+    // terms in x and slack terms; find the constant of each
+    std::vector<int64_t> const_term(k, -1);
+    {
+        int64_t off = 0;
+        for (int i = 0; i < n_eq; i++) {
+            for (int q = 0; q < tpe[i]; q++, off++) {
+                if (i < n_eq - k) continue;
+                int d = 0;
+                for (int j = 0; j < n; j++) d += exps[off * n + j];
+                if (d > 1) return fail(PHC_EINVAL, "equation %d is not a hyperplane (term of degree %d)", i, d);
+                if (d == 0) {
+                    if (const_term[i - (n_eq - k)] >= 0)
+                        return fail(PHC_EINVAL, "hyperplane %d has two constant terms", i);
+                    const_term[i - (n_eq - k)] = off;
+                }
+            }
+        }
+        for (int j = 0; j < k; j++)
+            if (const_term[j] < 0) return fail(PHC_EINVAL, "hyperplane %d has no constant term", n_eq - k + j);
+    }
+    for (int64_t j = 0; j < p * nx; j++)
+        if (!std::isfinite(points[j].re) || !std::isfinite(points[j].im))
+            return fail(PHC_EINVAL, "test point coordinate %lld is not finite", (long long)j);
+    // target system of test point z: the constant of hyperplane j becomes
+    // -sum_i c_ji z_i, so (z, slacks 0) satisfies every hyperplane
+    std::vector<phc_cd> target((size_t)(p * T));
+    for (int64_t t = 0; t < p; t++) {
+        phc_cd *c = target.data() + t * T;
+        std::memcpy(c, coefs, T * sizeof(phc_cd));
+        const phc_cd *z = points + t * nx;
+        for (int j = 0; j < k; j++) {
+            const int row = n_eq - k + j;
+            int64_t o2 = 0;
+            for (int i = 0; i < row; i++) o2 += tpe[i];
+            double re = 0.0, im = 0.0;
+            for (int q = 0; q < tpe[row]; q++) {
+                const int64_t term = o2 + q;
+                int v = -1;
+                for (int jj = 0; jj < n; jj++)
+                    if (exps[term * n + jj]) v = jj;
+                if (v < 0 || v >= nx) continue;
+                const phc_cd a = coefs[term], zz = z[v];
+                re -= a.re * zz.re - a.im * zz.im;
+                im -= a.re * zz.im + a.im * zz.re;
+            }
+            c[const_term[j]] = {re, im};
+        }
+    }
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    rc = check_opts(o);
+    if (rc) return rc;
+    phc_homotopy *h = nullptr;
+    rc = phc_make_parameter_homotopy(n_eq, n_var, tpe, exps, (int)p, coefs, target.data(), phc_cd{1.0, 0.0}, &h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t total = p * m;
+    double2 *tiles = nullptr, *xo = reinterpret_cast<double2 *>(x_out), *pts = nullptr;
+    int8_t *co = cls_out;
+    cudaError_t e = cudaMalloc(&tiles, (size_t)total * n * sizeof(double2));
+    if (e == cudaSuccess && !xo) e = cudaMalloc(&xo, (size_t)total * n * sizeof(double2));
+    if (e == cudaSuccess && !co) e = cudaMalloc(&co, (size_t)total);
+    if (e == cudaSuccess) e = cudaMalloc(&pts, (size_t)p * nx * sizeof(double2));
+    std::vector<double2> pts_h((size_t)(p * nx));
+    for (int64_t t = 0; t < p; t++)
+        for (int l = 0; l < nx; l++) pts_h[(size_t)l * p + t] = make_double2(points[t * nx + l].re, points[t * nx + l].im);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pts, pts_h.data(), pts_h.size() * sizeof(double2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = phc::launch_tile_starts(reinterpret_cast<const double2 *>(witness), n, m, p, tiles, s);
+    if (e == cudaSuccess) {
+        rc = phc_track_from(h, reinterpret_cast<const phc_cd *>(tiles), total, m, &o, reinterpret_cast<phc_cd *>(xo), co,
+                            nullptr, stream);
+        if (!rc) e = phc::launch_match_points(xo, co, n, m, p, pts, nx, tol, on_out, s);
+    }
+    if (e != cudaSuccess && !rc) rc = fail(PHC_ECUDA, "membership test: %s", cudaGetErrorString(e));
+    // the temporaries and the handle are released once the work is done
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (es != cudaSuccess && !rc) rc = fail(PHC_ECUDA, "membership test: %s", cudaGetErrorString(es));
+    if (tiles) cudaFree(tiles);
+    if (pts) cudaFree(pts);
+    if (!x_out && xo) cudaFree(xo);
+    if (!cls_out && co) cudaFree(co);
+    phc_destroy_homotopy(h);
+    return rc;
+}
+
 extern "C" int phc_refine_endpoints(const phc_homotopy *hc, phc_cd *x_hi, phc_cd *x_lo, int64_t n,
                                     double cond_threshold, double cond_max, int max_iters, int8_t *cls,
                                     phc_path_stats *stats, void *stream)
@@ -862,7 +1086,7 @@ extern "C" int phc_refine_endpoints(const phc_homotopy *hc, phc_cd *x_hi, phc_cd
     if (n == 0) return PHC_OK;
     if (!x_hi || !x_lo || !cls || !stats) return fail(PHC_EINVAL, "NULL array");
     phc::RefineLaunch L{};
-    L.tab = hc->total.view;
+    L.tab = end_table(hc);
     L.n = n;
     L.x_hi = reinterpret_cast<double2 *>(x_hi);
     L.x_lo = reinterpret_cast<double2 *>(x_lo);
@@ -961,6 +1185,84 @@ extern "C" int phc_embed(int n_eq, int n_var, const int32_t *tpe, const uint8_t 
     std::memcpy(L->coefs, ocoef.data(), ocoef.size() * sizeof(phc_cd));
     *out = L;
     return PHC_OK;
+}
+
+// Output lists of a host-side transformation (phc_embed, phc_square).
+static int make_lists(int n_eq, int n_var, const std::vector<int32_t> &tpe, const std::vector<uint8_t> &ex,
+                      const std::vector<phc_cd> &co, phc_system_lists **out)
+{
+    phc_system_lists *L = new (std::nothrow) phc_system_lists();
+    if (!L) return fail(PHC_ENOMEM, "host allocation");
+    L->n_eq = n_eq;
+    L->n_var = n_var;
+    L->n_terms = (int32_t)co.size();
+    L->terms_per_eq = new (std::nothrow) int32_t[tpe.size()];
+    L->exps = new (std::nothrow) uint8_t[ex.size() ? ex.size() : 1];
+    L->coefs = new (std::nothrow) phc_cd[co.size() ? co.size() : 1];
+    if (!L->terms_per_eq || !L->exps || !L->coefs) {
+        phc_free_lists(L);
+        return fail(PHC_ENOMEM, "host allocation");
+    }
+    std::memcpy(L->terms_per_eq, tpe.data(), tpe.size() * sizeof(int32_t));
+    std::memcpy(L->exps, ex.data(), ex.size());
+    std::memcpy(L->coefs, co.data(), co.size() * sizeof(phc_cd));
+    *out = L;
+    return PHC_OK;
+}
+
+extern "C" int phc_square(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                          const phc_cd *consts, uint64_t seed, phc_system_lists **out)
+{
+    if (!out) return fail(PHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_lists(n_eq, n_var, tpe, exps, coefs, false, nullptr);
+    if (rc) return rc;
+    const int N = n_eq > n_var ? n_eq : n_var;  // unknowns and equations of the square system
+    if (N > PHC_MAX_VARS) return fail(PHC_EINVAL, "the square system has %d unknowns, above %d", N, PHC_MAX_VARS);
+    const int extra = N - (n_eq < n_var ? n_eq : n_var);
+    const size_t n_const = n_eq < n_var ? (size_t)extra * (n_var + 1) : (size_t)n_eq * extra;
+    std::vector<phc_cd> drawn(consts ? 0 : n_const);
+    if (!consts) {
+        Lcg r{seed ^ 0x9E3779B97F4A7C15ULL};
+        for (auto &v : drawn) v = r.cnormal();
+    }
+    const phc_cd *C = consts ? consts : drawn.data();
+    for (size_t i = 0; i < n_const; i++)
+        if (!std::isfinite(C[i].re) || !std::isfinite(C[i].im)) return fail(PHC_EINVAL, "constant %zu is not finite", i);
+    std::vector<int32_t> otpe;
+    std::vector<uint8_t> oexp;
+    std::vector<phc_cd> ocoef;
+    int64_t off = 0;
+    for (int i = 0; i < n_eq; i++) {
+        for (int k = 0; k < tpe[i]; k++, off++) {
+            for (int j = 0; j < N; j++) oexp.push_back(j < n_var ? exps[off * n_var + j] : 0);
+            ocoef.push_back(coefs[off]);
+        }
+        int m = tpe[i];
+        if (n_eq > n_var) {
+            // overdetermined: every equation gains consts[i][k] s_k for the new unknowns s_k
+            for (int k = 0; k < extra; k++) {
+                for (int j = 0; j < N; j++) oexp.push_back(j == n_var + k ? 1 : 0);
+                ocoef.push_back(C[(size_t)i * extra + k]);
+            }
+            m += extra;
+        }
+        otpe.push_back(m);
+    }
+    if (n_eq < n_var) {
+        // underdetermined: consts[k][0] + sum_j consts[k][j+1] x_j = 0, k < n_var - n_eq
+        for (int k = 0; k < extra; k++) {
+            const phc_cd *h = C + (size_t)k * (n_var + 1);
+            for (int j = 0; j < N; j++) oexp.push_back(0);
+            ocoef.push_back(h[0]);
+            for (int v = 0; v < n_var; v++) {
+                for (int j = 0; j < N; j++) oexp.push_back(j == v ? 1 : 0);
+                ocoef.push_back(h[v + 1]);
+            }
+            otpe.push_back(n_var + 1);
+        }
+    }
+    return make_lists(N, N, otpe, oexp, ocoef, out);
 }
 
 extern "C" void phc_free_lists(phc_system_lists *L)

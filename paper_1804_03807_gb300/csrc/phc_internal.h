@@ -119,6 +119,7 @@ struct TrackLaunch {
     int64_t first;
     int64_t n_paths;
     int64_t paths_per_system; // global path p belongs to system p / paths_per_system
+    int64_t starts_per_system;  // modes 1 and 2: entry q belongs to system q / starts_per_system (0: system 0)
     double2 *x_out;           // SoA [n][n_paths]
     phc_path_stats *stats;    // [n_paths]
     unsigned long long *qhead;
@@ -232,6 +233,14 @@ int64_t pipe_lanes(const TrackLaunch &L, int block_threads, int max_blocks);
 bool tail_pipe_supported(const DevTables &t1, const DevTables &t2);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
+// match[j] = 1 when one of the m endpoints x[:, j*m .. j*m+m) (SoA over
+// p*m entries, N unknowns) of class PHC_REGULAR or PHC_SINGULAR equals
+// points[:, j] (SoA [n_pt][p]) in its first n_pt unknowns and has its other
+// unknowns (the slacks) zero, within tol (1 + ||points_j||).
+cudaError_t launch_match_points(const double2 *x, const int8_t *cls, int N, int64_t m, int64_t p,
+                                const double2 *points, int n_pt, double tol, uint8_t *match, cudaStream_t s);
+// Copies the m start points (SoA [N][m]) p times: out SoA [N][p*m].
+cudaError_t launch_tile_starts(const double2 *starts, int N, int64_t m, int64_t p, double2 *out, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,
                              uint8_t *slack_zero, int has_next_slack, double slack_tol, cudaStream_t s);
 

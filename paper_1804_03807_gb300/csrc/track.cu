@@ -36,6 +36,47 @@ __global__ void drop_last_kernel(const double2 *x_full, int n_full, int64_t np, 
     }
 }
 
+// One block per test point j: its m endpoints are compared with the point
+// (homotopy membership test, Section 4.1: the point lies on the component
+// when it is one of the endpoints of the paths from the witness points).
+__global__ void match_points_kernel(const double2 *x, const int8_t *cls, int N, int64_t m, int64_t p,
+                                    const double2 *points, int n_pt, double tol, uint8_t *match)
+{
+    const int64_t j = blockIdx.x;
+    if (j >= p) return;
+    double np = 0.0;
+    for (int l = 0; l < n_pt; l++) {
+        const double a = absinf(points[(int64_t)l * p + j]);
+        if (!(a <= np)) np = a;
+    }
+    const double bound = tol * (1.0 + np);
+    int hit = 0;
+    const int64_t total = p * m;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const int64_t e = j * m + i;
+        if (cls[e] != PHC_REGULAR && cls[e] != PHC_SINGULAR) continue;
+        bool same = true;
+        for (int l = 0; l < N; l++) {
+            const double2 v = x[(int64_t)l * total + e];
+            const double2 w = l < n_pt ? points[(int64_t)l * p + j] : make_double2(0.0, 0.0);
+            const double d = absinf(make_double2(v.x - w.x, v.y - w.y));
+            same = same && d <= bound;
+        }
+        hit |= same ? 1 : 0;
+    }
+    hit = __syncthreads_or(hit);
+    if (threadIdx.x == 0) match[j] = hit ? 1 : 0;
+}
+
+__global__ void tile_starts_kernel(const double2 *starts, int N, int64_t m, int64_t p, double2 *out)
+{
+    const int64_t total = p * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % m;
+        for (int l = 0; l < N; l++) out[(int64_t)l * total + e] = starts[(int64_t)l * m + i];
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 
 int g_num_sms = 0, g_smem_optin = 0;
@@ -125,6 +166,25 @@ cudaError_t launch_roots(const int32_t *deg, const int32_t *root_off, double2 *r
 {
     (void)total;
     roots_kernel<<<n, 64, 0, s>>>(deg, root_off, roots, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_points(const double2 *x, const int8_t *cls, int N, int64_t m, int64_t p,
+                                const double2 *points, int n_pt, double tol, uint8_t *match, cudaStream_t s)
+{
+    if (p <= 0) return cudaSuccess;
+    if (p > 0x7fffffffLL) return cudaErrorInvalidValue;
+    match_points_kernel<<<(unsigned)p, 128, 0, s>>>(x, cls, N, m, p, points, n_pt, tol, match);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_starts(const double2 *starts, int N, int64_t m, int64_t p, double2 *out, cudaStream_t s)
+{
+    device_limits();
+    if (p <= 0 || m <= 0) return cudaSuccess;
+    int64_t grid = (p * m + 255) / 256;
+    if (grid > (int64_t)g_num_sms * 16) grid = (int64_t)g_num_sms * 16;
+    tile_starts_kernel<<<(unsigned)grid, 256, 0, s>>>(starts, N, m, p, out);
     return cudaGetLastError();
 }
 

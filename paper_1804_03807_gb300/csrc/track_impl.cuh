@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                     x0[i] = L.roots[L.root_off[i] + k];
                 }
             } else {
-                sys = 0;
+                sys = L.starts_per_system > 0 ? (int)(q / L.starts_per_system) : 0;
                 double nx = 0.0;
 #pragma unroll
                 for (int i = 0; i < N; i++) {

@@ -123,3 +123,63 @@ def test_embed_errors_and_seeded_constants():
     b = P.phc_embed(cyclic(4), 1, seed=7)
     c = P.phc_embed(cyclic(4), 1, seed=8)
     assert np.array_equal(a.coefs, b.coefs) and not np.array_equal(a.coefs, c.coefs)
+
+
+def test_parameter_homotopy_and_membership_reject_bad_input():
+    """Checked on the host before any device work."""
+    s = cyclic(3)
+    with pytest.raises(P.PhcError) as e:
+        P.phc_make_parameter_homotopy(s, s.coefs, 0.0)
+    assert e.value.code == P._lib.PHC_EINVAL and "gamma" in str(e.value)
+    bad = np.array(s.coefs, dtype=complex)
+    bad[1] = np.nan
+    with pytest.raises(P.PhcError) as e:
+        P.phc_make_parameter_homotopy(s, bad, 1.0)
+    assert "start coefficient" in str(e.value)
+    E = P.phc_embed(multistep_example(), 1, *embedding_constants(rng_for(5), 4, 4, 1))
+
+    class Fake:  # stands for device tensors: never dereferenced on these paths
+        def __init__(self, shape):
+            self.shape = shape
+
+        def data_ptr(self):
+            return 16
+
+        def contiguous(self):
+            return self
+
+    on = Fake((1,))
+    for k, tol, needle in [(0, 1e-3, "k = 0"), (5, 1e-3, "k = 5"), (1, 0.0, "tol")]:
+        with pytest.raises(P.PhcError) as e:
+            P.phc_membership_test(E, k, Fake((5, 1)), np.zeros((1, 4)), tol, None, on, stream=0)
+        assert needle in str(e.value)
+    # the last equation of the original system is not a hyperplane
+    with pytest.raises(P.PhcError) as e:
+        P.phc_membership_test(multistep_example(), 1, Fake((4, 1)), np.zeros((1, 3)), 1e-3, None, on, stream=0)
+    assert "not a hyperplane" in str(e.value)
+    pts = np.zeros((1, 4), complex)
+    pts[0, 2] = np.inf
+    with pytest.raises(P.PhcError) as e:
+        P.phc_membership_test(E, 1, Fake((5, 1)), pts, 1e-3, None, on, stream=0)
+    assert "not finite" in str(e.value)
+
+
+def test_square_matches_the_oracle():
+    """phc_square (host code of the library) against the oracle's list
+    manipulation, with the same constants: an underdetermined, an
+    overdetermined and a square system."""
+    rng = rng_for(81)
+    sphere = PolySystem(1, 3, np.array([4]), np.array([[2, 0, 0], [0, 2, 0], [0, 0, 2], [0, 0, 0]], np.uint8),
+                        np.array([1, 1, 1, -1], complex), name="sphere")
+    over = PolySystem(3, 2, np.array([2, 2, 2]), np.array([[1, 0], [0, 0], [0, 1], [0, 0], [1, 1], [0, 0]], np.uint8),
+                      np.array([1, -1, 1, -2, 1, -2], complex), name="over")
+    for sys, shape in [(sphere, (2, 4)), (over, (3, 1)), (cyclic(4), (0, 0))]:
+        c = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+        a = P.phc_square(sys, c if c.size else None)
+        b = oracle.square(sys, c)
+        assert (a.n_eq, a.n_var) == (b.n_eq, b.n_var) == (max(sys.n_eq, sys.n_var),) * 2
+        assert np.array_equal(a.terms_per_eq, b.terms_per_eq)
+        assert np.array_equal(a.exps, b.exps)
+        assert np.array_equal(a.coefs, b.coefs)
+    with pytest.raises(P.PhcError):
+        P.phc_embed(sphere, 1)  # embedding needs a square system
