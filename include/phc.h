@@ -342,6 +342,26 @@ int phc_membership_test(int n_eq, int n_var, const int32_t *terms_per_eq, const 
                         int64_t p, double tol, const phc_opts *opts, uint8_t *on_out, phc_cd *x_out,
                         int8_t *cls_out, void *cuda_stream);
 
+/* A prepared phc_track_many call (the same systems, options and output
+ * arrays every time): phc_many_plan_create checks the arguments, groups the
+ * systems by number of unknowns, uploads the per-system descriptors and
+ * allocates the path counters, the hand-off records of the tail kernel and,
+ * for handles given no stats array, per-path records of its own (host call:
+ * it synchronises with the device; the helper streams it creates inherit
+ * cuda_stream's priority).  phc_many_plan_run then enqueues, on cuda_stream,
+ * only memsets and kernel launches -- no allocation, no host
+ * synchronisation -- so it can be captured in a CUDA graph and replayed;
+ * every run writes the outputs phc_track_many would.  Runs of one plan must
+ * not overlap on the GPU, and the handles must outlive the plan.
+ * phc_many_plan_destroy frees the plan after its work has finished.
+ * Errors: as phc_track_many. */
+typedef struct phc_many_plan phc_many_plan;
+int phc_many_plan_create(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
+                         int8_t *const *cls_out, phc_path_stats *const *stats_out, void *cuda_stream,
+                         phc_many_plan **out);
+int phc_many_plan_run(phc_many_plan *plan, void *cuda_stream);
+void phc_many_plan_destroy(phc_many_plan *plan);
+
 /* The top stage and the cascade stage below it in one launch (Section 3.1,
  * Figure 3; the GPU counterpart of the paper's pipelining, Section 2.2).
  * Tracks paths first_path .. first_path + n_paths - 1 of the total-degree

@@ -31,7 +31,8 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    phc_make_homotopy_batch,
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
                    phc_tail_paths, phc_track_many, phc_track_paths_noalloc, phc_track_pipeline,
-                   phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square)
+                   phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square,
+                   phc_many_plan_create, phc_many_plan_run, ManyPlan)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -42,7 +43,7 @@ __all__ = [
     "phc_track_pipeline", "track_many", "phc_cascade_from", "PHC_STOP_SKIPPED", "cascade_from",
     "Tracked", "pipeline", "track", "cascade", "refine",
     "stats_numpy", "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
-    "track_from", "membership", "phc_square",
+    "track_from", "membership", "phc_square", "phc_many_plan_create", "phc_many_plan_run", "ManyPlan",
 ]
 
 

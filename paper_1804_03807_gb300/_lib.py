@@ -29,7 +29,7 @@ EXPORTED = [
     "phc_refine_endpoints", "phc_last_error", "phc_destroy_homotopy", "phc_free_lists", "phc_sizeof_opts",
     "phc_sizeof_stats", "phc_track_paths_noalloc", "phc_make_homotopy_batch", "phc_track_pipeline",
     "phc_track_many", "phc_cascade_from", "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from",
-    "phc_membership_test", "phc_square",
+    "phc_membership_test", "phc_square", "phc_many_plan_create", "phc_many_plan_run", "phc_many_plan_destroy",
 ]
 
 
@@ -94,6 +94,10 @@ def load() -> ctypes.CDLL:
     L.phc_track_paths_noalloc.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
+    L.phc_many_plan_create.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp, ctypes.POINTER(vp)]
+    L.phc_many_plan_run.argtypes = [vp, vp]
+    L.phc_many_plan_destroy.argtypes = [vp]
+    L.phc_many_plan_destroy.restype = None
     L.phc_square.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.c_uint64,
                              ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_cascade_stage.argtypes = [vp, i32, vp, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
@@ -117,7 +121,7 @@ def load() -> ctypes.CDLL:
                  "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats",
                  "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
-                 "phc_square"):
+                 "phc_square", "phc_many_plan_create", "phc_many_plan_run"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
         raise ImportError("phc_opts layout mismatch between phc.h and the binding")
@@ -354,6 +358,36 @@ def phc_track_many(hs, opts, x_outs, cls_outs, stats_outs=None, stream=None):
     S = None if stats_outs is None else (ctypes.c_void_p * n)(*[_ptr(t) for t in stats_outs])
     _check(load().phc_track_many(H, n, ctypes.byref(opts) if opts is not None else None, X, C, S,
                                  _stream_ptr(stream)))
+
+
+class ManyPlan:
+    """Owning wrapper of a phc_many_plan* (destroyed with the object); keeps
+    the handles and output tensors it refers to alive."""
+
+    def __init__(self, ptr: int, keep):
+        self.ptr = ptr
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.phc_many_plan_destroy(ctypes.c_void_p(self.ptr))
+            self.ptr = None
+
+
+def phc_many_plan_create(hs, opts, x_outs, cls_outs, stats_outs=None, stream=None) -> ManyPlan:
+    n = len(hs)
+    H = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in x_outs])
+    C = (ctypes.c_void_p * n)(*[_ptr(c) for c in cls_outs])
+    S = None if stats_outs is None else (ctypes.c_void_p * n)(*[_ptr(t) for t in stats_outs])
+    out = ctypes.c_void_p()
+    _check(load().phc_many_plan_create(H, n, ctypes.byref(opts) if opts is not None else None, X, C, S,
+                                       _stream_ptr(stream), ctypes.byref(out)))
+    return ManyPlan(out.value, (list(hs), list(x_outs), list(cls_outs), stats_outs))
+
+
+def phc_many_plan_run(plan: ManyPlan, stream=None):
+    _check(load().phc_many_plan_run(ctypes.c_void_p(plan.ptr), _stream_ptr(stream)))
 
 
 def phc_track_pipeline(h: Homotopy, k: int, first_path: int, n_paths: int, opts, x_top, cls_top, stats_top, x_next,

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -498,42 +499,38 @@ extern "C" int phc_sizeof_stats(void) { return (int)sizeof(phc_path_stats); }
 
 // ------------------------------------------------------------------ scratch
 
-static int ensure_stats(phc_homotopy *h, int64_t n)
+// The handle's scratch grows on the stream of the call that needs it
+// (stream-ordered free and allocation: no device-wide synchronisation, so a
+// call that grows it does not wait for work on other streams).
+static int grow(void **ptr, int64_t *cap, int64_t want, size_t elem, cudaStream_t s, const char *what)
 {
-    if (h->stats_cap >= n) return PHC_OK;
-    if (h->d_stats) cudaFree(h->d_stats);
-    h->d_stats = nullptr;
-    h->stats_cap = 0;
-    if (cudaMalloc(&h->d_stats, n * sizeof(phc_path_stats)) != cudaSuccess)
-        return fail(PHC_ENOMEM, "cudaMalloc of %lld path records", (long long)n);
-    h->stats_cap = n;
+    if (*cap >= want) return PHC_OK;
+    if (*ptr) cudaFreeAsync(*ptr, s);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMallocAsync(ptr, (size_t)want * elem, s) != cudaSuccess)
+        return fail(PHC_ENOMEM, "cudaMallocAsync of %lld %s", (long long)want, what);
+    *cap = want;
     return PHC_OK;
 }
 
-static int ensure_handoff(phc_homotopy *h, int64_t lanes)
+static int ensure_stats(phc_homotopy *h, int64_t n, cudaStream_t s)
 {
-    if (!h->d_tailc && cudaMalloc(&h->d_tailc, 4 * sizeof(unsigned long long)) != cudaSuccess)
-        return fail(PHC_ENOMEM, "cudaMalloc of the tail counters");
-    if (h->handoff_cap >= lanes) return PHC_OK;
-    if (h->d_handoff) cudaFree(h->d_handoff);
-    h->d_handoff = nullptr;
-    h->handoff_cap = 0;
-    if (cudaMalloc(&h->d_handoff, lanes * sizeof(phc::Handoff)) != cudaSuccess)
-        return fail(PHC_ENOMEM, "cudaMalloc of %lld hand-off records", (long long)lanes);
-    h->handoff_cap = lanes;
-    return PHC_OK;
+    return grow(reinterpret_cast<void **>(&h->d_stats), &h->stats_cap, n, sizeof(phc_path_stats), s, "path records");
 }
 
-static int ensure_xfull(phc_homotopy *h, int64_t elems)
+static int ensure_handoff(phc_homotopy *h, int64_t lanes, cudaStream_t s)
 {
-    if (h->xfull_cap >= elems) return PHC_OK;
-    if (h->d_xfull) cudaFree(h->d_xfull);
-    h->d_xfull = nullptr;
-    h->xfull_cap = 0;
-    if (cudaMalloc(&h->d_xfull, elems * sizeof(double2)) != cudaSuccess)
-        return fail(PHC_ENOMEM, "cudaMalloc of %lld endpoint values", (long long)elems);
-    h->xfull_cap = elems;
-    return PHC_OK;
+    if (!h->d_tailc && cudaMallocAsync(reinterpret_cast<void **>(&h->d_tailc), 4 * sizeof(unsigned long long), s) !=
+                           cudaSuccess)
+        return fail(PHC_ENOMEM, "cudaMallocAsync of the tail counters");
+    return grow(reinterpret_cast<void **>(&h->d_handoff), &h->handoff_cap, lanes, sizeof(phc::Handoff), s,
+                "hand-off records");
+}
+
+static int ensure_xfull(phc_homotopy *h, int64_t elems, cudaStream_t s)
+{
+    return grow(reinterpret_cast<void **>(&h->d_xfull), &h->xfull_cap, elems, sizeof(double2), s, "endpoint values");
 }
 
 // ------------------------------------------------------------------ tracking
@@ -573,7 +570,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     if (tail) {
         const int64_t lanes = phc::track_lanes(L, o.block_threads, o.max_blocks);
         if (lanes < 1) return fail(PHC_EUNSUPPORTED, "no launch configuration for %d unknowns", tab.n);
-        int rc = ensure_handoff(h, lanes);
+        int rc = ensure_handoff(h, lanes, s);
         if (rc) return rc;
         CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));
         L.handoff = h->d_handoff;
@@ -621,7 +618,7 @@ extern "C" int phc_track_paths(phc_homotopy *h, int64_t first, int64_t n, const 
     if (rc) return rc;
     phc_path_stats *st = stats_out;
     if (!st) {
-        rc = ensure_stats(h, n);
+        rc = ensure_stats(h, n, static_cast<cudaStream_t>(stream));
         if (rc) return rc;
         st = h->d_stats;
     }
@@ -647,7 +644,7 @@ extern "C" int phc_track_from(phc_homotopy *h, const phc_cd *starts, int64_t n, 
     if (rc) return rc;
     phc_path_stats *st = stats_out;
     if (!st) {
-        rc = ensure_stats(h, n);
+        rc = ensure_stats(h, n, static_cast<cudaStream_t>(stream));
         if (rc) return rc;
         st = h->d_stats;
     }
@@ -703,11 +700,11 @@ extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *st
     if (rc) return rc;
     rc = ensure_cascade(h);
     if (rc) return rc;
-    rc = ensure_xfull(h, (int64_t)h->n * n);
+    rc = ensure_xfull(h, (int64_t)h->n * n, static_cast<cudaStream_t>(stream));
     if (rc) return rc;
     phc_path_stats *st = stats_out;
     if (!st) {
-        rc = ensure_stats(h, n);
+        rc = ensure_stats(h, n, static_cast<cudaStream_t>(stream));
         if (rc) return rc;
         st = h->d_stats;
     }
@@ -720,36 +717,32 @@ extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *st
     return PHC_OK;
 }
 
-extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
-                              int8_t *const *cls_out, phc_path_stats *const *stats_out, void *stream)
+// The systems of a multi-system call, grouped by number of unknowns: per
+// group the descriptors, the prefix sums of the path counts and the sizes
+// of the shared-memory regions of the tracker and of its tail kernel.
+struct ManyGroup {
+    int n = 0;
+    std::vector<phc::SysDesc> descs;
+    std::vector<int64_t> prefix{0};
+    int wtb = 0;
+    phc::TailMultiSizes tz{0, 0, 0, 0};
+};
+
+// stats_fallback(i, paths) gives the records of handle i when the caller passes none.
+template <typename F>
+static int many_groups(phc_homotopy *const *hs, int n_h, const phc_opts &o, phc_cd *const *x_out,
+                       int8_t *const *cls_out, phc_path_stats *const *stats_out, F stats_fallback,
+                       std::vector<ManyGroup> &groups)
 {
-    if (n_h < 0 || (n_h > 0 && (!hs || !x_out || !cls_out))) return fail(PHC_EINVAL, "NULL argument");
-    if (n_h == 0) return PHC_OK;
-    phc_opts o;
-    if (opts) o = *opts; else phc_default_opts(&o);
-    int rc = check_opts(o);
-    if (rc) return rc;
     for (int i = 0; i < n_h; i++) {
         if (!hs[i]) return fail(PHC_EINVAL, "handle %d is NULL", i);
         if (hs[i]->n_sys != 1) return fail(PHC_EUNSUPPORTED, "handle %d is a batch handle", i);
         if (hs[i]->parameter) return fail(PHC_EINVAL, "handle %d is a parameter homotopy", i);
         if (!x_out[i] || !cls_out[i]) return fail(PHC_EINVAL, "NULL output array of handle %d", i);
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the launches of different sizes run side by side on helper streams
-    // that fork from and join back into the caller's stream
-    static std::mutex pool_mutex;
-    static std::vector<cudaStream_t> pool;
-    cudaEvent_t fork_ev = nullptr;
-    CU(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
-    CU(cudaEventRecord(fork_ev, st));
-    std::vector<cudaEvent_t> joins;
-    int used = 0;
     for (int n = 1; n <= PHC_MAX_VARS; n++) {
-        std::vector<phc::SysDesc> descs;
-        std::vector<int64_t> prefix(1, 0);
-        int wtb = 0;
-        phc::TailMultiSizes tz{0, 0, 0, 0};
+        ManyGroup g;
+        g.n = n;
         for (int i = 0; i < n_h; i++) {
             phc_homotopy *h = hs[i];
             if (h->n != n || h->num_paths == 0) continue;
@@ -764,77 +757,152 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
             d.cls_out = cls_out[i];
             phc_path_stats *sp = stats_out ? stats_out[i] : nullptr;
             if (!sp) {
-                rc = ensure_stats(h, h->num_paths);
+                const int rc = stats_fallback(i, h->num_paths, &sp);
                 if (rc) return rc;
-                sp = h->d_stats;
             }
             d.stats = sp;
-            descs.push_back(d);
-            prefix.push_back(prefix.back() + h->num_paths);
+            g.descs.push_back(d);
+            g.prefix.push_back(g.prefix.back() + h->num_paths);
             const int b = (int)phc::warp_table_bytes(d.tab.n_terms, d.tab.n_ve, d.tab.f32);
-            if (b > wtb) wtb = b;
+            if (b > g.wtb) g.wtb = b;
             // the multi-system tail kernel's per-warp region (double precision tables)
             const int T = d.tab.n_terms, V = d.tab.n_ve, S = phc::tail_store_slots(T, V);
-            tz.table_cap = std::max(tz.table_cap, phc::warp_table_bytes(T, V, false));
-            tz.plan_cap = std::max(tz.plan_cap, phc::tail_plan_bytes(n, T, V));
-            tz.group_slots = std::max(tz.group_slots, phc::tail_group_slots(n, S));
-            tz.max_store = std::max(tz.max_store, S);
+            g.tz.table_cap = std::max(g.tz.table_cap, phc::warp_table_bytes(T, V, false));
+            g.tz.plan_cap = std::max(g.tz.plan_cap, phc::tail_plan_bytes(n, T, V));
+            g.tz.group_slots = std::max(g.tz.group_slots, phc::tail_group_slots(n, S));
+            g.tz.max_store = std::max(g.tz.max_store, S);
         }
-        if (descs.empty()) continue;
-        cudaStream_t hs_st;
-        {
-            std::lock_guard<std::mutex> lock(pool_mutex);
-            while ((int)pool.size() <= used) {
-                cudaStream_t ns;
-                CU(cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
-                pool.push_back(ns);
-            }
-            hs_st = pool[used++];
-        }
+        if (!g.descs.empty()) groups.push_back(std::move(g));
+    }
+    return PHC_OK;
+}
+
+// Device block of a group: descriptors, path counters, prefix sums, then
+// (256-aligned) the 8 hand-off counters and the hand-off records.
+struct ManyLayout {
+    int m = 0;
+    int64_t lanes = 0;
+    size_t q_off = 0, pre_off = 0, hoff = 0, bytes = 0;
+};
+
+static ManyLayout many_layout(const ManyGroup &g, const phc_opts &o, phc::TrackLaunch &L)
+{
+    ManyLayout y;
+    y.m = (int)g.descs.size();
+    L = phc::TrackLaunch{};
+    L.n_paths = g.prefix.back();
+    L.o = o;
+    L.n_multi = y.m;
+    L.warp_table_bytes = g.wtb;
+    const bool tail = o.tail_drain > 0.0 && phc::tail_multi_supported(g.tz);
+    y.lanes = tail ? phc::multi_lanes(L, g.n, o.block_threads, o.max_blocks) : 0;
+    if (y.lanes < 0) y.lanes = 0;
+    y.q_off = (size_t)y.m * sizeof(phc::SysDesc);
+    y.pre_off = y.q_off + (size_t)y.m * sizeof(unsigned long long);
+    const size_t head = y.pre_off + (size_t)(y.m + 1) * sizeof(int64_t);
+    y.hoff = (head + 255) & ~(size_t)255;
+    y.bytes = y.hoff + 8 * sizeof(unsigned long long) + (size_t)y.lanes * sizeof(phc::Handoff);
+    return y;
+}
+
+// Points L at a group's device block.
+static void many_bind(phc::TrackLaunch &L, const ManyLayout &y, char *b, const phc_opts &o)
+{
+    L.multi = reinterpret_cast<const phc::SysDesc *>(b);
+    L.multi_q = reinterpret_cast<unsigned long long *>(b + y.q_off);
+    L.multi_prefix = reinterpret_cast<const int64_t *>(b + y.pre_off);
+    unsigned long long *c = reinterpret_cast<unsigned long long *>(b + y.hoff);
+    if (y.lanes > 0) {
+        L.handoff_n = c;
+        L.idle_n = c + 1;
+        L.tail_q = c + 2;
+        L.tail_units = c + 3;
+        L.multi_claimed = c + 4;
+        L.handoff = reinterpret_cast<phc::Handoff *>(c + 8);
+        L.drain_frac = o.tail_drain;
+    }
+}
+
+// Stream-ordered work of one group on stream s: counters cleared, the
+// multi-system tracker and its tail kernel.  Allocates nothing.
+static int many_launch(const phc::TrackLaunch &L, const ManyLayout &y, const ManyGroup &g, char *b, const phc_opts &o,
+                       cudaStream_t s)
+{
+    CU(cudaMemsetAsync(b + y.q_off, 0, (size_t)y.m * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(b + y.hoff, 0, 8 * sizeof(unsigned long long), s));
+    cudaError_t e = phc::launch_multi(L, g.n, o.block_threads, o.max_blocks, s);
+    if (e == cudaSuccess && y.lanes > 0) e = phc::launch_tail_multi(L, g.n, g.tz, o.max_blocks, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "multi-system kernel launch (n = %d): %s", g.n, cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+// Helper streams for the groups of a call on caller stream st: each caller
+// stream has helpers of its own, created with its priority, so calls on
+// different streams neither wait for each other's launches nor lose their
+// priority.
+static int helper_streams(cudaStream_t st, size_t count, std::vector<cudaStream_t> &out)
+{
+    static std::mutex pool_mutex;
+    static std::map<cudaStream_t, std::vector<cudaStream_t>> pools;  // nodes stay where they are
+    int prio = 0;
+    CU(cudaStreamGetPriority(st, &prio));
+    std::lock_guard<std::mutex> lock(pool_mutex);
+    std::vector<cudaStream_t> &pool = pools[st];
+    while (pool.size() < count) {
+        cudaStream_t ns;
+        CU(cudaStreamCreateWithPriority(&ns, cudaStreamNonBlocking, prio));
+        pool.push_back(ns);
+    }
+    out.assign(pool.begin(), pool.begin() + count);
+    return PHC_OK;
+}
+
+extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
+                              int8_t *const *cls_out, phc_path_stats *const *stats_out, void *stream)
+{
+    if (n_h < 0 || (n_h > 0 && (!hs || !x_out || !cls_out))) return fail(PHC_EINVAL, "NULL argument");
+    if (n_h == 0) return PHC_OK;
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    std::vector<ManyGroup> groups;
+    rc = many_groups(hs, n_h, o, x_out, cls_out, stats_out,
+                     [&](int i, int64_t paths, phc_path_stats **sp) -> int {
+                         const int r = ensure_stats(hs[i], paths, static_cast<cudaStream_t>(stream));
+                         *sp = hs[i]->d_stats;
+                         return r;
+                     },
+                     groups);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the launches of different sizes run side by side on helper streams
+    // that fork from and join back into the caller's stream
+    std::vector<cudaStream_t> helpers;
+    rc = helper_streams(st, groups.size(), helpers);
+    if (rc) return rc;
+    cudaEvent_t fork_ev = nullptr;
+    CU(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    CU(cudaEventRecord(fork_ev, st));
+    std::vector<cudaEvent_t> joins;
+    for (size_t gi = 0; gi < groups.size(); gi++) {
+        const ManyGroup &g = groups[gi];
+        cudaStream_t hs_st = helpers[gi];
         CU(cudaStreamWaitEvent(hs_st, fork_ev, 0));
-        const int m = (int)descs.size();
-        phc::TrackLaunch L{};
-        L.n_paths = prefix.back();
-        L.o = o;
-        L.n_multi = m;
-        L.warp_table_bytes = wtb;
-        // tail hand-off (double precision): buffer for one record per lane
-        const bool tail =
-            o.tail_drain > 0.0 && phc::tail_multi_supported(tz);
-        const int64_t lanes = tail ? phc::multi_lanes(L, n, o.block_threads, o.max_blocks) : 0;
-        const size_t head = m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long) + (m + 1) * sizeof(int64_t);
-        const size_t hoff = (head + 255) & ~(size_t)255;
-        const size_t bytes = hoff + (lanes > 0 ? 8 * sizeof(unsigned long long) + lanes * sizeof(phc::Handoff) : 0);
+        phc::TrackLaunch L;
+        const ManyLayout y = many_layout(g, o, L);
         void *blob = nullptr;
-        CU(cudaMallocAsync(&blob, bytes, hs_st));
+        CU(cudaMallocAsync(&blob, y.bytes, hs_st));
         char *b = static_cast<char *>(blob);
-        phc::SysDesc *d_desc = reinterpret_cast<phc::SysDesc *>(b);
-        unsigned long long *d_q = reinterpret_cast<unsigned long long *>(b + m * sizeof(phc::SysDesc));
-        int64_t *d_pre = reinterpret_cast<int64_t *>(b + m * sizeof(phc::SysDesc) + m * sizeof(unsigned long long));
-        CU(cudaMemcpyAsync(d_desc, descs.data(), m * sizeof(phc::SysDesc), cudaMemcpyHostToDevice, hs_st));
-        CU(cudaMemsetAsync(d_q, 0, m * sizeof(unsigned long long), hs_st));
-        CU(cudaMemcpyAsync(d_pre, prefix.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, hs_st));
-        L.multi = d_desc;
-        L.multi_q = d_q;
-        L.multi_prefix = d_pre;
-        if (lanes > 0) {
-            unsigned long long *c = reinterpret_cast<unsigned long long *>(b + hoff);
-            CU(cudaMemsetAsync(c, 0, 8 * sizeof(unsigned long long), hs_st));
-            L.handoff_n = c;
-            L.idle_n = c + 1;
-            L.tail_q = c + 2;
-            L.tail_units = c + 3;
-            L.multi_claimed = c + 4;
-            L.handoff = reinterpret_cast<phc::Handoff *>(c + 8);
-            L.drain_frac = o.tail_drain;
-        }
+        CU(cudaMemcpyAsync(b, g.descs.data(), (size_t)y.m * sizeof(phc::SysDesc), cudaMemcpyHostToDevice, hs_st));
+        CU(cudaMemcpyAsync(b + y.pre_off, g.prefix.data(), (size_t)(y.m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           hs_st));
+        many_bind(L, y, b, o);
         // the host vectors must outlive the copies from pageable memory
         CU(cudaStreamSynchronize(hs_st));
-        cudaError_t e = phc::launch_multi(L, n, o.block_threads, o.max_blocks, hs_st);
-        if (e == cudaSuccess && lanes > 0) e = phc::launch_tail_multi(L, n, tz, o.max_blocks, hs_st);
+        rc = many_launch(L, y, g, b, o, hs_st);
         cudaFreeAsync(blob, hs_st);
-        if (e != cudaSuccess) return fail(PHC_ECUDA, "multi-system kernel launch (n = %d): %s", n,
-                                          cudaGetErrorString(e));
+        if (rc) return rc;
         cudaEvent_t j;
         CU(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
         CU(cudaEventRecord(j, hs_st));
@@ -848,16 +916,121 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
     return PHC_OK;
 }
 
-static int ensure_stats2(phc_homotopy *h, int64_t n)
+// ------------------------------------------------------------------ multi-system plans
+
+struct phc_many_plan {
+    phc_opts o{};
+    std::vector<ManyGroup> groups;
+    std::vector<ManyLayout> layouts;
+    std::vector<phc::TrackLaunch> launches;
+    std::vector<void *> blobs;
+    std::vector<phc_path_stats *> own_stats;  // records for handles the caller gave none
+    std::vector<cudaStream_t> helpers;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+};
+
+extern "C" void phc_many_plan_destroy(phc_many_plan *p)
 {
-    if (h->stats2_cap >= n) return PHC_OK;
-    if (h->d_stats2) cudaFree(h->d_stats2);
-    h->d_stats2 = nullptr;
-    h->stats2_cap = 0;
-    if (cudaMalloc(&h->d_stats2, n * sizeof(phc_path_stats)) != cudaSuccess)
-        return fail(PHC_ENOMEM, "cudaMalloc of %lld path records", (long long)n);
-    h->stats2_cap = n;
+    if (!p) return;
+    for (void *b : p->blobs)
+        if (b) cudaFree(b);
+    for (phc_path_stats *s : p->own_stats)
+        if (s) cudaFree(s);
+    for (cudaStream_t s : p->helpers)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : p->joins)
+        if (e) cudaEventDestroy(e);
+    if (p->fork) cudaEventDestroy(p->fork);
+    delete p;
+}
+
+extern "C" int phc_many_plan_create(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
+                                    int8_t *const *cls_out, phc_path_stats *const *stats_out, void *stream,
+                                    phc_many_plan **out)
+{
+    if (!out) return fail(PHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_h < 1 || !hs || !x_out || !cls_out) return fail(PHC_EINVAL, "NULL argument or n_h < 1");
+    phc_many_plan *p = new (std::nothrow) phc_many_plan();
+    if (!p) return fail(PHC_ENOMEM, "host allocation");
+    if (opts) p->o = *opts; else phc_default_opts(&p->o);
+    int rc = check_opts(p->o);
+    if (!rc)
+        rc = many_groups(hs, n_h, p->o, x_out, cls_out, stats_out,
+                         [&](int i, int64_t paths, phc_path_stats **sp) -> int {
+                             (void)i;
+                             *sp = nullptr;
+                             if (cudaMalloc(sp, paths * sizeof(phc_path_stats)) != cudaSuccess)
+                                 return fail(PHC_ENOMEM, "cudaMalloc of %lld path records", (long long)paths);
+                             p->own_stats.push_back(*sp);
+                             return PHC_OK;
+                         },
+                         p->groups);
+    int prio = 0;
+    if (!rc && cudaStreamGetPriority(static_cast<cudaStream_t>(stream), &prio) != cudaSuccess)
+        rc = fail(PHC_ECUDA, "cudaStreamGetPriority");
+    if (!rc && cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(PHC_ECUDA, "cudaEventCreate");
+    for (size_t gi = 0; !rc && gi < p->groups.size(); gi++) {
+        const ManyGroup &g = p->groups[gi];
+        phc::TrackLaunch L;
+        const ManyLayout y = many_layout(g, p->o, L);
+        void *blob = nullptr;
+        if (cudaMalloc(&blob, y.bytes) != cudaSuccess) {
+            rc = fail(PHC_ENOMEM, "cudaMalloc of %zu bytes for the multi-system plan", y.bytes);
+            break;
+        }
+        p->blobs.push_back(blob);
+        char *b = static_cast<char *>(blob);
+        if (cudaMemcpy(b, g.descs.data(), (size_t)y.m * sizeof(phc::SysDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b + y.pre_off, g.prefix.data(), (size_t)(y.m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            rc = fail(PHC_ECUDA, "upload of the multi-system descriptors");
+            break;
+        }
+        many_bind(L, y, b, p->o);
+        p->layouts.push_back(y);
+        p->launches.push_back(L);
+        cudaStream_t hs_st = nullptr;
+        cudaEvent_t j = nullptr;
+        if (cudaStreamCreateWithPriority(&hs_st, cudaStreamNonBlocking, prio) != cudaSuccess ||
+            cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) {
+            if (hs_st) cudaStreamDestroy(hs_st);
+            rc = fail(PHC_ECUDA, "helper stream or event of the multi-system plan");
+            break;
+        }
+        p->helpers.push_back(hs_st);
+        p->joins.push_back(j);
+    }
+    if (rc) {
+        phc_many_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
     return PHC_OK;
+}
+
+extern "C" int phc_many_plan_run(phc_many_plan *p, void *stream)
+{
+    if (!p) return fail(PHC_EINVAL, "NULL plan");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CU(cudaEventRecord(p->fork, st));
+    for (size_t gi = 0; gi < p->groups.size(); gi++) {
+        cudaStream_t hs_st = p->helpers[gi];
+        CU(cudaStreamWaitEvent(hs_st, p->fork, 0));
+        const int rc = many_launch(p->launches[gi], p->layouts[gi], p->groups[gi], static_cast<char *>(p->blobs[gi]),
+                                   p->o, hs_st);
+        if (rc) return rc;
+        CU(cudaEventRecord(p->joins[gi], hs_st));
+        CU(cudaStreamWaitEvent(st, p->joins[gi], 0));
+    }
+    return PHC_OK;
+}
+
+static int ensure_stats2(phc_homotopy *h, int64_t n, cudaStream_t s)
+{
+    return grow(reinterpret_cast<void **>(&h->d_stats2), &h->stats2_cap, n, sizeof(phc_path_stats), s, "path records");
 }
 
 extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t n, const phc_opts *opts,
@@ -881,12 +1054,12 @@ extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t
     if (rc) return rc;
     phc_path_stats *st = stats_top, *st2 = stats_next;
     if (!st) {
-        rc = ensure_stats(h, n);
+        rc = ensure_stats(h, n, static_cast<cudaStream_t>(stream));
         if (rc) return rc;
         st = h->d_stats;
     }
     if (!st2) {
-        rc = ensure_stats2(h, n);
+        rc = ensure_stats2(h, n, static_cast<cudaStream_t>(stream));
         if (rc) return rc;
         st2 = h->d_stats2;
     }
@@ -918,7 +1091,7 @@ extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t
     if (tail) {
         const int64_t lanes = phc::pipe_lanes(L, o.block_threads, o.max_blocks);
         if (lanes < 1) return fail(PHC_EUNSUPPORTED, "no launch configuration for %d unknowns", L.tab.n);
-        rc = ensure_handoff(h, lanes);
+        rc = ensure_handoff(h, lanes, static_cast<cudaStream_t>(stream));
         if (rc) return rc;
         CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));
         L.handoff = h->d_handoff;
@@ -956,11 +1129,11 @@ extern "C" int phc_cascade_from(const phc_homotopy *hc, int k, const phc_cd *x_p
     if (rc) return rc;
     rc = ensure_cascade(h);
     if (rc) return rc;
-    rc = ensure_xfull(h, (int64_t)h->n * n);
+    rc = ensure_xfull(h, (int64_t)h->n * n, static_cast<cudaStream_t>(stream));
     if (rc) return rc;
     phc_path_stats *st = stats_out;
     if (!st) {
-        rc = ensure_stats(h, n);
+        rc = ensure_stats(h, n, static_cast<cudaStream_t>(stream));
         if (rc) return rc;
         st = h->d_stats;
     }

@@ -9,19 +9,34 @@ and their work overlaps on the device:
   batches are on the GPU: one phc_track_many call (one launch per number of
   unknowns, every warp on one request's system at a time), so small
   requests share launches that fill the GPU;
-* an embedded request runs on a stream of its own as soon as it arrives:
-  the top stage of E_D, then one phc_cascade_from per cascade stage, each
-  fed directly by the previous stage's device outputs (Section 3.1: regular
-  endpoints with a nonzero slack start the next stage); with pipelined=True
-  the top stage and the first cascade stage share one launch
-  (phc_track_pipeline).  It gets a grid cap (big_share of the SMs) so that
-  batches of small requests keep SMs.
+* an embedded request is cut into chunks of its top-stage paths;
+  every chunk runs the top stage of E_D, then one phc_cascade_from per
+  cascade stage, each fed directly by the previous stage's device outputs
+  (Section 3.1: regular endpoints with a nonzero slack start the next
+  stage), so a chunk's paths flow through every stage while later chunks
+  are still waiting; with pipelined=True the top stage and the first
+  cascade stage share one launch (phc_track_pipeline).
+
+Small requests come first.  Batches run on high-priority streams, chunks on
+low-priority ones (big_streams of them, each with handles of its own, since
+calls on one handle must not overlap), and the server launches a chunk only
+when a chunk stream is free: while small requests wait or run (or did within
+idle_after seconds) one chunk at a time of big_chunk paths under a grid cap
+of big_share_busy of the SMs, otherwise up to one chunk per chunk stream of
+big_chunk_idle paths under big_share.  A
+persistent launch keeps its SMs until its paths are done and the FP64 pipe
+of an SM is shared by every warp resident on it, so it is this cap -- not
+the stream priority alone -- that keeps most SMs for the small requests
+while the large one advances on the rest; every chunk ends within about the
+time of its longest path, so the cap follows the load.  Every path gives the
+same result in any chunk and under any grid (a path's arithmetic does not
+depend on the launch), so no result depends on the schedule.
 
 Every unit of work ends with an event; the loop polls the events, copies the
 classes and endpoints of finished work to the host, retires it (freeing its
-memory budget) and launches waiting work.  Nothing waits on the
-host between stages.  Latency is the time from a request's arrival to the
-moment the server sees its results on the host.
+memory budget) and launches waiting work.  Nothing waits on the host
+between stages.  Latency is the time from a request's arrival to the moment
+the server sees its results on the host.
 
 All tracking runs in libphc.so; this module only schedules.
 """
@@ -77,24 +92,51 @@ def _bytes_for(n_var: int, n_paths: int) -> int:
     return n_paths * (16 * n_var + 1 + 1 + STATS_DTYPE.itemsize)
 
 
+class _Embedded:
+    """An admitted embedded request: its systems E_D, ..., E_1 (host
+    lists), per chunk stream its handles, and its chunks so far."""
+
+    def __init__(self, req, systems, handles, n_paths, admitted, nbytes):
+        self.req = req
+        self.systems = systems
+        self.handles = handles        # [stream][stage] phc_homotopy handles
+        self.n_paths = n_paths
+        self.admitted = admitted
+        self.nbytes = nbytes
+        self.next_first = 0
+        self.chunks = []              # (first, per stage (x, cls) device outputs, event)
+        self.pending = 0              # chunks launched and not yet finished
+
+    @property
+    def launched_all(self) -> bool:
+        return self.next_first >= self.n_paths
+
+
 class Server:
-    def __init__(self, slots: int = 4, mem_bytes: int = 16 << 30, big_share: float = 0.6, opts=None,
-                 device="cuda", max_inflight: int = 4, batch_paths: int = 60_000, pipelined: bool = False):
+    def __init__(self, slots: int = 4, mem_bytes: int = 16 << 30, big_share: float = 1.0, opts=None,
+                 device="cuda", max_inflight: int = 4, batch_paths: int = 60_000, pipelined: bool = False,
+                 big_chunk: int = 2048, big_streams: int = 3, big_share_busy: float = 0.3,
+                 big_chunk_idle: int = 16384, idle_after: float = 0.5):
         import torch
         self.torch = torch
         self.device = torch.device(device)
-        self.slots = slots                  # streams for embedded requests
+        self.slots = slots                  # embedded requests admitted at once
         self.max_inflight = max_inflight    # batches of plain requests on the GPU at once
         self.batch_paths = batch_paths      # paths per batch (bounds a batch's duration)
         self.mem_bytes = mem_bytes
-        self.big_share = big_share
+        self.big_share = big_share          # grid cap of a chunk when no small request waits or runs
+        self.big_share_busy = big_share_busy  # ... and while small requests wait or run
+        self.big_chunk = big_chunk          # top-stage paths per chunk while small requests wait or run
+        self.big_chunk_idle = big_chunk_idle  # ... and when none do
+        self.idle_after = idle_after        # seconds without small requests before chunks grow
         # embedded requests: the top stage and the first cascade stage in one
         # pipelined launch, or (default) one launch each, which lets both use
         # the tail hand-off
         self.pipelined = pipelined
         self.opts = opts if opts is not None else phc_default_opts()
-        self.batch_streams = [torch.cuda.Stream(device=self.device) for _ in range(max_inflight)]
-        self.big_streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        # lower number = higher priority: small requests first, chunks of large ones after
+        self.batch_streams = [torch.cuda.Stream(device=self.device, priority=-100) for _ in range(max_inflight)]
+        self.chunk_streams = [torch.cuda.Stream(device=self.device, priority=0) for _ in range(big_streams)]
         self.n_sms = torch.cuda.get_device_properties(self.device).multi_processor_count
         self._keep = []  # handles of finished work, destroyed after the run
 
@@ -132,47 +174,67 @@ class Server:
             ev.record(stream)
         return hs, [[(o[0], o[1])] for o in outs], ev, [phc_num_paths(h) for h in hs]
 
-    def _launch_embedded(self, req: Request, stream):
+    def _admit_embedded(self, req: Request, admitted: float, nbytes: int) -> _Embedded:
+        """The systems E_D, ..., E_1 of the request and, per chunk stream,
+        handles of its own."""
+        D = req.top_dim
+        systems = [phc_embed(req.system, D, req.gammas, req.hyper)]
+        for k in range(D - 1, 0, -1):
+            systems.append(phc_embed(req.system, k, req.gammas[:, :k], req.hyper[:k]))
+        handles = [[phc_make_homotopy(E, req.gamma) for E in systems] for _ in self.chunk_streams]
+        return _Embedded(req, systems, handles, phc_num_paths(handles[0][0]), admitted, nbytes)
+
+    def _launch_chunk(self, e: _Embedded, si: int, cap: float, chunk: int):
+        """The next chunk of e on chunk stream si: the top stage, then every
+        cascade stage from the device outputs of the stage above."""
         torch = self.torch
         opts = self._opts()
-        handles, stages = [], []
+        if cap < 1.0:
+            opts.max_blocks = max(1, int(cap * self.n_sms))
+        D = e.req.top_dim
+        first = e.next_first
+        n = min(chunk, e.n_paths - first)
+        e.next_first += n
+        stream, hs = self.chunk_streams[si], e.handles[si]
+        N = hs[0].n
         with torch.cuda.stream(stream):
-            D = req.top_dim
-            E = phc_embed(req.system, D, req.gammas, req.hyper)
-            h = phc_make_homotopy(E, req.gamma)
-            handles.append(h)
-            P = phc_num_paths(h)
-            opts.max_blocks = max(1, int(self.big_share * self.n_sms))
-            N = h.n
-
             def buf(n_var):
-                return (torch.empty((n_var, P), dtype=torch.complex128, device=self.device),
-                        torch.empty(P, dtype=torch.int8, device=self.device),
-                        torch.empty((P, STATS_DTYPE.itemsize), dtype=torch.uint8, device=self.device),
-                        torch.empty(P, dtype=torch.uint8, device=self.device))
+                return (torch.empty((n_var, n), dtype=torch.complex128, device=self.device),
+                        torch.empty(n, dtype=torch.int8, device=self.device),
+                        torch.empty((n, STATS_DTYPE.itemsize), dtype=torch.uint8, device=self.device),
+                        torch.empty(n, dtype=torch.uint8, device=self.device))
 
             xt, ct, stt, _ = buf(N)
             xn, cn, stn, szn = buf(N - 1)
             if self.pipelined:
-                phc_track_pipeline(h, D, 0, P, opts, xt, ct, stt, xn, cn, szn, stn, stream)
+                phc_track_pipeline(hs[0], D, first, n, opts, xt, ct, stt, xn, cn, szn, stn, stream)
             else:
                 # top stage, then the first cascade stage from its device outputs
                 # (each launch with its tail hand-off)
-                phc_track_paths(h, 0, P, opts, xt, ct, stt, stream)
-                phc_cascade_from(h, D, xt, ct, None, P, opts, xn, cn, szn, stn, stream)
-            stages += [(xt, ct), (xn, cn)]
+                phc_track_paths(hs[0], first, n, opts, xt, ct, stt, stream)
+                phc_cascade_from(hs[0], D, xt, ct, None, n, opts, xn, cn, szn, stn, stream)
+            stages = [(xt, ct), (xn, cn)]
             prev = (xn, cn, szn)
-            for k in range(D - 1, 0, -1):
-                Ek = phc_embed(req.system, k, req.gammas[:, :k], req.hyper[:k])
-                hk = phc_make_homotopy(Ek, req.gamma)
-                handles.append(hk)
+            for j, k in enumerate(range(D - 1, 0, -1)):
+                hk = hs[j + 1]
                 xo, co, sto, szo = buf(hk.n - 1)
-                phc_cascade_from(hk, k, prev[0], prev[1], prev[2], P, opts, xo, co, szo, sto, stream)
+                phc_cascade_from(hk, k, prev[0], prev[1], prev[2], n, opts, xo, co, szo, sto, stream)
                 stages.append((xo, co))
                 prev = (xo, co, szo)
             ev = torch.cuda.Event()
             ev.record(stream)
-        return handles, stages, ev, P
+        e.chunks.append((first, stages, ev))
+        e.pending += 1
+        return ev
+
+    @staticmethod
+    def _download_chunks(e: _Embedded):
+        """Host copies of a finished embedded request: per stage the chunks
+        concatenated in path order."""
+        chunks = sorted(e.chunks, key=lambda c: c[0])
+        n_stages = len(chunks[0][1])
+        return [(np.concatenate([c[1][s][0].cpu().numpy() for c in chunks], axis=1),
+                 np.concatenate([c[1][s][1].cpu().numpy() for c in chunks])) for s in range(n_stages)]
 
     def run(self, requests, realtime: bool = True, poll: float = 2e-4):
         """Serve `requests` (arrival times relative to the start); returns
@@ -181,44 +243,51 @@ class Server:
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         waiting = []                                   # arrived plain requests
         free_batch = list(range(self.max_inflight))
-        free_big = list(range(self.slots))
+        free_chunk = list(range(len(self.chunk_streams)))
+        chunk_busy = {}                                # chunk stream -> (embedded request, event)
+        bigs = []                                      # admitted embedded requests
         mem_used = 0
-        active = []   # (kind, slot, reqs, bytes, admitted, handles, host, event, n_paths)
+        active = []   # batches: (slot, reqs, bytes, admitted, handles, host, event, n_paths)
         results = {}
+        last_small = -1e9                              # last time a small request waited or ran
         t0 = time.perf_counter()
-        while pending or waiting or active:
+        while pending or waiting or active or bigs:
             now = time.perf_counter() - t0
             progressed = False
             for a in list(active):
-                kind, slot, reqs, nbytes, admitted, handles, host, ev, npaths = a
+                slot, reqs, nbytes, admitted, handles, host, ev, npaths = a
                 if not ev.query():
                     continue
-                if kind == "batch":
-                    for r, dev_stages, P in zip(reqs, host, npaths):
-                        results[r.rid] = Result(r.rid, r.arrival, admitted, 0.0, P, self._download(dev_stages))
-                    free_batch.append(slot)
-                else:
-                    r = reqs[0]
-                    results[r.rid] = Result(r.rid, r.arrival, admitted, 0.0, npaths, self._download(host))
-                    free_big.append(slot)
                 fin = time.perf_counter() - t0
-                for r in reqs:
-                    results[r.rid].finished = fin
+                for r, dev_stages, P in zip(reqs, host, npaths):
+                    results[r.rid] = Result(r.rid, r.arrival, admitted, fin, P, self._download(dev_stages))
+                free_batch.append(slot)
                 self._keep.extend(handles)
                 active.remove(a)
                 mem_used -= nbytes
                 progressed = True
+            for si, (e, ev) in list(chunk_busy.items()):
+                if not ev.query():
+                    continue
+                del chunk_busy[si]
+                free_chunk.append(si)
+                e.pending -= 1
+                progressed = True
+                if e.launched_all and e.pending == 0:
+                    fin = time.perf_counter() - t0
+                    r = e.req
+                    results[r.rid] = Result(r.rid, r.arrival, e.admitted, fin, e.n_paths, self._download_chunks(e))
+                    self._keep.extend(h for hs in e.handles for h in hs)
+                    bigs.remove(e)
+                    mem_used -= e.nbytes
             while pending and (pending[0].arrival <= now or not realtime):
                 req = pending[0]
                 if req.top_dim > 0:
                     _, nbytes = self.plan_paths(req)
-                    if not free_big or (active and mem_used + nbytes > self.mem_bytes):
+                    if len(bigs) >= self.slots or ((active or bigs) and mem_used + nbytes > self.mem_bytes):
                         break
                     pending.pop(0)
-                    slot = free_big.pop(0)
-                    admitted = time.perf_counter() - t0
-                    handles, host, ev, P = self._launch_embedded(req, self.big_streams[slot])
-                    active.append(("big", slot, [req], nbytes, admitted, handles, host, ev, P))
+                    bigs.append(self._admit_embedded(req, time.perf_counter() - t0, nbytes))
                     mem_used += nbytes
                 else:
                     waiting.append(pending.pop(0))
@@ -235,9 +304,21 @@ class Server:
                 slot = free_batch.pop(0)
                 admitted = time.perf_counter() - t0
                 hs, host, ev, npaths = self._launch_batch(batch, self.batch_streams[slot])
-                active.append(("batch", slot, batch, nbytes, admitted, hs, host, ev, npaths))
+                active.append((slot, batch, nbytes, admitted, hs, host, ev, npaths))
                 mem_used += nbytes
                 progressed = True
+            # chunks of embedded requests (first admitted first) on free chunk streams
+            if waiting or active:
+                last_small = now
+            busy = now - last_small < self.idle_after
+            for e in bigs:
+                # while small requests are served one chunk at a time runs (the cap
+                # bounds the SMs of all chunks together), otherwise one per chunk stream
+                while free_chunk and not e.launched_all and not (busy and chunk_busy):
+                    si = free_chunk.pop(0)
+                    chunk_busy[si] = (e, self._launch_chunk(e, si, self.big_share_busy if busy else self.big_share,
+                                                            self.big_chunk if busy else self.big_chunk_idle))
+                    progressed = True
             if not progressed:
                 time.sleep(poll)
         torch.cuda.synchronize(self.device)

@@ -1,0 +1,121 @@
+"""Full-size parity of the two largest benchmark workloads with the oracle.
+
+The oracle's results were computed once, un-timed, by
+tests/golden/make_fullsize_expected.py (which calls only the oracle and the
+seeded generators) and stored in tests/golden/fullsize_expected.npz: per
+system (or cascade stage) the class counts and, for every regular endpoint,
+its value under a fixed seeded linear form l(x) = sum_j r_j x_j and its
+norm.  Here the GPU tracks every path of the same workloads, and
+
+* the class counts equal the oracle's exactly, system by system (stage by
+  stage);
+* the regular endpoints match the oracle's one to one: l-values within
+  1e-10 (1 + ||x||) sum_j |r_j| (l is one random projection, so a root that
+  moved moves its value, and distinct roots keep distinct values);
+* every regular endpoint is a root of its system (independent evaluation)
+  and the regular endpoints of a system are pairwise distinct.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import paper_1804_03807_gb300 as P
+from workloads import configs
+from tests._checks import relative_residual
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-10
+EXPECTED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_expected.npz")
+
+
+def _expected():
+    if not os.path.exists(EXPECTED):
+        pytest.fail("tests/golden/fullsize_expected.npz is missing: run tests/golden/make_fullsize_expected.py")
+    return np.load(EXPECTED)
+
+
+def match_projections(xg: np.ndarray, r: np.ndarray, lo: np.ndarray, no: np.ndarray):
+    """Largest relative mismatch of a one-to-one matching of the GPU regular
+    endpoints xg [P, n] with the oracle's l-values lo (norms no); inf when the
+    sizes differ or two GPU endpoints match the same oracle value."""
+    if len(xg) != len(lo):
+        return np.inf
+    if len(xg) == 0:
+        return 0.0
+    lg = xg @ r[:xg.shape[1]]
+    ng = np.max(np.maximum(np.abs(xg.real), np.abs(xg.imag)), axis=1)
+    tree = cKDTree(np.stack([lo.real, lo.imag], axis=1))
+    d, idx = tree.query(np.stack([lg.real, lg.imag], axis=1), k=1)
+    if len(np.unique(idx)) != len(idx):
+        return np.inf
+    scale = np.sum(np.abs(r[:xg.shape[1]])) * (1.0 + np.maximum(ng, no[idx]))
+    return float(np.max(d / scale))
+
+
+def _check_system(label, sys, xg, cg, counts_o, lo, no, r, report):
+    cnt = np.bincount(cg[cg >= 0].astype(int), minlength=4)
+    rel = match_projections(xg[cg == 0], r, lo, no)
+    ok = np.array_equal(cnt, counts_o) and rel <= RTOL
+    if not ok:
+        report.append(f"{label}: gpu {cnt.tolist()} oracle {counts_o.tolist()} regular mismatch {rel:.3g}")
+    reg = xg[cg == 0]
+    if len(reg):
+        assert relative_residual(sys, reg).max() <= 1e-12, label
+    return ok
+
+
+def test_sparse_batch_full_size_exact():
+    """The batching workload: 256 random sparse systems (4,322,140 paths) in
+    one phc_track_many call; every system against the oracle."""
+    exp = _expected()
+    r = exp["r"]
+    w = configs.sparse_batch()
+    hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
+    rs = P.track_many(hs)
+    report, n_ok = [], 0
+    off = exp["sparse_off"]
+    for i, (s, res) in enumerate(zip(w.systems, rs)):
+        xg = res.x.cpu().numpy().T
+        cg = res.cls.cpu().numpy()
+        sl = slice(int(off[i]), int(off[i + 1]))
+        n_ok += _check_system(f"system {i} (n={s.n_var})", s, xg, cg, exp["sparse_counts"][i], exp["sparse_l"][sl],
+                              exp["sparse_norm"][sl], r, report)
+    print(f"{n_ok} of {len(hs)} systems equal")
+    for line in report:
+        print(line)
+    assert not report, f"{len(report)} systems differ"
+
+
+def test_cyclic9_d2_all_stages_full_size_exact():
+    """The large request of the serving workload: cyclic 9 embedded for top
+    dimension 2 (362,880 paths), its cascade stage from E_2 and the stage
+    from E_1, chained on the device as the server runs them; each stage's
+    class counts and regular endpoints against the oracle's stage-by-stage
+    flow."""
+    exp = _expected()
+    r = exp["r"]
+    w = configs.serving(n_requests=1, big=(9, 2))
+    b = w.extra["big"]
+    base, g, hy, gamma = b["system"], b["gammas"], b["hyper"], b["gamma"]
+    E2 = P.phc_embed(base, 2, g, hy)
+    E1 = P.phc_embed(base, 1, g[:, :1], hy[:1])
+    h2 = P.phc_make_homotopy(E2, gamma)
+    h1 = P.phc_make_homotopy(E1, gamma)
+    top = P.track(h2)
+    s2 = P.cascade_from(h2, 2, top)
+    s1 = P.cascade_from(h1, 1, s2)
+    systems = [E2, E1, base]
+    off = exp["c9_off"]
+    report = []
+    for k, (res, sys) in enumerate(zip([top, s2, s1], systems)):
+        xg = res.x.cpu().numpy().T
+        cg = res.cls.cpu().numpy()
+        if k > 0:
+            assert int((cg >= 0).sum()) == int(exp["c9_starts"][k - 1]), f"stage {k}: number of starts"
+        sl = slice(int(off[k]), int(off[k + 1]))
+        _check_system(f"stage {k}", sys, xg, cg, exp["c9_counts"][k], exp["c9_l"][sl], exp["c9_norm"][sl], r, report)
+    for line in report:
+        print(line)
+    assert not report
