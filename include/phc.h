@@ -128,6 +128,11 @@ typedef struct {
                                 the arithmetic is the same, operation for operation, so the
                                 results do not change.  0 = never. */
     int32_t tail_threads;    /* threads per path in that kernel: 8 (N <= 8), 16 or 32; 0 = 32 */
+    int32_t compact;         /* phc_track_paths, phc_track_from and the cascade stages, N >= 4: once
+                                no path is left to claim, every 8 units each block moves its running
+                                paths to its lowest threads, so that warps without a path stop
+                                issuing (the arithmetic of a path does not change).  1 (default) on,
+                                0 off */
 } phc_opts;
 
 /* Per-path statistics (device array of these, optional). */
@@ -424,7 +429,7 @@ int phc_refine_endpoints(const phc_homotopy *h, phc_cd *x_hi_io, phc_cd *x_lo_ou
  * The tail hand-off (opts.tail_drain) holds at most PHC_NOALLOC_MAX_HANDOFF
  * paths, so on launches of more threads it starts once no more than that
  * many threads still hold a path (a later start than tail_drain alone, the
- * same results).  The call resets the handle's hand-off counters:
+ * same results), and opts.compact is ignored (no compaction).  The call resets the handle's hand-off counters:
  * phc_tail_paths reports 0 after it. */
 int phc_track_paths_noalloc(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts,
                             phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);

@@ -27,8 +27,9 @@
 //  * The tail hand-off (opts.tail_drain) keeps at most
 //    PHC_NOALLOC_MAX_HANDOFF paths: it starts once no more than that many
 //    of the tracker's threads still hold a path (later than tail_drain alone
-//    would start it on launches of more threads).  Results are the same
-//    either way; only the time changes.
+//    would start it on launches of more threads), and the tracker runs
+//    without the compaction of running paths (opts.compact is ignored).
+//    Results are the same either way; only the time changes.
 #include <mutex>
 
 #include "phc_internal.h"
@@ -123,6 +124,10 @@ extern "C" int phc_track_paths_noalloc(phc_homotopy *h, int64_t first, int64_t n
     L.stats = st;
     L.qhead = counter;
     L.o = o;
+    // no compaction here: the hand-off cap relies on idle lanes staying idle
+    // (running paths <= lanes - idle_n at every moment), which moving paths
+    // between lanes only keeps up to a transient
+    L.compact = 0;
     const bool tail = o.tail_drain > 0.0 && phc::tail_supported(L.tab);
     if (tail) {
         L.handoff = reinterpret_cast<phc::Handoff *>(b + NOALLOC_HEAD_BYTES);

@@ -74,6 +74,7 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->max_blocks = 0;
     o->tail_drain = 0.8;
     o->tail_threads = 0;
+    o->compact = 1;
     return PHC_OK;
 }
 
@@ -94,6 +95,7 @@ static int check_opts(const phc_opts &o)
     if (!(o.tail_drain >= 0.0 && o.tail_drain <= 1.0)) return fail(PHC_EINVAL, "tail_drain must be in [0, 1]");
     if (o.tail_threads != 0 && o.tail_threads != 8 && o.tail_threads != 16 && o.tail_threads != 32)
         return fail(PHC_EINVAL, "tail_threads must be 0, 8, 16 or 32");
+    if (o.compact != 0 && o.compact != 1) return fail(PHC_EINVAL, "compact must be 0 or 1");
     return PHC_OK;
 }
 
@@ -562,6 +564,7 @@ static int run_track(phc_homotopy *h, const DevTables &tab, int start_mode, cons
     L.n_paths = n;
     L.paths_per_system = h->paths_per_system > 0 ? h->paths_per_system : 1;
     L.starts_per_system = starts_per_system;
+    L.compact = o.compact;
     L.x_out = x_out;
     L.stats = stats;
     L.qhead = h->d_qhead;

@@ -78,7 +78,7 @@ __host__ __device__ inline size_t table_smem_bytes(const DevTables &t)
 // S (N slots); one slot is a complex double (single precision values use its
 // first half).  Without X a 160-thread block of the 7-unknown tracker grows
 // to 192 threads.
-inline size_t thread_smem_bytes(int n, bool scale = false, bool f32 = true)
+__host__ __device__ inline size_t thread_smem_bytes(int n, bool scale = false, bool f32 = true)
 {
     return (size_t)(n * n + 3 * n + (f32 ? n : 0) + (scale ? n : 0)) * sizeof(double2);
 }
@@ -149,6 +149,8 @@ struct TrackLaunch {
     unsigned long long *multi_claimed;  // multi-system: paths claimed over all systems
     unsigned long long drain_at;  // set by the launcher from drain_frac
     double drain_frac;            // fraction of idle lanes that starts the hand-off; 0: never
+    int compact;                  // single-homotopy mode: move running paths to the lowest lanes
+                                  // of their block once the queue is empty (N >= 4)
     int64_t handoff_cap;          // records the hand-off buffer holds; 0: one per lane.  With a
                                   // cap the hand-off starts no earlier than when at most this many
                                   // lanes still hold a path (each writes one record at most)

@@ -122,7 +122,7 @@ cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks
 {
     device_limits();
     if (L.n_paths <= 0) return cudaSuccess;
-    const size_t tb = table_smem_bytes(L.tab);
+    const size_t tb = table_smem_bytes(L.tab) + compact_smem_bytes(256);
     const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
     if (bt == 0) return cudaErrorInvalidConfiguration;
 #define PHC_CALL_TRACK(NN) launch_track_n<NN, MODE_SINGLE>(L, bt, max_blocks, L.n_paths, s)
@@ -133,7 +133,7 @@ cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks
 int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks)
 {
     device_limits();
-    const size_t tb = table_smem_bytes(L.tab);
+    const size_t tb = table_smem_bytes(L.tab) + compact_smem_bytes(256);
     const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
     if (bt == 0) return -1;
     switch (L.tab.n) {

@@ -569,6 +569,11 @@ __global__ void __launch_bounds__(256) classify_kernel(const ClassifyLaunch L, s
     }
 }
 
+// Units between two compaction checks of the single-homotopy tracker (a power of two).
+#define COMPACT_EVERY 8
+// Shared memory of the compaction bookkeeping: 64 ints and one int16 per thread.
+__host__ __device__ inline size_t compact_smem_bytes(int bt) { return 64 * sizeof(int) + (size_t)bt * sizeof(int16_t); }
+
 // Largest ||x|| at which a step may run in single precision (x^d stays far
 // from the float range for the degrees the library accepts).
 #define FP32_NORM_LIMIT 1.0e4
@@ -584,6 +589,8 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 {
     constexpr bool PIPE = MODE == MODE_PIPE;
     constexpr bool MULTI = MODE == MODE_MULTI;
+    // compaction needs 3N + 11 free slots per thread between units (R, P, J: N^2 + 2N)
+    constexpr bool COMPACT = MODE == MODE_SINGLE && N >= 4;
     extern __shared__ __align__(16) char smem[];
     SmTab tb{}, tb2{};
     if constexpr (!MULTI) {
@@ -660,7 +667,130 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 
     enum { ACT_NONE = 0, ACT_ACCEPT, ACT_REJECT, ACT_END };
 
+    // Compaction (single-homotopy mode).  Once the queue is empty, lanes go
+    // idle one by one while the paths left run on; an idle lane still costs
+    // its warp's FP64 instructions, so every COMPACT_EVERY units the block
+    // moves its running paths to its lowest lanes (their state goes through
+    // the owner's evaluation slots, which are free between units), and the
+    // warps left without a path stop issuing.  No path's arithmetic changes.
+    // Lanes then never leave the loop alone: the block leaves it together
+    // once every lane is idle and has found the queue empty.
+    const bool compact = COMPACT && L.compact;
+    bool done = false;  // (compaction) this lane is idle and counted in idle_n (it found the queue
+                        // empty or handed its path off); lanes the compaction empties are counted
+                        // too, and a counted lane that receives a path is taken off again, so
+                        // idle_n stays the number of idle lanes
+    int iter = 0;
+    int *cinfo = nullptr;  // [32] warp counts, [32] warp offsets
+    int16_t *cmap = nullptr;  // [bt] source lane of each destination
+    if constexpr (COMPACT) {
+        cinfo = reinterpret_cast<int *>(smem + table_bytes + table2_bytes + (size_t)bt * thread_smem_bytes(N, false, f32));
+        cmap = reinterpret_cast<int16_t *>(cinfo + 64);
+    }
+
     for (;;) {
+        if constexpr (COMPACT) {
+            if (compact && (iter++ & (COMPACT_EVERY - 1)) == 0) {
+                // every thread of the block reaches these barriers at the same iteration
+                if (__syncthreads_and(q < 0 && done)) break;
+                const int live = __syncthreads_count(q >= 0);
+                const bool warp_live = __any_sync(FULL, q >= 0);
+                const int wl = __syncthreads_count(lane == 0 && warp_live);
+                const int settled = __syncthreads_and(q >= 0 || done);
+                if (settled && (live + 31) / 32 < wl) {
+                    const unsigned bal = __ballot_sync(FULL, q >= 0);
+                    const int w = threadIdx.x >> 5, nw = bt >> 5;
+                    if (lane == 0) cinfo[w] = __popc(bal);
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        int o2 = 0;
+                        for (int k = 0; k < nw; k++) {
+                            cinfo[32 + k] = o2;
+                            o2 += cinfo[k];
+                        }
+                    }
+                    __syncthreads();
+                    // [R, P, (X), J] of a thread are contiguous slots, free between units
+                    double2 *base = A.R - threadIdx.x;
+                    if (q >= 0) {
+                        const int rank = cinfo[32 + w] + __popc(bal & ((1u << lane) - 1u));
+                        cmap[rank] = (int16_t)threadIdx.x;
+                        double2 *o = base + threadIdx.x;
+#pragma unroll
+                        for (int j = 0; j < N; j++) {
+                            o[j * bt] = x0[j];
+                            o[(N + j) * bt] = acc[j];
+                            o[(2 * N + j) * bt] = SL(A.xe, j);
+                        }
+                        double2 *sc = o + 3 * N * bt;
+                        sc[0] = make_double2(t, h);
+                        sc[bt] = make_double2(he, t1);
+                        sc[2 * bt] = make_double2(te, prev);
+                        sc[3 * bt] = make_double2(next_s, nx0);
+                        sc[4 * bt] = make_double2(r0, r1);
+                        sc[5 * bt] = make_double2(r2, r3);
+                        sc[6 * bt] = make_double2(r4, __longlong_as_double((long long)q));
+                        reinterpret_cast<int4 *>(sc)[7 * bt] = make_int4(sys, phase, it, streak);
+                        reinterpret_cast<int4 *>(sc)[8 * bt] = make_int4(steps, nck, since_ck, n_acc);
+                        reinterpret_cast<int4 *>(sc)[9 * bt] = make_int4(n_rej, n_newt, n_solve, n_f32);
+                        reinterpret_cast<int4 *>(sc)[10 * bt] = make_int4(use32 ? 1 : 0, fp32_off ? 1 : 0, 0, 0);
+                    }
+                    __syncthreads();
+                    if ((int)threadIdx.x < live) {
+                        const double2 *o = base + cmap[threadIdx.x];
+                        double2 xs[N];
+#pragma unroll
+                        for (int j = 0; j < N; j++) {
+                            x0[j] = o[j * bt];
+                            acc[j] = o[(N + j) * bt];
+                            xs[j] = o[(2 * N + j) * bt];
+                        }
+                        const double2 *sc = o + 3 * N * bt;
+                        double2 v = sc[0];
+                        t = v.x, h = v.y;
+                        v = sc[bt];
+                        he = v.x, t1 = v.y;
+                        v = sc[2 * bt];
+                        te = v.x, prev = v.y;
+                        v = sc[3 * bt];
+                        next_s = v.x, nx0 = v.y;
+                        v = sc[4 * bt];
+                        r0 = v.x, r1 = v.y;
+                        v = sc[5 * bt];
+                        r2 = v.x, r3 = v.y;
+                        v = sc[6 * bt];
+                        r4 = v.x;
+                        const int64_t qn = (int64_t)__double_as_longlong(v.y);
+                        int4 a = reinterpret_cast<const int4 *>(sc)[7 * bt];
+                        sys = a.x, phase = a.y, it = a.z, streak = a.w;
+                        a = reinterpret_cast<const int4 *>(sc)[8 * bt];
+                        steps = a.x, nck = a.y, since_ck = a.z, n_acc = a.w;
+                        a = reinterpret_cast<const int4 *>(sc)[9 * bt];
+                        n_rej = a.x, n_newt = a.y, n_solve = a.z, n_f32 = a.w;
+                        a = reinterpret_cast<const int4 *>(sc)[10 * bt];
+                        use32 = a.x != 0, fp32_off = a.y != 0;
+                        q = qn;
+                        // a thread's xe slots are not part of the staging area
+#pragma unroll
+                        for (int j = 0; j < N; j++) SL(A.xe, j) = xs[j];
+                        // idle_n counts the idle lanes: this one holds a path again
+                        if (done) {
+                            done = false;
+                            if (L.drain_at) atomicAdd(L.idle_n, ~0ull);
+                            __threadfence();
+                        }
+                    } else {
+                        q = -1;
+                    }
+                    __syncthreads();  // every read done before the next unit writes the slots
+                    // lanes emptied by the compaction count as idle, after the decrements
+                    if ((int)threadIdx.x >= live && !done) {
+                        done = true;
+                        if (L.drain_at) atomicAdd(L.idle_n, 1ull);
+                    }
+                }
+            }
+        }
         // ---------------------------------------------------------- claim a path
         if constexpr (MULTI) {
             // claim from the warp's system; when every lane of the warp is
@@ -711,9 +841,14 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             }
             if (q < 0) continue;
         } else if (q < 0) {
+            if (compact && done) continue;  // idle until the block leaves the loop
             const unsigned long long c = atomicAdd(L.qhead, 1ull);
             if (c >= (unsigned long long)np) {
                 if (L.drain_at) atomicAdd(L.idle_n, 1ull);
+                if (compact) {
+                    done = true;
+                    continue;
+                }
                 break;
             }
             q = (int64_t)c;
@@ -973,6 +1108,11 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                     }
                     continue;
                 } else {
+                    if (compact) {
+                        q = -1;
+                        done = true;
+                        continue;
+                    }
                     break;
                 }
             }
@@ -1061,7 +1201,8 @@ static int64_t lanes_n(const TrackLaunch &L, int bt, int max_blocks)
     const size_t tb = MODE == MODE_MULTI  ? (size_t)(bt / 32) * (size_t)L.warp_table_bytes
                       : MODE == MODE_PIPE ? table_smem_bytes(L.tab) + table_smem_bytes(L.tab2)
                                           : table_smem_bytes(L.tab);
-    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32);
+    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32) +
+                        (MODE == MODE_SINGLE ? compact_smem_bytes(bt) : 0);
     if (cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
@@ -1088,7 +1229,8 @@ static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_block
         if (MODE == MODE_PIPE) tb2 = table_smem_bytes(L.tab2);
     }
     const size_t smem =
-        tb + tb2 + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, L.o.precision == PHC_PREC_FP32_INTERIOR);
+        tb + tb2 + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, L.o.precision == PHC_PREC_FP32_INTERIOR) +
+        (MODE == MODE_SINGLE ? compact_smem_bytes(bt) : 0);
     cudaError_t e =
         cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -49,7 +49,7 @@ def test_default_launch_options():
     result): the tail hand-off on by default at 0.8 idle with 32 threads per
     path, double precision, library-chosen grid."""
     g = P.phc_default_opts()
-    assert g.tail_drain == 0.8 and g.tail_threads == 0
+    assert g.tail_drain == 0.8 and g.tail_threads == 0 and g.compact == 1
     assert g.precision == P.PHC_PREC_FP64 and g.block_threads == 0 and g.max_blocks == 0
     assert g.fp32_t_max == 0.9 and g.fp32_pivot_ratio == 1e4
 

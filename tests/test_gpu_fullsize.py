@@ -9,11 +9,13 @@ norm.  Here the GPU tracks every path of the same workloads, and
 
 * the class counts equal the oracle's exactly, system by system (stage by
   stage);
-* the regular endpoints match the oracle's one to one: l-values within
+* the regular endpoints match the oracle's as multisets: l-values within
   1e-10 (1 + ||x||) sum_j |r_j| (l is one random projection, so a root that
-  moved moves its value, and distinct roots keep distinct values);
-* every regular endpoint is a root of its system (independent evaluation)
-  and the regular endpoints of a system are pairwise distinct.
+  moved moves its value, and distinct roots keep distinct values); where
+  two paths of a system reach the same regular root (path jumping, which
+  the oracle shows on 3 of the 256 sparse systems with the same readings),
+  the GPU shows the same pair;
+* every regular endpoint is a root of its system (independent evaluation).
 """
 import os
 
@@ -37,21 +39,46 @@ def _expected():
 
 
 def match_projections(xg: np.ndarray, r: np.ndarray, lo: np.ndarray, no: np.ndarray):
-    """Largest relative mismatch of a one-to-one matching of the GPU regular
-    endpoints xg [P, n] with the oracle's l-values lo (norms no); inf when the
-    sizes differ or two GPU endpoints match the same oracle value."""
+    """Largest relative mismatch between the GPU regular endpoints xg [P, n]
+    and the oracle's l-values lo (norms no), as multisets: points within
+    1e-10 (1 + norm) sum|r_j| of each other are grouped (union of the
+    close pairs), and every group must hold as many GPU as oracle points
+    (two paths that reach the same root give a group of two on each side).
+    inf when a group is unbalanced."""
     if len(xg) != len(lo):
         return np.inf
     if len(xg) == 0:
         return 0.0
     lg = xg @ r[:xg.shape[1]]
     ng = np.max(np.maximum(np.abs(xg.real), np.abs(xg.imag)), axis=1)
-    tree = cKDTree(np.stack([lo.real, lo.imag], axis=1))
-    d, idx = tree.query(np.stack([lg.real, lg.imag], axis=1), k=1)
-    if len(np.unique(idx)) != len(idx):
+    pts = np.concatenate([lg, lo])
+    nrm = np.concatenate([ng, no])
+    side = np.concatenate([np.zeros(len(lg), int), np.ones(len(lo), int)])
+    s1 = np.sum(np.abs(r[:xg.shape[1]]))
+    tol = RTOL * s1 * (1.0 + nrm)
+    tree = cKDTree(np.stack([pts.real, pts.imag], axis=1))
+    parent = np.arange(len(pts))
+
+    def find(i):
+        while parent[i] != i:
+            parent[i] = parent[parent[i]]
+            i = parent[i]
+        return i
+
+    for i, j in tree.query_pairs(r=float(tol.max())):
+        if abs(pts[i] - pts[j]) <= max(tol[i], tol[j]):
+            a, b = find(i), find(j)
+            if a != b:
+                parent[a] = b
+    roots = np.array([find(i) for i in range(len(pts))])
+    bal = np.zeros(len(pts), int)
+    np.add.at(bal, roots, np.where(side == 0, 1, -1))
+    if np.any(bal != 0):
         return np.inf
-    scale = np.sum(np.abs(r[:xg.shape[1]])) * (1.0 + np.maximum(ng, no[idx]))
-    return float(np.max(d / scale))
+    # relative distance of every GPU point to the nearest oracle point
+    to = cKDTree(np.stack([lo.real, lo.imag], axis=1))
+    d, idx = to.query(np.stack([lg.real, lg.imag], axis=1), k=1)
+    return float(np.max(d / (s1 * (1.0 + np.maximum(ng, no[idx])))))
 
 
 def _check_system(label, sys, xg, cg, counts_o, lo, no, r, report):

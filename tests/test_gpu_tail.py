@@ -1,14 +1,17 @@
-"""The tail kernels change nothing but where a path is finished.
+"""The tail kernels and the compaction change nothing but where a path is
+finished.
 
 When most threads of a tracking launch have run out of paths, the paths
 that are still running move, at the start of their next step, to a kernel
 that gives every path a group of threads (opts.tail_drain, opts.tail_threads).
 That kernel performs the same floating point operations in the same order, so
 endpoints, classes and every per-path statistic must be identical, bit for
-bit, to a run without the hand-off.  Each case runs with the hand-off off;
-with the default; and, for every group size of the tail kernel, on a
-one-block grid with a drain fraction so small that nearly every path is
-handed off after its first step.
+bit, to a run without the hand-off.  The same holds for the compaction of
+the single-homotopy tracker (opts.compact: running paths move to the lowest
+threads of their block once the queue is empty).  Each case runs with both
+off; with the compaction alone; with the default; and, for every group size
+of the tail kernel, on a one-block grid with a drain fraction so small that
+nearly every path is handed off after its first step.
 """
 import numpy as np
 import pytest
@@ -19,10 +22,11 @@ from workloads import configs, cyclic, embedding_constants, multistep_example, r
 pytestmark = pytest.mark.gpu
 
 
-def _opts(drain, tiny_grid=False, group=0):
+def _opts(drain, tiny_grid=False, group=0, compact=1):
     o = P.phc_default_opts()
     o.tail_drain = drain
     o.tail_threads = group
+    o.compact = compact
     if tiny_grid:
         o.block_threads = 32
         o.max_blocks = 1
@@ -45,8 +49,9 @@ def _same(a, b, label):
 def _three_ways(run, h):
     """Hand-off off, default, and forced with each group size the kernel has
     for this number of unknowns; returns the results and the fewest paths moved."""
-    base = _host(run(_opts(0.0)))
+    base = _host(run(_opts(0.0, compact=0)))
     assert P.phc_tail_paths(h) == 0
+    _same(base, _host(run(_opts(0.0))), "compaction of running paths")
     dflt = _host(run(_opts(0.8)))
     _same(base, dflt, "default drain")
     moved = []
@@ -188,8 +193,22 @@ def test_tail_handoff_bit_identical_fp32_interior():
         o.precision = P.PHC_PREC_FP32_INTERIOR
         return P.track(h, opts=o)
 
-    base = _host(run(_opts(0.0)))
+    base = _host(run(_opts(0.0, compact=0)))
     assert P.stats_numpy(run(_opts(0.0)).stats)["n_fp32"].sum() > 0
-    for o in (_opts(0.85), _opts(1e-9, tiny_grid=True)):
-        _same(base, _host(run(o)), "FP32 interior with the tail hand-off")
+    for o in (_opts(0.0), _opts(0.85), _opts(1e-9, tiny_grid=True)):
+        _same(base, _host(run(o)), "FP32 interior with the tail hand-off and the compaction")
     assert P.phc_tail_paths(h) > 0
+
+
+def test_compaction_bit_identical_on_a_full_cyclic7_system():
+    """5040 paths of a random cyclic 7 copy on the full grid: compaction and
+    hand-off off, compaction alone, both (the default): the same bytes, and
+    with the compaction fewer paths reach the tail kernel."""
+    w = configs.cyclic7_batch()
+    h = P.phc_make_homotopy(w.systems[1], w.gammas[1])
+    base = _host(P.track(h, opts=_opts(0.0, compact=0)))
+    _same(base, _host(P.track(h, opts=_opts(0.0))), "compaction")
+    _same(base, _host(P.track(h, opts=_opts(0.8, compact=0))), "hand-off")
+    moved_plain = P.phc_tail_paths(h)
+    _same(base, _host(P.track(h, opts=_opts(0.8))), "compaction and hand-off")
+    print(f"paths moved to the tail kernel: {moved_plain} without, {P.phc_tail_paths(h)} with the compaction")
