@@ -1,7 +1,10 @@
 """Build libphc.so in-tree with nvcc for sm_103a (GB300).
 
 Translation units are compiled in parallel into ``_build/`` and linked into
-``paper_1804_03807_gb300/libphc.so`` next to this file.  Run as
+``paper_1804_03807_gb300/libphc.so`` next to this file.  ``PHC_NVCC_DEFINES``
+(environment) adds preprocessor definitions, e.g. ``-DPHC_LOCALP_MASK=0x900``
+to keep the prefix products of the 8- and 11-unknown trackers in local
+memory, for comparing layouts; call ``build(force=True)`` after changing it.  Run as
 ``python -m paper_1804_03807_gb300.build`` or call :func:`build`.
 """
 from __future__ import annotations
@@ -36,7 +39,8 @@ def _deps_mtime() -> float:
 def _compile(src: str, verbose_ptxas: bool) -> tuple[str, str]:
     obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-           "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
+           "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj,
+           *os.environ.get("PHC_NVCC_DEFINES", "").split()]
     if verbose_ptxas and src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

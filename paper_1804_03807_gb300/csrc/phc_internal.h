@@ -78,10 +78,22 @@ __host__ __device__ inline size_t table_smem_bytes(const DevTables &t)
 // S (N slots); one slot is a complex double (single precision values use its
 // first half).  Without X a 160-thread block of the 7-unknown tracker grows
 // to 192 threads.
-__host__ __device__ inline size_t thread_smem_bytes(int n, bool scale = false, bool f32 = true)
+// With localp the prefix products live in the thread's local memory (L1)
+// instead of shared memory: N fewer slots, which lets the single-homotopy
+// tracker hold more threads per block for the numbers of unknowns in
+// PHC_LOCALP_MASK (bit N set).  The default takes N = 7, 8 and 11, where the
+// block grows (N = 11: from 64 to 96 threads, 2 to 3 of the 4 SM partitions
+// busy; the cyclic 9 D=2 top stage went from 12.57 to 8.54 s; N = 7, 8: from
+// 160 to 192 and from 128 to 160 threads, 2 % faster); for the other N the
+// block size is the same either way (or already at 256 threads).
+__host__ __device__ inline size_t thread_smem_bytes(int n, bool scale = false, bool f32 = true, bool localp = false)
 {
-    return (size_t)(n * n + 3 * n + (f32 ? n : 0) + (scale ? n : 0)) * sizeof(double2);
+    return (size_t)(n * n + 3 * n - (localp ? n : 0) + (f32 ? n : 0) + (scale ? n : 0)) * sizeof(double2);
 }
+#ifndef PHC_LOCALP_MASK
+#define PHC_LOCALP_MASK ((1u << 7) | (1u << 8) | (1u << 11))
+#endif
+__host__ __device__ constexpr bool localp_of(int n) { return ((PHC_LOCALP_MASK) >> n) & 1u; }
 
 // One system of a multi-system launch (systems of different structure and
 // equal number of unknowns tracked in one kernel).
@@ -248,6 +260,7 @@ cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths,
 
 // Threads per block the tracker uses for n unknowns and a table of the given
 // size (fills up to the opt-in shared memory of one block).
-int track_block_threads(int n, size_t table_bytes, int requested, bool scale = false, bool f32 = true);
+int track_block_threads(int n, size_t table_bytes, int requested, bool scale = false, bool f32 = true,
+                        bool localp = false);
 
 }  // namespace phc

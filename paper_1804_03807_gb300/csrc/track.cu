@@ -90,10 +90,10 @@ void device_limits()
     cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 }
 
-int track_block_threads(int n, size_t table_bytes, int requested, bool scale, bool f32)
+int track_block_threads(int n, size_t table_bytes, int requested, bool scale, bool f32, bool localp)
 {
     device_limits();
-    const size_t per = thread_smem_bytes(n, scale, f32);
+    const size_t per = thread_smem_bytes(n, scale, f32, localp);
     long fit = ((long)g_smem_optin - (long)table_bytes) / (long)per;
     int bt = (int)((fit / 32) * 32);
     if (bt > 256) bt = 256;
@@ -123,7 +123,8 @@ cudaError_t launch_track(const TrackLaunch &L, int block_threads, int max_blocks
     device_limits();
     if (L.n_paths <= 0) return cudaSuccess;
     const size_t tb = table_smem_bytes(L.tab) + compact_smem_bytes(256);
-    const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR,
+                                       localp_of(L.tab.n));
     if (bt == 0) return cudaErrorInvalidConfiguration;
 #define PHC_CALL_TRACK(NN) launch_track_n<NN, MODE_SINGLE>(L, bt, max_blocks, L.n_paths, s)
     PHC_DISPATCH_N(L.tab.n, PHC_CALL_TRACK)
@@ -134,7 +135,8 @@ int64_t track_lanes(const TrackLaunch &L, int block_threads, int max_blocks)
 {
     device_limits();
     const size_t tb = table_smem_bytes(L.tab) + compact_smem_bytes(256);
-    const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, false, L.o.precision == PHC_PREC_FP32_INTERIOR,
+                                       localp_of(L.tab.n));
     if (bt == 0) return -1;
     switch (L.tab.n) {
     case 1: return lanes_n<1, MODE_SINGLE>(L, bt, max_blocks);

@@ -286,14 +286,24 @@ __device__ __forceinline__ C add_term(const TermRec r, const uint8_t *v, const u
 }
 
 // Adds a term's pieces into row Jrow / Rrow of the thread (slot stride bt);
-// prefix products in P.
-template <typename C>
+// prefix products in P (shared memory) or, with LP, in the thread's local
+// memory (NP entries).
+template <typename C, bool LP = false, int NP = 1>
 struct AccumSink {
     double2 *Jrow, *Rrow, *P;
     int bt;
     bool want_rhs;
-    __device__ __forceinline__ void put_prefix(int j, C p) { st(P, j, bt, p); }
-    __device__ __forceinline__ C get_prefix(int j) const { return ld<C>(P, j, bt); }
+    C pl[LP ? NP : 1];
+    __device__ __forceinline__ void put_prefix(int j, C p)
+    {
+        if constexpr (LP) pl[j] = p;
+        else st(P, j, bt, p);
+    }
+    __device__ __forceinline__ C get_prefix(int j) const
+    {
+        if constexpr (LP) return pl[j];
+        else return ld<C>(P, j, bt);
+    }
     __device__ __forceinline__ void last(int col, C d) { st(Jrow, col, bt, cadd(ld<C>(Jrow, col, bt), d)); }
     __device__ __forceinline__ void deriv(int, int col, C pj, C suf)
     {
@@ -315,7 +325,7 @@ struct AccumSink {
 //   d/dx_{v_j} c(t) x^a = a_j c(t) cf prod_{i<j} x_{v_i} prod_{i>j} x_{v_i}.
 // With SCALE, S[i].x accumulates sum over the terms of equation i of
 // |c(t)|_1 |x^a|_1 (relative residual and condition number; double only).
-template <int N, typename C, bool SCALE>
+template <int N, typename C, bool SCALE, bool LP = false>
 __device__ __forceinline__ void evaluate(const C *C0, const C *C1, const SmTab &tb,
                                          typename real_of<C>::type t, bool dt, bool want_rhs, const double2 *X,
                                          double2 *R, double2 *J, double2 *P, double2 *S, int bt)
@@ -340,7 +350,7 @@ __device__ __forceinline__ void evaluate(const C *C0, const C *C1, const SmTab &
             if (SCALE) SL(S, r.eq).x += abs1(ct);
             continue;
         }
-        AccumSink<C> sink{J + r.eq * N * bt, R + r.eq * bt, P, bt, want_rhs};
+        AccumSink<C, LP, N> sink{J + r.eq * N * bt, R + r.eq * bt, P, bt, want_rhs, {}};
         const C mono = add_term<C>(r, tb.vars + r.off, tb.exps + r.off, ct, cr, X, bt, sink);
         if (SCALE) SL(S, r.eq).x += abs1(ct) * abs1(mono);
     }
@@ -458,17 +468,19 @@ struct ThreadArrays {
     double2 *xe, *R, *P, *X, *J, *S;
 };
 
-// The layout of thread_smem_bytes; without f32 there is no X (it aliases P
-// and is never touched).
-template <int N>
+// The layout of thread_smem_bytes; without f32 there is no X (it aliases R
+// or P and is never touched); with LP there is no P (prefix products in
+// local memory).
+template <int N, bool LP = false>
 __device__ __forceinline__ ThreadArrays thread_arrays(char *smem, size_t table_bytes, int bt, bool f32)
 {
     ThreadArrays a;
     a.xe = reinterpret_cast<double2 *>(smem + table_bytes) + threadIdx.x;
     a.R = a.xe + N * bt;
-    a.P = a.R + N * bt;
-    a.X = f32 ? a.P + N * bt : a.P;
-    a.J = f32 ? a.X + N * bt : a.P + N * bt;
+    a.P = LP ? nullptr : a.R + N * bt;
+    double2 *after = LP ? a.R + N * bt : a.P + N * bt;
+    a.X = f32 ? after : a.R;
+    a.J = f32 ? after + N * bt : after;
     a.S = a.J + N * N * bt;  // classification only
     return a;
 }
@@ -589,8 +601,11 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 {
     constexpr bool PIPE = MODE == MODE_PIPE;
     constexpr bool MULTI = MODE == MODE_MULTI;
-    // compaction needs 3N + 11 free slots per thread between units (R, P, J: N^2 + 2N)
-    constexpr bool COMPACT = MODE == MODE_SINGLE && N >= 4;
+    // prefix products in local memory for the numbers of unknowns in PHC_LOCALP_MASK
+    constexpr bool LOCALP = MODE == MODE_SINGLE && localp_of(N);
+    // compaction needs 3N + 11 free slots per thread between units (R, (P), J:
+    // N^2 + 2N, with LOCALP N^2 + N)
+    constexpr bool COMPACT = MODE == MODE_SINGLE && N >= (LOCALP ? 5 : 4);
     extern __shared__ __align__(16) char smem[];
     SmTab tb{}, tb2{};
     if constexpr (!MULTI) {
@@ -600,7 +615,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
     }
     const int bt = blockDim.x;
     const bool f32 = L.o.precision == PHC_PREC_FP32_INTERIOR;
-    const ThreadArrays A = thread_arrays<N>(smem, table_bytes + table2_bytes, bt, f32);
+    const ThreadArrays A = thread_arrays<N, LOCALP>(smem, table_bytes + table2_bytes, bt, f32);
     const phc_opts &o = L.o;
     const int64_t np = L.n_paths;
     const bool interior32 = o.precision == PHC_PREC_FP32_INTERIOR;
@@ -684,7 +699,8 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
     int *cinfo = nullptr;  // [32] warp counts, [32] warp offsets
     int16_t *cmap = nullptr;  // [bt] source lane of each destination
     if constexpr (COMPACT) {
-        cinfo = reinterpret_cast<int *>(smem + table_bytes + table2_bytes + (size_t)bt * thread_smem_bytes(N, false, f32));
+        cinfo = reinterpret_cast<int *>(smem + table_bytes + table2_bytes +
+                                        (size_t)bt * thread_smem_bytes(N, false, f32, LOCALP));
         cmap = reinterpret_cast<int16_t *>(cinfo + 64);
     }
 
@@ -930,7 +946,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 #pragma unroll
                 for (int j = 0; j < N; j++) st(A.R, j, bt, to_f(SL(A.R, j)));
             }
-            evaluate<N, float2, false>(C0f, C1f, *cur, (float)te, true, dt, A.X, A.R, A.J, A.P, A.S, bt);
+            evaluate<N, float2, false, LOCALP>(C0f, C1f, *cur, (float)te, true, dt, A.X, A.R, A.J, A.P, A.S, bt);
             ok = lu_factor<N, float2>(A.J, perm, bt, (float)o.fp32_pivot_ratio);
             if (ok) lu_solve<N, float2>(A.J, perm, A.R, bt);
 #pragma unroll
@@ -938,7 +954,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
             n_f32++;
         } else {
             const double2 *C0 = cur->c0 + (size_t)sys * cur->n_terms, *C1 = cur->c1 + (size_t)sys * cur->n_terms;
-            evaluate<N, double2, false>(C0, C1, *cur, te, dt, true, A.xe, A.R, A.J, A.P, A.S, bt);
+            evaluate<N, double2, false, LOCALP>(C0, C1, *cur, te, dt, true, A.xe, A.R, A.J, A.P, A.S, bt);
             ok = lu_factor<N, double2>(A.J, perm, bt);
             if (ok) lu_solve<N, double2>(A.J, perm, A.R, bt);
 #pragma unroll
@@ -1201,7 +1217,7 @@ static int64_t lanes_n(const TrackLaunch &L, int bt, int max_blocks)
     const size_t tb = MODE == MODE_MULTI  ? (size_t)(bt / 32) * (size_t)L.warp_table_bytes
                       : MODE == MODE_PIPE ? table_smem_bytes(L.tab) + table_smem_bytes(L.tab2)
                                           : table_smem_bytes(L.tab);
-    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32) +
+    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32, MODE == MODE_SINGLE && localp_of(N)) +
                         (MODE == MODE_SINGLE ? compact_smem_bytes(bt) : 0);
     if (cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
@@ -1229,7 +1245,9 @@ static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_block
         if (MODE == MODE_PIPE) tb2 = table_smem_bytes(L.tab2);
     }
     const size_t smem =
-        tb + tb2 + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, L.o.precision == PHC_PREC_FP32_INTERIOR) +
+        tb + tb2 +
+        (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, L.o.precision == PHC_PREC_FP32_INTERIOR,
+                                       MODE == MODE_SINGLE && localp_of(N)) +
         (MODE == MODE_SINGLE ? compact_smem_bytes(bt) : 0);
     cudaError_t e =
         cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
