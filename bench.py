@@ -676,6 +676,21 @@ def run_configs(args):
                                               unit_flops(homotopy_terms(E1), 10)], ms2))
         return d
 
+    def config10():
+        """Double double tracking (Section 5, Table 2: the solver in double
+        double): one random-coefficient cyclic 7 copy (5040 paths), against
+        the same paths in double precision."""
+        w = configs.cyclic7_batch()
+        h = P.phc_make_homotopy(w.systems[1], w.gammas[1])
+        ms = _timed(lambda: out.__setitem__("r", P.track_dd(h)), 1, 1)
+        r, _ = out["r"]
+        ms64 = _timed(lambda: P.track(h), 3, 1)
+        st = P.stats_numpy(r.stats)
+        return {"config": "dd", "workload": "cyclic 7 random copy 1, 5040 paths, complex double double",
+                "paths_per_s": 5040 / (ms / 1e3), "ms": ms, "units": int(st["n_solve"].sum()),
+                "classes": np.bincount(r.cls.cpu().numpy(), minlength=4).tolist(),
+                "fp64": {"paths_per_s": 5040 / (ms64 / 1e3), "ms": ms64}}
+
     def config5():
         sv, reqs = serving_session(args.requests, not args.no_big, args.slots, args.batch_paths)
         d = {"config": 5, "workload": f"{args.requests} Poisson (200/s) sparse requests"
@@ -688,7 +703,7 @@ def run_configs(args):
         return d
 
     want = [int(c) for c in args.configs.split(",")] if args.configs else [1, 2, 3, 4, 5]
-    table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9}
+    table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9, 10: config10}
     for c in want:
         print(json.dumps(table[c]()), flush=True)
     return 0
@@ -742,7 +757,7 @@ def main(argv=None):
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the cyclic 9 request")
     ap.add_argument("--batch-paths", type=int, default=60_000, help="serving: most paths per batch of small requests")
     ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default 1-5; 9 = the "
-                    "cyclic 9 D=2 request of the serving workload alone)")
+                    "cyclic 9 D=2 request of the serving workload alone; 10 = double double tracking)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",

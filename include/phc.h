@@ -215,6 +215,23 @@ int phc_num_paths(const phc_homotopy *h, int64_t *out);
 int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_out,
                     int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
 
+/* phc_track_paths in complex double double arithmetic (Section 5 and
+ * Table 2: the solver run in double double, "quality up").  The same
+ * readings as phc_track_paths (RK4 predictor, Newton corrector, step
+ * control, tolerances, stall and divergence rules), but the point, the
+ * Runge-Kutta stages, H, H_x, H_t, the LU and the solves are complex double
+ * double (t, step sizes and norms stay double, norms from the double parts);
+ * the end Newton at t = 1 stops at ||dx|| <= 1e-26 (1 + ||x||), so a
+ * regular endpoint is accurate to about 1e-30.  The endpoint is classified
+ * from its double part as a double endpoint.  A unit costs about 15 times a
+ * double precision one; there is no tail hand-off and no compaction
+ * (opts.tail_drain, tail_threads, compact and precision are ignored).
+ * Outputs (device, caller-owned): x_hi and x_lo SoA [n_var][n_paths] (the
+ * endpoint is x_hi + x_lo), cls_out [n_paths], stats_out [n_paths] or NULL.
+ * Errors: as phc_track_paths. */
+int phc_track_paths_dd(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_hi,
+                       phc_cd *x_lo, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
+
 /* The embedded system E_D of Section 2.1 (eq. (2) for D = 1): unknowns
  * x_1..x_n, z_1..z_D; equation i is f_i(x) + sum_k gammas[i][k] z_k; equation
  * n_eq + k is hyper[k][0] + sum_j hyper[k][j+1] x_j + z_k.  A square f only

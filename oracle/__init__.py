@@ -192,6 +192,34 @@ def track(h: Homotopy, starts: np.ndarray | None = None, first: int = 0, n_paths
     return x, cls, stats
 
 
+def track_dd(h: Homotopy, starts: np.ndarray | None = None, first: int = 0, n_paths: int | None = None,
+             opts: Opts | None = None, threads: int | None = None):
+    """Track paths in complex double double (Section 5, Table 2: the solver in
+    double double arithmetic); returns (x_hi, x_lo [P, n] complex128, cls,
+    stats)."""
+    L = lib()
+    if starts is not None:
+        starts = np.ascontiguousarray(starts, dtype=np.complex128).reshape(-1, h.n)
+        n_paths = starts.shape[0]
+        sbuf = starts.view(np.float64).ctypes.data_as(ctypes.c_void_p)
+    else:
+        if n_paths is None:
+            n_paths = num_paths(h) - first
+        sbuf = None
+    xh = np.zeros((n_paths, h.n), dtype=np.complex128)
+    xl = np.zeros((n_paths, h.n), dtype=np.complex128)
+    cls = np.zeros(n_paths, dtype=np.int8)
+    stats = np.zeros(n_paths, dtype=STATS_DTYPE)
+    o = opts if opts is not None else default_opts()
+    rc = L.orc_track_dd(h.ref(), sbuf, ctypes.c_int64(first), ctypes.c_int64(n_paths), ctypes.byref(o),
+                        int(threads or host_threads()), xh.view(np.float64).ctypes.data_as(ctypes.c_void_p),
+                        xl.view(np.float64).ctypes.data_as(ctypes.c_void_p), cls.ctypes.data_as(ctypes.c_void_p),
+                        stats.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError(f"orc_track_dd failed: {rc}")
+    return xh, xl, cls, stats
+
+
 def refine(h: Homotopy, x: np.ndarray, cls: np.ndarray, cond: np.ndarray, reached: np.ndarray,
            cond_threshold: float = 1e6, cond_max: float = 1e12, max_iters: int = 8):
     """Double double Newton refinement at t = 1 of the ill-conditioned

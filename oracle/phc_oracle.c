@@ -856,6 +856,290 @@ int orc_refine(const orc_homotopy *h, double *x_hi, double *x_lo, int64_t n_path
     return 0;
 }
 
+/* ================================================================ double double path tracking
+ * Section 5 and Table 2 run the whole solver in double double arithmetic
+ * ("quality up").  Here a path is tracked with the readings of track_one
+ * (RK4 predictor, Newton corrector, the same step control, tolerances,
+ * stall and divergence rules), but the point x, the predictor stages, H,
+ * H_x, H_t, the LU and the solves are complex double double; t, the step
+ * sizes and the norms (taken from the double parts) stay double.  The end
+ * Newton at t = 1 stops at ||dx|| <= END_TOL_DD (1 + ||x||); the endpoint is
+ * classified from its double part with end_measures, as a double endpoint. */
+
+#define END_TOL_DD 1e-26
+
+static cdd cdd_scale(double a, cdd z)
+{
+    cdd r = { dd_mul(dd_from(a), z.re), dd_mul(dd_from(a), z.im) };
+    return r;
+}
+
+/* H(x,t), H_x(x,t), H_t(x,t) in complex double double, every monomial and
+ * partial derivative from scratch (as eval_homotopy). */
+static void eval_homotopy_dd(const orc_homotopy *h, const cdd *x, double t, cdd *H, cdd *Hx, cdd *Ht)
+{
+    const int n = h->n;
+    const cdd gamma = cdd_from(h->gamma_re + I * h->gamma_im);
+    const cdd one = cdd_from(1.0);
+    const dd omt = dd_sub(dd_from(1.0), dd_from(t)); /* 1 - t, exact */
+    const cdd w1 = { omt, dd_from(0.0) };
+    const cdd tt = cdd_from(t);
+    int off = 0;
+    for (int i = 0; i < n; i++) {
+        cdd f = cdd_from(0.0), ft = cdd_from(0.0);
+        for (int j = 0; j < n; j++) Hx[i * n + j] = cdd_from(0.0);
+        for (int k = 0; k < h->terms_per_eq[i]; k++) {
+            const uint8_t *a = h->exps + (size_t)(off + k) * n;
+            const cdd c = cdd_from(coef_of(h, off + k));
+            cdd ct, dct;
+            if (h->kind == 0) {
+                ct = cdd_mul(tt, c);
+                dct = c;
+            } else if (h->kind == 2) {
+                const cdd c0 = cdd_from(h->coefs0[2 * (off + k)] + I * h->coefs0[2 * (off + k) + 1]);
+                const cdd gc0 = cdd_mul(gamma, c0);
+                ct = cdd_add(cdd_mul(w1, gc0), cdd_mul(tt, c));
+                dct = cdd_sub(c, gc0);
+            } else if (i == h->row && !is_unit(a, n, h->slack)) {
+                ct = cdd_mul(w1, c);
+                dct = cdd_sub(cdd_from(0.0), c);
+            } else {
+                ct = c;
+                dct = cdd_from(0.0);
+            }
+            cdd m = one;
+            for (int j = 0; j < n; j++) m = cdd_mul(m, cdd_ipow(x[j], a[j]));
+            f = cdd_add(f, cdd_mul(ct, m));
+            ft = cdd_add(ft, cdd_mul(dct, m));
+            for (int j = 0; j < n; j++) {
+                if (a[j] == 0) continue;
+                cdd d = cdd_scale((double)a[j], cdd_ipow(x[j], a[j] - 1));
+                for (int q = 0; q < n; q++)
+                    if (q != j) d = cdd_mul(d, cdd_ipow(x[q], a[q]));
+                Hx[i * n + j] = cdd_add(Hx[i * n + j], cdd_mul(ct, d));
+            }
+        }
+        if (h->kind == 0) {
+            /* start system g_i = x_i^{d_i} - 1, weighted by (1-t) gamma */
+            const int d = eq_degree(h, i, off);
+            const cdd xd = cdd_ipow(x[i], d);
+            const cdd g = cdd_sub(xd, one);
+            const cdd w = cdd_mul(w1, gamma);
+            f = cdd_add(f, cdd_mul(w, g));
+            ft = cdd_sub(ft, cdd_mul(gamma, g));
+            Hx[i * n + i] = cdd_add(Hx[i * n + i], cdd_mul(w, cdd_scale((double)d, cdd_ipow(x[i], d - 1))));
+        }
+        H[i] = f;
+        Ht[i] = ft;
+        off += h->terms_per_eq[i];
+    }
+}
+
+static double vnorm_dd(int n, const cdd *v)
+{
+    double m = 0.0;
+    for (int j = 0; j < n; j++) {
+        double a = cdd_absinf(v[j]);
+        if (!(a <= m)) m = a;
+    }
+    return m;
+}
+
+static int all_finite_dd(int n, const cdd *x)
+{
+    for (int j = 0; j < n; j++)
+        if (!isfinite(x[j].re.hi) || !isfinite(x[j].im.hi) || !isfinite(x[j].re.lo) || !isfinite(x[j].im.lo)) return 0;
+    return 1;
+}
+
+/* v = -H_x^{-1} H_t at (x, t).  Returns -1 if the LU meets a zero pivot. */
+static int tangent_dd(const orc_homotopy *h, const cdd *x, double t, cdd *v, orc_stats *st)
+{
+    cdd H[NMAX], Hx[NMAX * NMAX];
+    eval_homotopy_dd(h, x, t, H, Hx, v);
+    st->n_solve++;
+    if (lu_solve_dd(h->n, Hx, v)) return -1;
+    for (int j = 0; j < h->n; j++) v[j] = cdd_sub(cdd_from(0.0), v[j]);
+    return 0;
+}
+
+/* One Newton step at fixed t: x -= H_x^{-1} H.  Returns ||dx||, NAN when singular. */
+static double newton_step_dd(const orc_homotopy *h, cdd *x, double t, orc_stats *st)
+{
+    cdd H[NMAX], Hx[NMAX * NMAX], Ht[NMAX];
+    eval_homotopy_dd(h, x, t, H, Hx, Ht);
+    st->n_solve++;
+    st->n_newton++;
+    if (lu_solve_dd(h->n, Hx, H)) return NAN;
+    for (int j = 0; j < h->n; j++) x[j] = cdd_sub(x[j], H[j]);
+    return vnorm_dd(h->n, H);
+}
+
+/* track_one in complex double double (the same readings, step for step). */
+static void track_one_dd(const orc_homotopy *h, const orc_opts *o, cdd *x, orc_stats *st)
+{
+    const int n = h->n;
+    cdd x0[NMAX], xs[NMAX], k1[NMAX], k2[NMAX], k3[NMAX], k4[NMAX];
+    double t = 0.0, step = o->h_init;
+    int streak = 0, steps = 0;
+    double ck[5];
+    int nck = 0;
+    double next_s = 0.1;
+    int since_ck = 0;
+    memset(st, 0, sizeof *st);
+    while (t < 1.0) {
+        double he = step;
+        double t1 = t + he;
+        if (he >= 1.0 - t) { he = 1.0 - t; t1 = 1.0; }
+        memcpy(x0, x, sizeof(cdd) * n);
+        const cdd hh = cdd_from(0.5 * he), hf = cdd_from(he), h6 = cdd_from(he / 6.0), two = cdd_from(2.0);
+        int ok = 1;
+        ok = ok && !tangent_dd(h, x0, t, k1, st);
+        for (int j = 0; j < n; j++) xs[j] = cdd_add(x0[j], cdd_mul(hh, k1[j]));
+        ok = ok && !tangent_dd(h, xs, t + 0.5 * he, k2, st);
+        for (int j = 0; j < n; j++) xs[j] = cdd_add(x0[j], cdd_mul(hh, k2[j]));
+        ok = ok && !tangent_dd(h, xs, t + 0.5 * he, k3, st);
+        for (int j = 0; j < n; j++) xs[j] = cdd_add(x0[j], cdd_mul(hf, k3[j]));
+        ok = ok && !tangent_dd(h, xs, t1, k4, st);
+        if (ok)
+            for (int j = 0; j < n; j++) {
+                cdd acc = cdd_add(cdd_add(k1[j], cdd_mul(two, k2[j])), cdd_add(cdd_mul(two, k3[j]), k4[j]));
+                x[j] = cdd_add(x0[j], cdd_mul(h6, acc));
+            }
+        int conv = 0;
+        double prev = INFINITY;
+        for (int it = 0; ok && it < o->max_corr_iters; it++) {
+            double d = newton_step_dd(h, x, t1, st);
+            if (!(d == d) || !all_finite_dd(n, x)) break;
+            if (d <= o->corr_tol * (1.0 + vnorm_dd(n, x))) { conv = 1; break; }
+            if (it > 0 && d > o->corr_contract * prev) break;
+            prev = d;
+        }
+        steps++;
+        if (conv) {
+            t = t1;
+            st->n_accept++;
+            while (1.0 - t <= next_s && next_s > 0.0) {
+                ck[nck % 5] = vnorm_dd(n, x);
+                nck++;
+                since_ck = 0;
+                next_s *= 0.1;
+                if (nck >= 40) next_s = 0.0;
+            }
+            if (vnorm_dd(n, x) > o->diverge_norm) { st->stop = 1; break; }
+            if (++streak >= o->expand_after) {
+                streak = 0;
+                step = step * o->expand;
+                if (step > o->h_max) step = o->h_max;
+            }
+        } else {
+            memcpy(x, x0, sizeof(cdd) * n);
+            st->n_reject++;
+            streak = 0;
+            step = he * o->shrink;
+            if (step < o->h_min) { st->stop = 2; break; }
+        }
+        if (steps >= o->max_steps) { st->stop = 3; break; }
+        if (++since_ck >= o->max_steps_decade && t < 1.0) { st->stop = 3; break; }
+    }
+    st->t = t;
+    st->h = step;
+    int grew = 0;
+    st->growth = 0.0;
+    if (nck >= 2) {
+        int l = nck - 1, m = l < 4 ? l : 4;
+        double a = ck[l % 5], b = ck[(l - m) % 5], g = 1.0;
+        for (int k = 0; k < m; k++) g *= o->growth_inf;
+        grew = a > b * g;
+        st->growth = log10(a / b) / m;
+    }
+    cplx xh[NMAX];
+    if (!all_finite_dd(n, x)) { st->stop = 4; st->cls = ORC_FAILED; st->norm_x = NAN; st->cond = NAN; st->relres = NAN; return; }
+    st->norm_x = vnorm_dd(n, x);
+    if (st->stop == 1) { st->cls = ORC_AT_INFINITY; st->cond = INFINITY; st->relres = NAN; return; }
+    if (st->stop != 0) {
+        for (int j = 0; j < n; j++) xh[j] = x[j].re.hi + I * x[j].im.hi;
+        end_measures(h, xh, &st->cond, &st->relres);
+        if (st->norm_x > o->endpoint_inf_norm || (t >= o->end_zone && grew)) st->cls = ORC_AT_INFINITY;
+        else if (t < o->end_zone) st->cls = ORC_FAILED;
+        else st->cls = ORC_SINGULAR;
+        return;
+    }
+    for (int it = 0; it < o->end_iters; it++) {
+        double d = newton_step_dd(h, x, 1.0, st);
+        if (!(d == d) || !all_finite_dd(n, x)) break;
+        if (d <= END_TOL_DD * (1.0 + vnorm_dd(n, x))) break;
+    }
+    if (!all_finite_dd(n, x)) { st->stop = 4; st->cls = ORC_FAILED; st->norm_x = NAN; st->cond = NAN; st->relres = NAN; return; }
+    st->norm_x = vnorm_dd(n, x);
+    for (int j = 0; j < n; j++) xh[j] = x[j].re.hi + I * x[j].im.hi;
+    end_measures(h, xh, &st->cond, &st->relres);
+    if (st->norm_x > o->endpoint_inf_norm) st->cls = ORC_AT_INFINITY;
+    else if (st->cond <= o->cond_regular && st->relres <= o->res_regular) st->cls = ORC_REGULAR;
+    else st->cls = ORC_SINGULAR;
+}
+
+typedef struct {
+    const orc_homotopy *h;
+    const orc_opts *o;
+    const double *starts; /* [n_paths][n][2] or NULL */
+    int64_t first, n_paths;
+    double *x_hi, *x_lo;  /* [n_paths][n][2] */
+    int8_t *cls_out;
+    orc_stats *stats_out;
+    atomic_llong next;
+} crew_dd_t;
+
+static void *crew_dd_worker(void *arg)
+{
+    crew_dd_t *c = (crew_dd_t *)arg;
+    const int n = c->h->n;
+    cdd x[NMAX];
+    cplx xs[NMAX];
+    orc_stats st;
+    for (;;) {
+        int64_t q = atomic_fetch_add(&c->next, 1);
+        if (q >= c->n_paths) break;
+        if (c->starts)
+            for (int j = 0; j < n; j++) xs[j] = c->starts[(q * n + j) * 2] + I * c->starts[(q * n + j) * 2 + 1];
+        else
+            start_solution(c->h, c->first + q, xs);
+        for (int j = 0; j < n; j++) x[j] = cdd_from(xs[j]);
+        track_one_dd(c->h, c->o, x, &st);
+        for (int j = 0; j < n; j++) {
+            c->x_hi[(q * n + j) * 2] = x[j].re.hi;
+            c->x_hi[(q * n + j) * 2 + 1] = x[j].im.hi;
+            c->x_lo[(q * n + j) * 2] = x[j].re.lo;
+            c->x_lo[(q * n + j) * 2 + 1] = x[j].im.lo;
+        }
+        if (c->cls_out) c->cls_out[q] = (int8_t)st.cls;
+        if (c->stats_out) c->stats_out[q] = st;
+    }
+    return NULL;
+}
+
+/* Track paths in complex double double (see track_one_dd); x_hi and x_lo
+ * receive the two parts of every endpoint. */
+int orc_track_dd(const orc_homotopy *h, const double *starts, int64_t first, int64_t n_paths, const orc_opts *o_in,
+                 int n_threads, double *x_hi, double *x_lo, int8_t *cls_out, orc_stats *stats_out)
+{
+    orc_opts o;
+    if (o_in) o = *o_in; else orc_default_opts(&o);
+    if (h->n < 1 || h->n > NMAX || n_paths < 0) return -1;
+    if (!starts && h->kind != 0) return -1;
+    crew_dd_t c;
+    c.h = h; c.o = &o; c.starts = starts; c.first = first; c.n_paths = n_paths;
+    c.x_hi = x_hi; c.x_lo = x_lo; c.cls_out = cls_out; c.stats_out = stats_out;
+    atomic_init(&c.next, 0);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads == 1) { crew_dd_worker(&c); return 0; }
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * n_threads);
+    for (int k = 0; k < n_threads; k++) pthread_create(&th[k], NULL, crew_dd_worker, &c);
+    for (int k = 0; k < n_threads; k++) pthread_join(th[k], NULL);
+    free(th);
+    return 0;
+}
+
 /* Size of the stats record, so the Python side can check its mirror. */
 int orc_stats_size(void) { return (int)sizeof(orc_stats); }
 int orc_opts_size(void) { return (int)sizeof(orc_opts); }

@@ -32,7 +32,7 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
                    phc_tail_paths, phc_track_many, phc_track_paths_noalloc, phc_track_pipeline,
                    phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square,
-                   phc_many_plan_create, phc_many_plan_run, ManyPlan)
+                   phc_many_plan_create, phc_many_plan_run, ManyPlan, phc_track_paths_dd)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -44,6 +44,7 @@ __all__ = [
     "Tracked", "pipeline", "track", "cascade", "refine",
     "stats_numpy", "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
     "track_from", "membership", "phc_square", "phc_many_plan_create", "phc_many_plan_run", "ManyPlan",
+    "phc_track_paths_dd", "track_dd",
 ]
 
 
@@ -103,6 +104,18 @@ def membership(emb, k: int, witness, points, tol: float = 1e-3, opts=None, strea
     cls = torch.empty(p * m, dtype=torch.int8, device=dev)
     phc_membership_test(emb, k, witness.contiguous(), pts, tol, opts, on, x, cls, stream)
     return on.cpu().numpy().astype(bool), Tracked(x, cls, None)
+
+
+def track_dd(h: Homotopy, first: int = 0, n_paths: int | None = None, opts=None, stream=None, device="cuda"):
+    """Total-degree paths tracked in complex double double; returns
+    (Tracked with the double parts in x, the low parts [n_var, P])."""
+    import torch
+    if n_paths is None:
+        n_paths = phc_num_paths(h) - first
+    x, cls, st = _alloc(h.n, n_paths, device)
+    xlo = torch.empty_like(x)
+    phc_track_paths_dd(h, first, n_paths, opts, x, xlo, cls, st, stream)
+    return Tracked(x, cls, st), xlo
 
 
 def cascade(h_k: Homotopy, k: int, starts, opts=None, stream=None) -> Tracked:

@@ -246,6 +246,9 @@ cudaError_t launch_tail_pipe(const TrackLaunch &L, int max_blocks, cudaStream_t 
 int64_t pipe_lanes(const TrackLaunch &L, int block_threads, int max_blocks);
 bool tail_pipe_supported(const DevTables &t1, const DevTables &t2);
 cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
+// Total-degree paths of L tracked in complex double double (track_dd.cu):
+// double parts to L.x_out, low parts to L.x_out2, records to L.stats.
+cudaError_t launch_track_dd(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 cudaError_t launch_refine(const RefineLaunch &L, cudaStream_t s);
 // match[j] = 1 when one of the m endpoints x[:, j*m .. j*m+m) (SoA over
 // p*m entries, N unknowns) of class PHC_REGULAR or PHC_SINGULAR equals

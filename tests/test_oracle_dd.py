@@ -68,3 +68,55 @@ def test_refinement_reaches_double_double_accuracy():
         before = exact_residual(sys, x[p], np.zeros_like(x[p]))
         after = exact_residual(sys, xh[p], xl[p])
         assert after <= 1e-28, (p, before, after)
+
+
+# ------------------------------------------------------------ double double path tracking (Section 5, Table 2)
+
+def test_dd_tracker_dense4_reaches_double_double_accuracy():
+    """The whole path in double double: the same 16 regular endpoints as the
+    double tracker (1e-10), with the same step counts (the readings are the
+    same), and each endpoint x_hi + x_lo a root of f to 1e-28 in exact
+    rational arithmetic."""
+    from workloads import configs
+    from tests._checks import exact_residual, same_set
+    w = configs.dense4()
+    s, g = w.systems[0], w.gammas[0]
+    h = oracle.total_degree(s, g)
+    xh, xl, c, st = oracle.track_dd(h, threads=1)
+    x, c2, st2 = oracle.track(h, threads=1)
+    assert np.all(c == oracle.REGULAR) and np.all(c2 == oracle.REGULAR)
+    ok, err = same_set(xh, x, 1e-10)
+    assert ok, err
+    assert np.array_equal(st["n_accept"] + st["n_reject"], st2["n_accept"] + st2["n_reject"])
+    for p in range(16):
+        assert exact_residual(s, xh[p], xl[p]) <= 1e-28
+
+
+def test_dd_tracker_univariate_and_cyclic5():
+    """A degree 6 polynomial: the double double endpoints are its companion
+    matrix eigenvalues (1e-12) and roots to 1e-28 exactly; cyclic 5: the
+    double tracker's classes and regular set, every regular endpoint a root
+    to 1e-28."""
+    from workloads import cyclic, rng_for, unit_gamma, univariate
+    from tests._checks import exact_residual, same_set
+    rng = rng_for(91)
+    c = rng.normal(size=7) + 1j * rng.normal(size=7)
+    s = univariate(c)
+    h = oracle.total_degree(s, unit_gamma(rng))
+    xh, xl, cls, st = oracle.track_dd(h, threads=1)
+    assert np.all(cls == oracle.REGULAR)
+    comp = np.roots(c[::-1])
+    ok, err = same_set(xh, comp[:, None], 1e-12)
+    assert ok, err
+    for p in range(6):
+        assert exact_residual(s, xh[p], xl[p]) <= 1e-28
+    s5 = cyclic(5)
+    h5 = oracle.total_degree(s5, unit_gamma(rng_for(92)))
+    xh, xl, cls, st = oracle.track_dd(h5)
+    x, c2, _ = oracle.track(h5)
+    assert np.array_equal(np.bincount(cls, minlength=4), np.bincount(c2, minlength=4))
+    ok, err = same_set(xh[cls == 0], x[c2 == 0], 1e-10)
+    assert ok, err
+    reg = np.where(cls == 0)[0]
+    for p in reg[:10]:
+        assert exact_residual(s5, xh[p], xl[p]) <= 1e-28
