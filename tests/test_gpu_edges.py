@@ -1,0 +1,78 @@
+"""Edge cases through the C ABI on the GPU: the largest number of unknowns
+(12) in every tracker (double, double double, forced tail hand-off and
+compaction off and on), single paths at the ends of the range, and empty
+calls of every entry point."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1804_03807_gb300 as P
+from workloads import PolySystem, cn01, configs, cyclic, rng_for, unit_gamma
+from workloads.systems import all_monomials
+from tests._checks import relative_residual, same_set
+
+pytestmark = pytest.mark.gpu
+
+
+def _system12(seed=95):
+    """11 random linear equations and one random quadratic in 12 unknowns
+    (every monomial present): Bezout number 2."""
+    rng = rng_for(seed)
+    n = 12
+    lin, quad = all_monomials(n, 1), all_monomials(n, 2)
+    exps = np.array(lin * 11 + quad, dtype=np.uint8).reshape(-1, n)
+    tpe = np.array([len(lin)] * 11 + [len(quad)])
+    return PolySystem(n, n, tpe, exps, cn01(rng, exps.shape[0]), name="mixed12")
+
+
+def test_twelve_unknowns_every_tracker():
+    s = _system12()
+    g = unit_gamma(rng_for(96))
+    h = P.phc_make_homotopy(s, g)
+    assert P.phc_num_paths(h) == 2
+    xo, co, _ = oracle.track(oracle.total_degree(s, g), threads=1)
+    assert np.bincount(co, minlength=4)[0] == 2
+    outs = []
+    for o in (P.phc_default_opts(tail_drain=0.0, compact=0), P.phc_default_opts(),
+              P.phc_default_opts(tail_drain=1e-9, block_threads=32, max_blocks=1)):
+        r = P.track(h, opts=o)
+        outs.append((r.x.cpu().numpy(), r.cls.cpu().numpy(), r.stats.cpu().numpy()))
+    for a in outs[1:]:
+        for u, v in zip(outs[0], a):
+            assert u.tobytes() == v.tobytes()
+    x, c = outs[0][0].T, outs[0][1]
+    ok, err = same_set(x[c == 0], xo[co == 0], 1e-10)
+    assert ok and relative_residual(s, x[c == 0]).max() <= 1e-12, err
+    rd, xlo = P.track_dd(h)
+    xd = rd.x.cpu().numpy().T
+    assert np.array_equal(rd.cls.cpu().numpy(), c)
+    ok, err = same_set(xd[c == 0], xo[co == 0], 1e-10)
+    assert ok, err
+
+
+def test_single_paths_at_the_ends_and_empty_calls():
+    w = configs.cyclic7_batch()
+    hb = P.phc_make_homotopy_batch(w.systems[:2], w.gammas[:2])
+    total = P.phc_num_paths(hb)
+    whole = P.track(hb)
+    for first in (0, total - 1):
+        r = P.track(hb, first=first, n_paths=1)
+        assert np.array_equal(r.x.cpu().numpy()[:, 0], whole.x.cpu().numpy()[:, first])
+        assert r.cls.cpu().numpy()[0] == whole.cls.cpu().numpy()[first]
+    # empty calls return without work
+    e = torch.empty((7, 0), dtype=torch.complex128, device="cuda")
+    c = torch.empty(0, dtype=torch.int8, device="cuda")
+    P.phc_track_paths(hb, total, 0, None, e, c)
+    P.phc_track_paths_dd(hb, 0, 0, None, e, e, c)
+    P.phc_track_many([], None, [], [])
+    h5 = P.phc_make_homotopy(cyclic(5), 0.6 + 0.8j)
+    P.phc_track_from(h5, e[:5], 0, 0, None, e[:5], c)
+    P.phc_cascade_stage(h5, 1, e[:5], 0, None, e[:4], c, c)
+    on = torch.empty(0, dtype=torch.uint8, device="cuda")
+    E = P.phc_embed(cyclic(4), 1)
+    P.phc_membership_test(E, 1, torch.zeros((5, 1), dtype=torch.complex128, device="cuda"), np.zeros((0, 4)),
+                          1e-3, None, on)
+    with pytest.raises(P.PhcError):
+        P.phc_track_paths(hb, total, 1, None, e, c)  # beyond the last path
+    torch.cuda.synchronize()
