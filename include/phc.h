@@ -232,6 +232,30 @@ int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const 
 int phc_track_paths_dd(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_hi,
                        phc_cd *x_lo, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
 
+/* The Cauchy endgame for singular endpoints (the paper distinguishes
+ * isolated multiple solutions from regular ones, Section 4; Example 4.1's
+ * point (2, 0) has multiplicity two).  A path converging to a singular
+ * endpoint x* has near t = 1 an expansion x(s) = x* + sum_k a_k s^{k/c} in
+ * s = 1 - t, c its cycle number; double precision Newton steps at t = 1
+ * leave x* accurate to about 1e-8 only.  For each total-degree path
+ * first_path .. first_path + n_paths - 1 the call tracks the path to
+ * t = 0.99 (the tracker's predictor, corrector and step control; the step
+ * clamped to land on 0.99), then around the circle 1 - t = 0.01 e^{i theta}
+ * in complex t, sampling x at 16 angles per loop, until the path closes
+ * (||x - x_start|| <= 1e-8 (1 + ||x_start||)) after c <= 8 loops.  The
+ * estimate is the mean of the 16 c samples (Cauchy's integral formula in
+ * s^{1/c}); it counts when its relative residual
+ * max_i |H_i(x, 1)|_1 / (1 + scale_i) is <= 1e-10 (a path that runs to
+ * infinity also closes, around a pole, and is rejected here).
+ * Outputs (device): x_out SoA [n_var][n_paths] (the estimate, or the last
+ * point when there is none), cycle_out [n_paths] int32 (c, 0 when there is
+ * no estimate), stats_out [n_paths] or NULL (steps, Newton steps, relres of
+ * the estimate, stop as phc_track_paths for a path that stopped before 0.99
+ * or failed on the circle).  Total-degree and batch handles.
+ * Errors: as phc_track_paths. */
+int phc_endgame(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_out,
+                int32_t *cycle_out, phc_path_stats *stats_out, void *cuda_stream);
+
 /* The embedded system E_D of Section 2.1 (eq. (2) for D = 1): unknowns
  * x_1..x_n, z_1..z_D; equation i is f_i(x) + sum_k gammas[i][k] z_k; equation
  * n_eq + k is hyper[k][0] + sum_j hyper[k][j+1] x_j + z_k.  A square f only

@@ -220,6 +220,25 @@ def track_dd(h: Homotopy, starts: np.ndarray | None = None, first: int = 0, n_pa
     return xh, xl, cls, stats
 
 
+def endgame(h: Homotopy, first: int = 0, n_paths: int | None = None, opts: Opts | None = None):
+    """Cauchy endgame (reading in phc_oracle.c): per total-degree path the
+    cycle number c (0: no estimate) and the mean of the samples of x over c
+    loops around t = 1 (the estimate of the endpoint).  Returns (x [P, n],
+    cycle [P], stats)."""
+    if n_paths is None:
+        n_paths = num_paths(h) - first
+    x = np.zeros((n_paths, h.n), dtype=np.complex128)
+    cyc = np.zeros(n_paths, dtype=np.int32)
+    stats = np.zeros(n_paths, dtype=STATS_DTYPE)
+    o = opts if opts is not None else default_opts()
+    rc = lib().orc_endgame(h.ref(), ctypes.c_int64(first), ctypes.c_int64(n_paths), ctypes.byref(o),
+                           x.view(np.float64).ctypes.data_as(ctypes.c_void_p), cyc.ctypes.data_as(ctypes.c_void_p),
+                           stats.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError(f"orc_endgame failed: {rc}")
+    return x, cyc, stats
+
+
 def refine(h: Homotopy, x: np.ndarray, cls: np.ndarray, cond: np.ndarray, reached: np.ndarray,
            cond_threshold: float = 1e6, cond_max: float = 1e12, max_iters: int = 8):
     """Double double Newton refinement at t = 1 of the ill-conditioned

@@ -856,6 +856,230 @@ int orc_refine(const orc_homotopy *h, double *x_hi, double *x_lo, int64_t n_path
     return 0;
 }
 
+/* ================================================================ Cauchy endgame
+ * A path that converges to a singular endpoint x* of a total-degree
+ * homotopy has near t = 1 an expansion x(s) = x* + sum_k a_k s^{k/c} in
+ * s = 1 - t, c the cycle number.  The endgame tracks the path to
+ * t0 = 1 - EG_RADIUS, then around the circle s = EG_RADIUS e^{i theta}
+ * (complex t) until the path closes up after c loops, sampling x at
+ * EG_SAMPLES equally spaced angles per loop; by Cauchy's integral formula
+ * in the variable s^{1/c} the mean of the c * EG_SAMPLES samples is x*
+ * (the trapezoidal rule, exact up to terms of order EG_RADIUS^EG_SAMPLES).
+ * A path that runs to infinity closes up too (a pole in s), but the mean of
+ * its samples is no root, so an estimate counts only when its relative
+ * residual (end_measures) is at most EG_RES. */
+
+#define EG_RADIUS 0.01
+#define EG_SAMPLES 16
+#define EG_MAX_CYCLES 8
+#define EG_CLOSE_TOL 1e-8
+#define EG_RES 1e-10
+
+/* H, H_x, H_t of the total-degree homotopy at a complex t (as eval_homotopy). */
+static void eval_homotopy_ct(const orc_homotopy *h, const cplx *x, cplx t, cplx *H, cplx *Hx, cplx *Ht)
+{
+    const int n = h->n;
+    const cplx gamma = h->gamma_re + I * h->gamma_im;
+    int off = 0;
+    for (int i = 0; i < n; i++) {
+        cplx f = 0.0, ft = 0.0;
+        for (int j = 0; j < n; j++) Hx[i * n + j] = 0.0;
+        for (int k = 0; k < h->terms_per_eq[i]; k++) {
+            const uint8_t *a = h->exps + (size_t)(off + k) * n;
+            cplx c = coef_of(h, off + k);
+            cplx m = monomial(n, a, x);
+            f += t * c * m;
+            ft += c * m;
+            for (int j = 0; j < n; j++) Hx[i * n + j] += t * c * monomial_dx(n, a, x, j);
+        }
+        int d = eq_degree(h, i, off);
+        cplx g = ipow(x[i], d) - 1.0;
+        cplx w = (1.0 - t) * gamma;
+        f += w * g;
+        ft -= gamma * g;
+        Hx[i * n + i] += w * (double)d * ipow(x[i], d - 1);
+        H[i] = f;
+        Ht[i] = ft;
+        off += h->terms_per_eq[i];
+    }
+}
+
+/* dx/dtheta at (x, theta) on the circle t = 1 - r e^{i theta}:
+ * -H_x^{-1} H_t dt/dtheta, dt/dtheta = -i r e^{i theta}. */
+static int tangent_theta(const orc_homotopy *h, const cplx *x, double r, double th, cplx *v, orc_stats *st)
+{
+    cplx H[NMAX], Hx[NMAX * NMAX];
+    int piv[NMAX];
+    const cplx e = cos(th) + I * sin(th);
+    eval_homotopy_ct(h, x, 1.0 - r * e, H, Hx, v);
+    st->n_solve++;
+    if (lu_factor(h->n, Hx, piv)) return -1;
+    lu_solve(h->n, Hx, piv, v);
+    const cplx dt = -I * r * e;
+    for (int j = 0; j < h->n; j++) v[j] = -v[j] * dt;
+    return 0;
+}
+
+static double newton_theta(const orc_homotopy *h, cplx *x, double r, double th, orc_stats *st)
+{
+    cplx H[NMAX], Hx[NMAX * NMAX], Ht[NMAX];
+    int piv[NMAX];
+    const cplx e = cos(th) + I * sin(th);
+    eval_homotopy_ct(h, x, 1.0 - r * e, H, Hx, Ht);
+    st->n_solve++;
+    st->n_newton++;
+    if (lu_factor(h->n, Hx, piv)) return NAN;
+    lu_solve(h->n, Hx, piv, H);
+    for (int j = 0; j < h->n; j++) x[j] -= H[j];
+    return vnorm(h->n, H);
+}
+
+/* Tracks x from t = 0 to t0 = 1 - EG_RADIUS with the tracker's readings
+ * (track_one, the step clamped to land on t0), then around the circle.
+ * Returns the cycle number (0 when the path stopped before t0 or did not
+ * close within EG_MAX_CYCLES loops); x holds the Cauchy estimate of the
+ * endpoint (or the last point). */
+static int endgame_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_stats *st)
+{
+    const int n = h->n;
+    const double t0 = 1.0 - EG_RADIUS;
+    cplx x0[NMAX], xs[NMAX], k1[NMAX], k2[NMAX], k3[NMAX], k4[NMAX];
+    double t = 0.0, step = o->h_init;
+    int streak = 0, steps = 0;
+    memset(st, 0, sizeof *st);
+    /* ---- to t0 */
+    while (t < t0) {
+        double he = step;
+        double t1 = t + he;
+        if (he >= t0 - t) { he = t0 - t; t1 = t0; }
+        memcpy(x0, x, sizeof(cplx) * n);
+        int ok = 1;
+        ok = ok && !tangent(h, x0, t, k1, st);
+        for (int j = 0; j < n; j++) xs[j] = x0[j] + (0.5 * he) * k1[j];
+        ok = ok && !tangent(h, xs, t + 0.5 * he, k2, st);
+        for (int j = 0; j < n; j++) xs[j] = x0[j] + (0.5 * he) * k2[j];
+        ok = ok && !tangent(h, xs, t + 0.5 * he, k3, st);
+        for (int j = 0; j < n; j++) xs[j] = x0[j] + he * k3[j];
+        ok = ok && !tangent(h, xs, t1, k4, st);
+        if (ok)
+            for (int j = 0; j < n; j++) x[j] = x0[j] + (he / 6.0) * (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]);
+        int conv = 0;
+        double prev = INFINITY;
+        for (int it = 0; ok && it < o->max_corr_iters; it++) {
+            double d = newton_step(h, x, t1, st);
+            if (!(d == d) || !all_finite(n, x)) break;
+            if (d <= o->corr_tol * (1.0 + vnorm(n, x))) { conv = 1; break; }
+            if (it > 0 && d > o->corr_contract * prev) break;
+            prev = d;
+        }
+        steps++;
+        if (conv) {
+            t = t1;
+            st->n_accept++;
+            if (vnorm(n, x) > o->diverge_norm) { st->stop = 1; break; }
+            if (++streak >= o->expand_after) {
+                streak = 0;
+                step = step * o->expand;
+                if (step > o->h_max) step = o->h_max;
+            }
+        } else {
+            memcpy(x, x0, sizeof(cplx) * n);
+            st->n_reject++;
+            streak = 0;
+            step = he * o->shrink;
+            if (step < o->h_min) { st->stop = 2; break; }
+        }
+        if (steps >= o->max_steps) { st->stop = 3; break; }
+    }
+    st->t = t;
+    if (st->stop != 0 || t < t0) return 0;
+    /* ---- around the circle s = r e^{i theta} */
+    const double r = EG_RADIUS, dth = 2.0 * M_PI / EG_SAMPLES, hmin = dth * 9.5367431640625e-07; /* 2^-20 */
+    cplx start[NMAX], sum[NMAX];
+    memcpy(start, x, sizeof(cplx) * n);
+    for (int j = 0; j < n; j++) sum[j] = 0.0;
+    double th = 0.0, hth = dth;
+    streak = 0;
+    for (int sample = 1; sample <= EG_SAMPLES * EG_MAX_CYCLES; sample++) {
+        for (int j = 0; j < n; j++) sum[j] += x[j];
+        const double target = sample * dth;
+        while (th < target) {
+            double he = hth;
+            double t1 = th + he;
+            if (he >= target - th) { he = target - th; t1 = target; }
+            memcpy(x0, x, sizeof(cplx) * n);
+            int ok = 1;
+            ok = ok && !tangent_theta(h, x0, r, th, k1, st);
+            for (int j = 0; j < n; j++) xs[j] = x0[j] + (0.5 * he) * k1[j];
+            ok = ok && !tangent_theta(h, xs, r, th + 0.5 * he, k2, st);
+            for (int j = 0; j < n; j++) xs[j] = x0[j] + (0.5 * he) * k2[j];
+            ok = ok && !tangent_theta(h, xs, r, th + 0.5 * he, k3, st);
+            for (int j = 0; j < n; j++) xs[j] = x0[j] + he * k3[j];
+            ok = ok && !tangent_theta(h, xs, r, t1, k4, st);
+            if (ok)
+                for (int j = 0; j < n; j++) x[j] = x0[j] + (he / 6.0) * (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]);
+            int conv = 0;
+            double prev = INFINITY;
+            for (int it = 0; ok && it < o->max_corr_iters; it++) {
+                double d = newton_theta(h, x, r, t1, st);
+                if (!(d == d) || !all_finite(n, x)) break;
+                if (d <= o->corr_tol * (1.0 + vnorm(n, x))) { conv = 1; break; }
+                if (it > 0 && d > o->corr_contract * prev) break;
+                prev = d;
+            }
+            if (conv) {
+                th = t1;
+                st->n_accept++;
+                if (++streak >= o->expand_after) {
+                    streak = 0;
+                    hth = hth * o->expand;
+                    if (hth > dth) hth = dth;
+                }
+            } else {
+                memcpy(x, x0, sizeof(cplx) * n);
+                st->n_reject++;
+                streak = 0;
+                hth = he * o->shrink;
+                if (hth < hmin) { st->stop = 2; return 0; }
+            }
+        }
+        if (sample % EG_SAMPLES == 0) {
+            cplx dx[NMAX];
+            for (int j = 0; j < n; j++) dx[j] = x[j] - start[j];
+            if (vnorm(n, dx) <= EG_CLOSE_TOL * (1.0 + vnorm(n, start))) {
+                const int c = sample / EG_SAMPLES;
+                for (int j = 0; j < n; j++) x[j] = sum[j] / (double)sample;
+                st->t = 1.0;
+                st->norm_x = vnorm(n, x);
+                end_measures(h, x, &st->cond, &st->relres);
+                return st->relres <= EG_RES ? c : 0;
+            }
+        }
+    }
+    return 0;
+}
+
+/* Exported: the Cauchy endgame of the total-degree paths first..first+n-1,
+ * one thread (x_out [n][dim][2]; cycle_out [n], 0 = no estimate). */
+int orc_endgame(const orc_homotopy *h, int64_t first, int64_t n_paths, const orc_opts *o_in, double *x_out,
+                int32_t *cycle_out, orc_stats *stats_out)
+{
+    orc_opts o;
+    if (o_in) o = *o_in; else orc_default_opts(&o);
+    if (h->kind != 0 || h->n < 1 || h->n > NMAX) return -1;
+    const int n = h->n;
+    cplx x[NMAX];
+    orc_stats st;
+    for (int64_t q = 0; q < n_paths; q++) {
+        start_solution(h, first + q, x);
+        const int c = endgame_one(h, &o, x, &st);
+        for (int j = 0; j < n; j++) { x_out[(q * n + j) * 2] = creal(x[j]); x_out[(q * n + j) * 2 + 1] = cimag(x[j]); }
+        cycle_out[q] = c;
+        if (stats_out) stats_out[q] = st;
+    }
+    return 0;
+}
+
 /* ================================================================ double double path tracking
  * Section 5 and Table 2 run the whole solver in double double arithmetic
  * ("quality up").  Here a path is tracked with the readings of track_one

@@ -32,7 +32,7 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
                    phc_tail_paths, phc_track_many, phc_track_paths_noalloc, phc_track_pipeline,
                    phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square,
-                   phc_many_plan_create, phc_many_plan_run, ManyPlan, phc_track_paths_dd)
+                   phc_many_plan_create, phc_many_plan_run, ManyPlan, phc_track_paths_dd, phc_endgame)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -44,7 +44,7 @@ __all__ = [
     "Tracked", "pipeline", "track", "cascade", "refine",
     "stats_numpy", "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
     "track_from", "membership", "phc_square", "phc_many_plan_create", "phc_many_plan_run", "ManyPlan",
-    "phc_track_paths_dd", "track_dd",
+    "phc_track_paths_dd", "track_dd", "phc_endgame", "endgame",
 ]
 
 
@@ -116,6 +116,19 @@ def track_dd(h: Homotopy, first: int = 0, n_paths: int | None = None, opts=None,
     xlo = torch.empty_like(x)
     phc_track_paths_dd(h, first, n_paths, opts, x, xlo, cls, st, stream)
     return Tracked(x, cls, st), xlo
+
+
+def endgame(h: Homotopy, first: int = 0, n_paths: int | None = None, opts=None, stream=None, device="cuda"):
+    """Cauchy endgame of total-degree paths; returns (Tracked with the
+    estimates in x (cls unused: -1), cycle numbers [P] int32)."""
+    import torch
+    if n_paths is None:
+        n_paths = phc_num_paths(h) - first
+    x, cls, st = _alloc(h.n, n_paths, device)
+    cls.fill_(-1)
+    cyc = torch.empty(n_paths, dtype=torch.int32, device=device)
+    phc_endgame(h, first, n_paths, opts, x, cyc, st, stream)
+    return Tracked(x, cls, st), cyc
 
 
 def cascade(h_k: Homotopy, k: int, starts, opts=None, stream=None) -> Tracked:

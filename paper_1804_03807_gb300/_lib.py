@@ -95,6 +95,7 @@ def load() -> ctypes.CDLL:
     L.phc_embed.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_track_paths_dd.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
+    L.phc_endgame.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_many_plan_create.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp, ctypes.POINTER(vp)]
     L.phc_many_plan_run.argtypes = [vp, vp]
     L.phc_many_plan_destroy.argtypes = [vp]
@@ -122,7 +123,7 @@ def load() -> ctypes.CDLL:
                  "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats",
                  "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
-                 "phc_square", "phc_many_plan_create", "phc_many_plan_run", "phc_track_paths_dd"):
+                 "phc_square", "phc_many_plan_create", "phc_many_plan_run", "phc_track_paths_dd", "phc_endgame"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
         raise ImportError("phc_opts layout mismatch between phc.h and the binding")
@@ -276,6 +277,13 @@ def phc_track_paths_dd(h: Homotopy, first_path: int, n_paths: int, opts, x_hi, x
     _check(load().phc_track_paths_dd(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
                                      ctypes.byref(opts) if opts is not None else None, _ptr(x_hi), _ptr(x_lo),
                                      _ptr(cls_out), _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_endgame(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cycle_out, stats_out=None, stream=None):
+    """Cauchy endgame: x_out complex128 [n_var, n_paths], cycle_out int32 [n_paths]."""
+    _check(load().phc_endgame(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
+                              ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cycle_out),
+                              _ptr(stats_out), _stream_ptr(stream)))
 
 
 def phc_track_paths_noalloc(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls_out, stats_out=None,
