@@ -61,6 +61,7 @@ class _Hom(ctypes.Structure):
         ("terms_per_eq", ctypes.c_void_p), ("exps", ctypes.c_void_p), ("coefs", ctypes.c_void_p),
         ("gamma_re", ctypes.c_double), ("gamma_im", ctypes.c_double),
         ("row", ctypes.c_int32), ("slack", ctypes.c_int32), ("coefs0", ctypes.c_void_p),
+        ("powers", ctypes.c_void_p),
     ]
 
 
@@ -108,7 +109,7 @@ class Homotopy:
     """Keeps the numpy buffers alive behind the C struct."""
 
     def __init__(self, sys: PolySystem, kind: int, gamma: complex = 1.0, row: int = -1, slack: int = -1,
-                 coefs0=None):
+                 coefs0=None, powers=None):
         assert sys.n_eq == sys.n_var, "the tracker needs a square system"
         self.sys = sys
         self.n = sys.n_var
@@ -120,9 +121,14 @@ class Homotopy:
             c0 = np.asarray(coefs0, dtype=np.complex128).reshape(-1)
             assert c0.shape[0] == sys.n_terms, "start coefficients must match the target's terms"
             self._coefs0 = np.ascontiguousarray(np.stack([c0.real, c0.imag], axis=1), dtype=np.float64)
+        self._powers = None
+        if powers is not None:
+            self._powers = np.ascontiguousarray(powers, dtype=np.float64).reshape(-1)
+            assert self._powers.shape[0] == sys.n_terms, "one power of t per term"
         self.c = _Hom(kind, self.n, sys.n_terms, self._tpe.ctypes.data, self._exps.ctypes.data,
                       self._coefs.ctypes.data, float(np.real(gamma)), float(np.imag(gamma)), row, slack,
-                      None if self._coefs0 is None else self._coefs0.ctypes.data)
+                      None if self._coefs0 is None else self._coefs0.ctypes.data,
+                      None if self._powers is None else self._powers.ctypes.data)
 
     def ref(self):
         return ctypes.byref(self.c)
@@ -139,6 +145,14 @@ def parameter_homotopy(target: PolySystem, start_coefs, gamma: complex) -> Homot
     of a random coefficient system start the paths to the target).  Paths
     start from explicit solutions of g (track(..., starts=...))."""
     return Homotopy(target, 2, gamma, coefs0=start_coefs)
+
+
+def polyhedral_homotopy(sys: PolySystem, powers) -> Homotopy:
+    """The polyhedral homotopy of one mixed cell (Section 2.2): term q of
+    sys carries the factor t^{powers[q]} (0 on the cell's terms); paths start
+    from the cell's binomial solutions (oracle.mixed.binomial_starts) and end
+    at solutions of sys."""
+    return Homotopy(sys, 3, 1.0, powers=powers)
 
 
 def end_measures(h: Homotopy, x: np.ndarray):

@@ -106,7 +106,11 @@ enum { ORC_REGULAR = 0, ORC_SINGULAR = 1, ORC_AT_INFINITY = 2, ORC_FAILED = 3 };
  * `slack` is z_k.  kind 2: coefficient-parameter homotopy
  * (1-t) gamma g(x) + t f(x) where g has the supports of f and the
  * coefficients coefs0 (Section 2.3: the solutions of a random coefficient
- * system start the paths to the target system). */
+ * system start the paths to the target system).  kind 3: polyhedral
+ * homotopy of one mixed cell (Section 2.2): the term c x^a of f carries
+ * the factor t^{p}, p = powers[term] (0 on the cell's two terms per
+ * equation, >= 1 elsewhere), so at t = 0 only the cell's binomial system
+ * remains and at t = 1 the system is f. */
 typedef struct {
     int32_t kind;
     int32_t n;
@@ -117,6 +121,7 @@ typedef struct {
     double gamma_re, gamma_im;   /* kinds 0 and 2        */
     int32_t row, slack;          /* kind 1               */
     const double *coefs0;        /* kind 2: [n_terms][2] coefficients of g */
+    const double *powers;        /* kind 3: [n_terms] power of t per term  */
 } orc_homotopy;
 
 typedef struct {
@@ -224,6 +229,19 @@ static void eval_homotopy(const orc_homotopy *h, const cplx *x, double t, cplx *
                 const cplx c0 = h->coefs0[2 * (off + k)] + I * h->coefs0[2 * (off + k) + 1];
                 ct = (1.0 - t) * gamma * c0 + t * c;
                 dct = c - gamma * c0;
+            } else if (h->kind == 3) {
+                /* c t^p and d/dt = c p t^{p-1}, with 0^0 = 1; p >= 1 when p != 0 */
+                const double p = h->powers[off + k];
+                if (p == 0.0) {
+                    ct = c;
+                    dct = 0.0;
+                } else if (t == 0.0) {
+                    ct = 0.0;
+                    dct = p == 1.0 ? c : 0.0;
+                } else {
+                    ct = c * pow(t, p);
+                    dct = c * (p * pow(t, p - 1.0));
+                }
             } else if (i == h->row && !is_unit(a, n, h->slack)) {
                 ct = (1.0 - t) * c;
                 dct = -c;
@@ -1351,6 +1369,7 @@ int orc_track_dd(const orc_homotopy *h, const double *starts, int64_t first, int
     if (o_in) o = *o_in; else orc_default_opts(&o);
     if (h->n < 1 || h->n > NMAX || n_paths < 0) return -1;
     if (!starts && h->kind != 0) return -1;
+    if (h->kind == 3) return -1; /* double double tracking covers kinds 0..2 */
     crew_dd_t c;
     c.h = h; c.o = &o; c.starts = starts; c.first = first; c.n_paths = n_paths;
     c.x_hi = x_hi; c.x_lo = x_lo; c.cls_out = cls_out; c.stats_out = stats_out;

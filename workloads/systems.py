@@ -92,6 +92,12 @@ def unit_gamma(rng: np.random.Generator) -> complex:
     return complex(np.cos(theta), np.sin(theta))
 
 
+def random_lifting(rng: np.random.Generator, n_terms: int, bits: int = 20) -> np.ndarray:
+    """Integer lifting values for the mixed cells of polyhedral homotopies
+    (Section 2.2): one uniform integer in [0, 2^bits) per term."""
+    return rng.integers(0, 1 << bits, n_terms).astype(np.int32)
+
+
 def embedding_constants(rng: np.random.Generator, n_eq: int, n_var: int, top_dim: int):
     """Random constants of the embedding E_D (Section 2.1, eq. (2)).
 
