@@ -475,6 +475,100 @@ int phc_refine_endpoints(const phc_homotopy *h, phc_cd *x_hi_io, phc_cd *x_lo_ou
 int phc_track_paths_noalloc(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts,
                             phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
 
+/* ---------------------------------------------------------------- polyhedral homotopies */
+
+/* Fine mixed cells of the Newton polytopes of a square system under an
+ * integer lifting (Section 2.2: polyhedral homotopies solve a random
+ * coefficient start system, one binomial start system per mixed cell, a cell
+ * of volume V starting V paths; Figure 2 pipelines the making of the cells
+ * with the tracking).  Host call, no device work.  Supports: the exponents
+ * of each equation's terms (terms_per_eq [n], exps [T][n] as in
+ * phc_make_homotopy; an equation may not list a monomial twice).
+ * lift [T]: one integer per term in 0..2^20 (random values put the lifting
+ * in general position).  A fine mixed cell picks two terms a_i < b_i
+ * (global term indices) of every equation i such that some v in Q^n makes
+ * <exps[a], v> + lift[a] equal on the pair and larger on every other term
+ * of equation i; its volume is |det D|, D the n x n matrix with rows
+ * exps[b_i] - exps[a_i].  The mixed volume (the sum of the volumes) counts
+ * the isolated roots in (C*)^n of a system with these supports and
+ * coefficients in general position (Bernstein).
+ * Outputs: *n_cells_out (every cell) and *mixed_volume_out (may be NULL);
+ * the first min(n_cells, max_cells) cells to cells_out [max_cells][n][2]
+ * (a_i, b_i per equation) and their volumes to volumes_out [max_cells] (may
+ * be NULL), in the order found (max_cells = 0 counts only).
+ * Errors: PHC_EINVAL for n outside 1..PHC_MAX_VARS, NULL lists, an equation
+ * without terms or with a repeated monomial, lifting values outside
+ * 0..2^20, or a lifting not in general position (a third term on a cell's
+ * lower facet: draw another lifting); PHC_EUNSUPPORTED when the exact
+ * arithmetic would overflow 128 bits. */
+int phc_mixed_cells(int n, const int32_t *terms_per_eq, const uint8_t *exps, const int32_t *lift,
+                    int64_t max_cells, int32_t *cells_out, int64_t *volumes_out, int64_t *n_cells_out,
+                    int64_t *mixed_volume_out);
+
+/* The polyhedral homotopies of a system g with coefficients in general
+ * position (host lists terms_per_eq, exps, coefs as in phc_make_homotopy)
+ * over cells of phc_mixed_cells (host cells [n_cells][n][2], the same
+ * lift [T]).  Cell k substitutes x = t^{v_k} y and divides equation i by
+ * t^{beta_i}: term c x^a becomes c y^a t^e, e = <a, v_k> + lift(a) - beta_i
+ * (0 on the cell's terms, > 0 on the others), every e divided by the cell's
+ * smallest positive one (a change of the parameter: the same paths, and a
+ * t-derivative bounded at t = 0).  At t = 0 the cell's binomial system
+ * c_{a_i} y^{a_i} + c_{b_i} y^{b_i} = 0 remains, with |det D| solutions; at
+ * t = 1 every cell's homotopy is g, and the paths of all cells end at the
+ * isolated roots of g in (C*)^n.  phc_num_paths reports the sum of the
+ * volumes; paths are numbered cell by cell in the given order.  Only
+ * phc_polyhedral_starts, phc_track_polyhedral, phc_refine_endpoints and
+ * phc_num_paths accept the handle.
+ * Errors: as phc_make_homotopy; PHC_EINVAL for n_cells < 1, a NULL cell
+ * list, a cell that is not a fine mixed cell of this lifting, or a zero
+ * coefficient on a cell's term; PHC_EUNSUPPORTED when a cell's exact data
+ * overflow. */
+int phc_make_polyhedral_homotopy(int n, const int32_t *terms_per_eq, const uint8_t *exps, const phc_cd *coefs,
+                                 const int32_t *lift, const int32_t *cells, int64_t n_cells, phc_homotopy **out);
+
+/* Start solutions of paths first_path .. first_path+n_paths-1 of a
+ * polyhedral handle to x_out (device SoA [n][n_paths]): the solutions of
+ * the cell's binomial system y^D = beta, beta_i = -c_{a_i} / c_{b_i}, from
+ * the Hermite form U D = H (U unimodular, H upper triangular with a positive
+ * diagonal): log y_k = (sum_j U_kj log beta_j - sum_{l>k} H_kl log y_l
+ * + 2 pi i r_k) / H_kk for k = n-1 .. 0, with r_k the digits of the path's
+ * index within its cell in the radices H_00 .. H_(n-1)(n-1) (r_0 fastest).
+ * Errors: PHC_EINVAL for a handle of another kind, a range outside the
+ * paths or a NULL x_out; PHC_ECUDA. */
+int phc_polyhedral_starts(const phc_homotopy *h, int64_t first_path, int64_t n_paths, phc_cd *x_out,
+                          void *cuda_stream);
+
+/* Track paths first_path .. first_path+n_paths-1 of a polyhedral handle from
+ * their start solutions at t = 0 to t = 1, with the readings of
+ * phc_track_paths (RK4 predictor, Newton corrector, step control, end Newton
+ * at t = 1, classification against g), one thread per path; outputs as
+ * phc_track_paths (x_out SoA [n][n_paths], cls_out, stats_out or NULL).  No
+ * tail hand-off and no compaction (tail_drain and compact do not apply).
+ * Errors: as phc_track_paths; PHC_EINVAL for a handle of another kind. */
+int phc_track_polyhedral(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts,
+                         phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
+
+/* Solve a system g with coefficients in general position by polyhedral
+ * homotopies in the two-stage pipeline of Section 2.2 (Figure 2): the calling
+ * thread makes the mixed cells one after the other (as phc_mixed_cells with
+ * lift) while the GPU already tracks the paths of the cells made so far
+ * (batches of cells of growing size, launched as they are made on helper
+ * streams with the priority of cuda_stream); the endpoints are classified
+ * against g at the end.  Outputs (device): x_out SoA [n][max_paths], cls_out
+ * [max_paths], stats_out [max_paths] or NULL; paths are numbered cell by
+ * cell in the order the cells were made (the order phc_mixed_cells
+ * reports), so the results equal those of phc_track_polyhedral on a handle
+ * over those cells.  *n_paths_out: the mixed volume; *n_cells_out (may be
+ * NULL): the number of cells.  Host call: returns once the work on
+ * cuda_stream has finished.
+ * Errors: as phc_mixed_cells and phc_make_polyhedral_homotopy; PHC_EINVAL
+ * when the mixed volume exceeds max_paths (*n_paths_out still reports it;
+ * the outputs are then incomplete); PHC_ENOMEM; PHC_ECUDA. */
+int phc_solve_polyhedral(int n, const int32_t *terms_per_eq, const uint8_t *exps, const phc_cd *coefs,
+                         const int32_t *lift, const phc_opts *opts, int64_t max_paths, phc_cd *x_out,
+                         int8_t *cls_out, phc_path_stats *stats_out, int64_t *n_paths_out, int64_t *n_cells_out,
+                         void *cuda_stream);
+
 /* Message of the last non-OK return on the calling thread ("" if none). */
 const char *phc_last_error(void);
 

@@ -32,7 +32,9 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    phc_num_paths, phc_opts, phc_refine_endpoints, phc_track_paths,
                    phc_tail_paths, phc_track_many, phc_track_paths_noalloc, phc_track_pipeline,
                    phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square,
-                   phc_many_plan_create, phc_many_plan_run, ManyPlan, phc_track_paths_dd, phc_endgame)
+                   phc_many_plan_create, phc_many_plan_run, ManyPlan, phc_track_paths_dd, phc_endgame,
+                   phc_mixed_cells, phc_make_polyhedral_homotopy, phc_polyhedral_starts, phc_track_polyhedral,
+                   phc_solve_polyhedral)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -45,6 +47,8 @@ __all__ = [
     "stats_numpy", "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
     "track_from", "membership", "phc_square", "phc_many_plan_create", "phc_many_plan_run", "ManyPlan",
     "phc_track_paths_dd", "track_dd", "phc_endgame", "endgame",
+    "phc_mixed_cells", "phc_make_polyhedral_homotopy", "phc_polyhedral_starts", "phc_track_polyhedral",
+    "phc_solve_polyhedral", "polyhedral_starts", "track_polyhedral", "solve_polyhedral",
 ]
 
 
@@ -182,3 +186,33 @@ def refine(h: Homotopy, r: Tracked, cond_threshold: float = 1e6, cond_max: float
     phc_refine_endpoints(h, r.x, x_lo, int(r.x.shape[1]), cond_threshold, cond_max, max_iters, r.cls, r.stats,
                          stream)
     return x_lo
+
+
+def polyhedral_starts(h: Homotopy, first: int = 0, n_paths: int | None = None, stream=None, device="cuda"):
+    """Start solutions of a polyhedral handle's paths: complex128 [n_var, P]."""
+    import torch
+    if n_paths is None:
+        n_paths = phc_num_paths(h) - first
+    x = torch.zeros((h.n, max(n_paths, 1)), dtype=torch.complex128, device=device)
+    phc_polyhedral_starts(h, first, n_paths, x, stream)
+    return x[:, :n_paths]
+
+
+def track_polyhedral(h: Homotopy, first: int = 0, n_paths: int | None = None, opts=None, stream=None,
+                     device="cuda") -> Tracked:
+    """Track the paths of a polyhedral handle (every cell's binomial solutions
+    to the roots of its system)."""
+    if n_paths is None:
+        n_paths = phc_num_paths(h) - first
+    x, cls, st = _alloc(h.n, n_paths, device)
+    phc_track_polyhedral(h, first, n_paths, opts, x, cls, st, stream)
+    return Tracked(x, cls, st)
+
+
+def solve_polyhedral(sys, lift, max_paths: int, opts=None, stream=None, device="cuda") -> Tracked:
+    """The pipelined polyhedral solver (cells made on this thread while the
+    GPU tracks): Tracked outputs of the mixed volume's paths, cells in the
+    order they were made."""
+    x, cls, st = _alloc(sys.n_var, max(max_paths, 1), device)
+    mv, _ = phc_solve_polyhedral(sys, lift, opts, max_paths, x, cls, st, stream)
+    return Tracked(x[:, :mv], cls[:mv], st[:mv])

@@ -112,6 +112,12 @@ def load() -> ctypes.CDLL:
     L.phc_track_from.argtypes = [vp, vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_membership_test.argtypes = [i32, i32, vp, vp, vp, i32, vp, i64, vp, i64, ctypes.c_double,
                                       ctypes.POINTER(phc_opts), vp, vp, vp, vp]
+    L.phc_mixed_cells.argtypes = [i32, vp, vp, vp, i64, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.phc_make_polyhedral_homotopy.argtypes = [i32, vp, vp, vp, vp, vp, i64, ctypes.POINTER(vp)]
+    L.phc_polyhedral_starts.argtypes = [vp, i64, i64, vp, vp]
+    L.phc_track_polyhedral.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
+    L.phc_solve_polyhedral.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(phc_opts), i64, vp, vp, vp,
+                                       ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
     L.phc_last_error.restype = ctypes.c_char_p
     L.phc_destroy_homotopy.argtypes = [vp]
     L.phc_destroy_homotopy.restype = None
@@ -123,7 +129,9 @@ def load() -> ctypes.CDLL:
                  "phc_embed",
                  "phc_cascade_stage", "phc_refine_endpoints", "phc_sizeof_opts", "phc_sizeof_stats",
                  "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
-                 "phc_square", "phc_many_plan_create", "phc_many_plan_run", "phc_track_paths_dd", "phc_endgame"):
+                 "phc_square", "phc_many_plan_create", "phc_many_plan_run", "phc_track_paths_dd", "phc_endgame",
+                 "phc_mixed_cells", "phc_make_polyhedral_homotopy", "phc_polyhedral_starts",
+                 "phc_track_polyhedral", "phc_solve_polyhedral"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
         raise ImportError("phc_opts layout mismatch between phc.h and the binding")
@@ -221,6 +229,63 @@ def phc_make_parameter_homotopy(target, start_coefs, gamma: complex = 1.0) -> Ho
                                          exps.ctypes.data, len(systems), cs.ctypes.data, ct.ctypes.data,
                                          phc_cd(float(np.real(gamma)), float(np.imag(gamma))), ctypes.byref(out)))
     return Homotopy(out.value, int(systems[0].n_var))
+
+
+def phc_mixed_cells(sys, lift):
+    """Fine mixed cells of the supports of ``sys`` under the integer lifting
+    ``lift`` [T] (host call): (cells int32 [n_cells, n, 2] of global term
+    indices, volumes int64 [n_cells], mixed volume)."""
+    L = load()
+    tpe, exps, _ = _lists(sys)
+    w = np.ascontiguousarray(np.asarray(lift).reshape(-1), dtype=np.int32)
+    n = int(sys.n_var)
+    count, mv = ctypes.c_int64(), ctypes.c_int64()
+    _check(L.phc_mixed_cells(n, tpe.ctypes.data, exps.ctypes.data, w.ctypes.data, 0, None, None, ctypes.byref(count),
+                             ctypes.byref(mv)))
+    cells = np.zeros((max(count.value, 1), n, 2), dtype=np.int32)
+    vols = np.zeros(max(count.value, 1), dtype=np.int64)
+    _check(L.phc_mixed_cells(n, tpe.ctypes.data, exps.ctypes.data, w.ctypes.data, int(cells.shape[0]),
+                             cells.ctypes.data, vols.ctypes.data, ctypes.byref(count), ctypes.byref(mv)))
+    return cells[:count.value], vols[:count.value], int(mv.value)
+
+
+def phc_make_polyhedral_homotopy(sys, lift, cells) -> Homotopy:
+    """Polyhedral homotopies of ``sys`` (coefficients in general position)
+    over ``cells`` (int32 [n_cells, n, 2] from phc_mixed_cells, same lift)."""
+    L = load()
+    tpe, exps, coefs = _lists(sys)
+    w = np.ascontiguousarray(np.asarray(lift).reshape(-1), dtype=np.int32)
+    c = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+    out = ctypes.c_void_p()
+    _check(L.phc_make_polyhedral_homotopy(int(sys.n_var), tpe.ctypes.data, exps.ctypes.data, coefs.ctypes.data,
+                                          w.ctypes.data, c.ctypes.data, int(c.shape[0]), ctypes.byref(out)))
+    return Homotopy(out.value, int(sys.n_var))
+
+
+def phc_polyhedral_starts(h: Homotopy, first_path: int, n_paths: int, x_out, stream=None):
+    _check(load().phc_polyhedral_starts(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths), _ptr(x_out),
+                                        _stream_ptr(stream)))
+
+
+def phc_track_polyhedral(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls_out, stats_out=None,
+                         stream=None):
+    _check(load().phc_track_polyhedral(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
+                                       ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
+                                       _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_solve_polyhedral(sys, lift, opts, max_paths: int, x_out, cls_out, stats_out=None, stream=None):
+    """Cells on this thread, paths on the GPU as the cells come (Figure 2);
+    returns (mixed volume, number of cells)."""
+    L = load()
+    tpe, exps, coefs = _lists(sys)
+    w = np.ascontiguousarray(np.asarray(lift).reshape(-1), dtype=np.int32)
+    npaths, ncells = ctypes.c_int64(), ctypes.c_int64()
+    _check(L.phc_solve_polyhedral(int(sys.n_var), tpe.ctypes.data, exps.ctypes.data, coefs.ctypes.data,
+                                  w.ctypes.data, ctypes.byref(opts) if opts is not None else None, int(max_paths),
+                                  _ptr(x_out), _ptr(cls_out), _ptr(stats_out), ctypes.byref(npaths),
+                                  ctypes.byref(ncells), _stream_ptr(stream)))
+    return int(npaths.value), int(ncells.value)
 
 
 def phc_track_from(h: Homotopy, starts, n_starts: int, starts_per_system: int, opts, x_out, cls_out,

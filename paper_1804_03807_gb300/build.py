@@ -21,8 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["track.cu", "track_pipe.cu", "track_multi.cu", "track_tail.cu", "track_dd.cu", "endgame.cu", "refine.cu",
-           "noalloc.cu", "phc_api.cpp"]
+SOURCES = ["track.cu", "track_pipe.cu", "track_multi.cu", "track_tail.cu", "track_dd.cu", "endgame.cu", "track_poly.cu", "refine.cu",
+           "noalloc.cu", "mixed_cells.cpp", "phc_api.cpp"]
 
 
 def nvcc() -> str:

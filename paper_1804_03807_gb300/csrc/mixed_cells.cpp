@@ -1,0 +1,539 @@
+// mixed_cells.cpp -- fine mixed cells of a lifted system of supports, and the
+// per-cell data of its polyhedral homotopy (host code).
+//
+// Section 2.2: a random coefficient start system is solved by polyhedral
+// homotopies, one per mixed cell of a mixed subdivision of the Newton
+// polytopes; a cell of volume V starts V paths, and the cells are produced one
+// after the other while the paths of the cells already made are tracked
+// (Figure 2).  Definitions used here:
+//   supports A_i = the exponent vectors of equation i's terms; an integer
+//   lifting w (one value per term).  A fine mixed cell picks {a_i, b_i} in
+//   every A_i and has an inner normal v in Q^n with, for every i,
+//       <a, v> + w(a) = beta_i  on the pair,  > beta_i  on the rest of A_i.
+//   Its volume is |det D|, D the integer matrix with rows b_i - a_i.
+//
+// Enumeration: depth first over the equations, the one with the fewest lower
+// edges first.  A pair of the next equation must (1) be a lower edge of its own
+// lifted support, (2) be compatible with every pair chosen so far (a relation
+// table of two-pair feasibility problems, solved once) and (3) keep the
+// problem of all pairs chosen so far feasible.  Complete choices are checked
+// exactly in 128-bit integer arithmetic.  The feasibility problems are linear
+// programs in double precision that only drop choices whose optimum is clearly
+// infeasible, so rounding can cost time but never a cell.
+//
+// Feasibility of the chosen pairs P: maximize tau over (v, tau) with
+//   <a - b, v> = w(b) - w(a)                    for every pair (a, b) in P,
+//   <c - a, v> + w(c) - w(a) >= tau             for every other point c of a
+//                                               chosen support,   tau <= 1;
+// strictly feasible when the optimum is positive.  It is solved through its
+// dual, min (sum_c (w(c)-w(a)) y_c + y_0 + sum_P (w(b)-w(a)) mu_P) subject to
+// sum_c y_c (a - c) + sum_P mu_P (a - b) = 0, sum_c y_c + y_0 = 1, y >= 0
+// (mu free, split in two), a standard-form problem with n + 1 rows that the
+// dense two-phase simplex below (Bland's rule) solves; an unbounded dual
+// means inconsistent equalities.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "phc_internal.h"
+
+namespace phc {
+
+int set_error(int code, const char *msg);
+
+namespace {
+
+typedef __int128 i128;
+
+// ------------------------------------------------------------------ linear programming
+
+// min cost.y subject to M y = b (b >= 0), y >= 0; M is R x C row-major.
+// Returns 0 (optimal, *val), 1 (unbounded), 2 (infeasible), 3 (no answer
+// within the iteration limit).
+int simplex(int R, int C, const double *M, const double *b, const double *cost, double *val)
+{
+    const int W = C + R + 1;
+    std::vector<double> T((size_t)(R + 1) * W, 0.0);
+    std::vector<int> basis(R);
+    double cmax = 0.0;
+    for (int j = 0; j < C; j++) cmax = std::max(cmax, std::fabs(cost[j]));
+    for (int i = 0; i < R; i++) {
+        for (int j = 0; j < C; j++) T[(size_t)i * W + j] = M[(size_t)i * C + j];
+        T[(size_t)i * W + C + i] = 1.0;
+        T[(size_t)i * W + W - 1] = b[i];
+        basis[i] = C + i;
+    }
+    double *obj = &T[(size_t)R * W];
+    auto pivot = [&](int r, int e) {
+        double *rr = &T[(size_t)r * W];
+        const double p = rr[e];
+        for (int j = 0; j < W; j++) rr[j] /= p;
+        for (int i = 0; i <= R; i++) {
+            if (i == r) continue;
+            double *ri = &T[(size_t)i * W];
+            const double f = ri[e];
+            if (f == 0.0) continue;
+            for (int j = 0; j < W; j++) ri[j] -= f * rr[j];
+        }
+        basis[r] = e;
+    };
+    // returns 0 optimal, 1 unbounded, 3 iteration limit
+    auto run = [&](int allow, double eps_cost) -> int {
+        const int limit = 64 * (R + C) + 256;
+        for (int it = 0; it < limit; it++) {
+            int e = -1;
+            for (int j = 0; j < allow; j++)
+                if (obj[j] < -eps_cost) {
+                    e = j;
+                    break;
+                }
+            if (e < 0) return 0;
+            int r = -1;
+            double best = 0.0;
+            for (int i = 0; i < R; i++) {
+                const double a = T[(size_t)i * W + e];
+                if (a <= 1e-11) continue;
+                const double ratio = T[(size_t)i * W + W - 1] / a;
+                if (r < 0 || ratio < best - 1e-13 || (ratio <= best + 1e-13 && basis[i] < basis[r])) {
+                    r = i;
+                    best = ratio;
+                }
+            }
+            if (r < 0) return 1;
+            pivot(r, e);
+        }
+        return 3;
+    };
+    // phase 1: minimise the sum of the artificial variables
+    for (int j = 0; j < C; j++) {
+        double s = 0.0;
+        for (int i = 0; i < R; i++) s += T[(size_t)i * W + j];
+        obj[j] = -s;
+    }
+    {
+        double s = 0.0;
+        for (int i = 0; i < R; i++) s += b[i];
+        obj[W - 1] = -s;
+    }
+    int rc = run(C, 1e-10);
+    if (rc == 3) return 3;
+    if (-obj[W - 1] > 1e-9) return 2;
+    for (int i = 0; i < R; i++) {
+        if (basis[i] < C) continue;
+        int e = -1;
+        for (int j = 0; j < C; j++)
+            if (std::fabs(T[(size_t)i * W + j]) > 1e-9) {
+                e = j;
+                break;
+            }
+        if (e >= 0) pivot(i, e);  // otherwise the row is redundant; its artificial stays at 0
+    }
+    // phase 2
+    for (int j = 0; j < W; j++) obj[j] = j < C ? cost[j] : 0.0;
+    for (int i = 0; i < R; i++) {
+        const double cb = basis[i] < C ? cost[basis[i]] : 0.0;
+        if (cb == 0.0) continue;
+        for (int j = 0; j < W; j++) obj[j] -= cb * T[(size_t)i * W + j];
+    }
+    rc = run(C, 1e-10 * (1.0 + cmax));
+    if (rc != 0) return rc;
+    *val = -obj[W - 1];
+    return 0;
+}
+
+struct Lifted {
+    int n = 0;
+    std::vector<int> off, m;                // per equation: first term, number of terms
+    std::vector<int64_t> A;                 // [T][n] exponents
+    std::vector<int64_t> w;                 // [T] lifting
+    double wmax = 0.0;
+    int64_t at(int t, int j) const { return A[(size_t)t * n + j]; }
+};
+
+struct Pair {
+    int eq, a, b;  // global term indices a < b of equation eq
+};
+
+// Is the set of pairs strictly feasible (see the file comment)?  Leans to
+// "yes" whenever the answer is not clear.
+bool feasible(const Lifted &L, const Pair *P, int np)
+{
+    const int n = L.n;
+    const int R = n + 1;
+    std::vector<double> cols, cost;  // column-major build, C columns of R
+    for (int p = 0; p < np; p++) {
+        const int i = P[p].eq, a = P[p].a, b = P[p].b;
+        for (int c = L.off[i]; c < L.off[i] + L.m[i]; c++) {
+            if (c == a || c == b) continue;
+            for (int j = 0; j < n; j++) cols.push_back((double)(L.at(a, j) - L.at(c, j)));
+            cols.push_back(1.0);
+            cost.push_back((double)(L.w[c] - L.w[a]));
+        }
+    }
+    for (int j = 0; j < n; j++) cols.push_back(0.0);  // y_0 (tau <= 1)
+    cols.push_back(1.0);
+    cost.push_back(1.0);
+    for (int p = 0; p < np; p++) {
+        const int a = P[p].a, b = P[p].b;
+        for (int s = 1; s >= -1; s -= 2) {
+            for (int j = 0; j < n; j++) cols.push_back((double)(s * (L.at(a, j) - L.at(b, j))));
+            cols.push_back(0.0);
+            cost.push_back((double)(s * (L.w[b] - L.w[a])));
+        }
+    }
+    const int C = (int)cost.size();
+    std::vector<double> M((size_t)R * C), rhs(R, 0.0);
+    for (int c = 0; c < C; c++)
+        for (int r = 0; r < R; r++) M[(size_t)r * C + c] = cols[(size_t)c * R + r];
+    rhs[n] = 1.0;
+    double val = 0.0;
+    const int rc = simplex(R, C, M.data(), rhs.data(), cost.data(), &val);
+    if (rc == 1 || rc == 2) return false;
+    if (rc != 0) return true;
+    return val > -1e-7 * (1.0 + L.wmax);
+}
+
+// ------------------------------------------------------------------ exact arithmetic
+
+bool mul_ok(i128 a, i128 b, i128 *out) { return !__builtin_mul_overflow(a, b, out); }
+bool add_ok(i128 a, i128 b, i128 *out) { return !__builtin_add_overflow(a, b, out); }
+
+// Determinant by fraction-free (Bareiss) elimination; false on overflow.
+bool det_exact(int n, std::vector<i128> M, i128 *out)
+{
+    i128 prev = 1;
+    int sign = 1;
+    for (int k = 0; k < n - 1; k++) {
+        if (M[(size_t)k * n + k] == 0) {
+            int p = -1;
+            for (int i = k + 1; i < n; i++)
+                if (M[(size_t)i * n + k] != 0) {
+                    p = i;
+                    break;
+                }
+            if (p < 0) {
+                *out = 0;
+                return true;
+            }
+            for (int j = 0; j < n; j++) std::swap(M[(size_t)k * n + j], M[(size_t)p * n + j]);
+            sign = -sign;
+        }
+        for (int i = k + 1; i < n; i++)
+            for (int j = k + 1; j < n; j++) {
+                i128 u, v;
+                if (!mul_ok(M[(size_t)i * n + j], M[(size_t)k * n + k], &u)) return false;
+                if (!mul_ok(M[(size_t)i * n + k], M[(size_t)k * n + j], &v)) return false;
+                M[(size_t)i * n + j] = (u - v) / prev;
+            }
+        prev = M[(size_t)k * n + k];
+    }
+    *out = sign * M[(size_t)(n - 1) * n + n - 1];
+    return true;
+}
+
+// Exact data of a complete choice: det D and x = det * v (Cramer), then the
+// scaled levels E_t = det * (<A_t, v> + w_t - beta_i) * sign(det) >= 0 of
+// every term.  Returns 1 for a fine mixed cell, 0 for no cell, -1 on a tie
+// (a choice that is otherwise a cell with a third point on its lower facet),
+// -2 on overflow.
+int exact_cell(const Lifted &L, const Pair *P, i128 *det_out, std::vector<i128> *E)
+{
+    const int n = L.n;
+    std::vector<i128> D((size_t)n * n);
+    std::vector<i128> r(n);
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) D[(size_t)i * n + j] = L.at(P[i].b, j) - L.at(P[i].a, j);
+        r[i] = L.w[P[i].a] - L.w[P[i].b];
+    }
+    i128 det = 0;
+    if (!det_exact(n, D, &det)) return -2;
+    if (det == 0) return 0;
+    std::vector<i128> x(n);
+    for (int j = 0; j < n; j++) {
+        std::vector<i128> Dj = D;
+        for (int i = 0; i < n; i++) Dj[(size_t)i * n + j] = r[i];
+        if (!det_exact(n, Dj, &x[j])) return -2;
+    }
+    const i128 sgn = det < 0 ? -1 : 1;
+    if (E) E->assign(L.A.size() / n, 0);
+    // a point below the pair's level rules the choice out; a tie matters
+    // only for a choice that is otherwise a cell
+    int result = 1;
+    bool tie = false;
+    auto level = [&](int t, i128 *out) -> bool {
+        i128 s = 0, u;
+        for (int j = 0; j < n; j++)
+            if (!mul_ok((i128)L.at(t, j), x[j], &u) || !add_ok(s, u, &s)) return false;
+        if (!mul_ok((i128)L.w[t], det, &u) || !add_ok(s, u, &s)) return false;
+        *out = s;
+        return true;
+    };
+    for (int i = 0; i < n; i++) {
+        i128 base;
+        if (!level(P[i].a, &base)) return -2;
+        for (int c = L.off[i]; c < L.off[i] + L.m[i]; c++) {
+            i128 val, diff;
+            if (!level(c, &val)) return -2;
+            if (__builtin_sub_overflow(val, base, &diff)) return -2;
+            diff *= sgn;
+            if (E) (*E)[c] = diff;
+            if (c == P[i].a || c == P[i].b) continue;  // equal level: v solves the pair's equation
+            if (diff == 0) tie = true;
+            if (diff < 0) result = 0;
+        }
+        if (result == 0 && !E) return 0;
+    }
+    *det_out = det;
+    if (result == 1 && tie) return -1;
+    return result;
+}
+
+int load(int n, const int32_t *tpe, const uint8_t *exps, const int32_t *lift, Lifted *L)
+{
+    if (n < 1 || n > PHC_MAX_VARS) return set_error(PHC_EINVAL, "mixed cells: n outside 1..PHC_MAX_VARS");
+    if (!tpe || !exps || !lift) return set_error(PHC_EINVAL, "mixed cells: NULL list");
+    L->n = n;
+    int T = 0;
+    for (int i = 0; i < n; i++) {
+        if (tpe[i] < 1 || tpe[i] > 4096) return set_error(PHC_EINVAL, "mixed cells: terms per equation outside 1..4096");
+        L->off.push_back(T);
+        L->m.push_back(tpe[i]);
+        T += tpe[i];
+    }
+    L->A.resize((size_t)T * n);
+    L->w.resize(T);
+    for (int t = 0; t < T; t++) {
+        for (int j = 0; j < n; j++) L->A[(size_t)t * n + j] = exps[(size_t)t * n + j];
+        if (lift[t] < 0 || lift[t] > (1 << 20))
+            return set_error(PHC_EINVAL, "mixed cells: lifting values must lie in 0..2^20");
+        L->w[t] = lift[t];
+        L->wmax = std::max(L->wmax, (double)lift[t]);
+    }
+    for (int i = 0; i < n; i++)
+        for (int a = L->off[i]; a < L->off[i] + L->m[i]; a++)
+            for (int b = a + 1; b < L->off[i] + L->m[i]; b++)
+                if (std::memcmp(&L->A[(size_t)a * n], &L->A[(size_t)b * n], n * sizeof(int64_t)) == 0)
+                    return set_error(PHC_EINVAL, "mixed cells: an equation lists a monomial twice");
+    return PHC_OK;
+}
+
+bool gcd_ext(int64_t a, int64_t b, int64_t *g, int64_t *s, int64_t *t)
+{
+    // s a + t b = g = gcd(a, b) >= 0
+    int64_t r0 = a, r1 = b, s0 = 1, s1 = 0, t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        const int64_t q = r0 / r1;
+        int64_t u, v;
+        if (__builtin_mul_overflow(q, r1, &u) || __builtin_sub_overflow(r0, u, &v)) return false;
+        r0 = r1;
+        r1 = v;
+        if (__builtin_mul_overflow(q, s1, &u) || __builtin_sub_overflow(s0, u, &v)) return false;
+        s0 = s1;
+        s1 = v;
+        if (__builtin_mul_overflow(q, t1, &u) || __builtin_sub_overflow(t0, u, &v)) return false;
+        t0 = t1;
+        t1 = v;
+    }
+    if (r0 < 0) {
+        r0 = -r0;
+        s0 = -s0;
+        t0 = -t0;
+    }
+    *g = r0;
+    *s = s0;
+    *t = t0;
+    return true;
+}
+
+}  // namespace
+
+int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const int32_t *lift,
+                          const std::function<int(const int32_t *pairs, int64_t volume)> &emit)
+{
+    Lifted L;
+    int rc = load(n, tpe, exps, lift, &L);
+    if (rc) return rc;
+    // (1) lower edges of every lifted support on its own
+    std::vector<std::vector<Pair>> edges(n);
+    for (int i = 0; i < n; i++)
+        for (int a = L.off[i]; a < L.off[i] + L.m[i]; a++)
+            for (int b = a + 1; b < L.off[i] + L.m[i]; b++) {
+                const Pair p{i, a, b};
+                if (feasible(L, &p, 1)) edges[i].push_back(p);
+            }
+    for (int i = 0; i < n; i++)
+        if (edges[i].empty()) return PHC_OK;  // a support of one point: no cell, mixed volume 0
+    std::vector<int> order(n);
+    for (int i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return edges[x].size() < edges[y].size(); });
+    // (2) relation table: edge e of one equation and f of another, feasible together
+    std::vector<int> eoff(n + 1, 0);
+    for (int i = 0; i < n; i++) eoff[i + 1] = eoff[i] + (int)edges[i].size();
+    const int NE = eoff[n];
+    const int words = (NE + 63) / 64;
+    std::vector<uint64_t> rel((size_t)NE * words, 0);
+    for (int i = 0; i < n; i++)
+        for (int e = 0; e < (int)edges[i].size(); e++) {
+            const int ge = eoff[i] + e;
+            for (int j = i + 1; j < n; j++)
+                for (int f = 0; f < (int)edges[j].size(); f++) {
+                    const Pair two[2] = {edges[i][e], edges[j][f]};
+                    if (!feasible(L, two, 2)) continue;
+                    const int gf = eoff[j] + f;
+                    rel[(size_t)ge * words + gf / 64] |= 1ull << (gf % 64);
+                    rel[(size_t)gf * words + ge / 64] |= 1ull << (ge % 64);
+                }
+        }
+    // (3) depth first
+    std::vector<Pair> chosen(n), sorted(n);
+    std::vector<int> chosen_id(n);
+    std::vector<int32_t> pairs(2 * n);
+    int status = PHC_OK;
+    std::function<void(int)> walk = [&](int d) {
+        if (status) return;
+        const int i = order[d];
+        for (int e = 0; e < (int)edges[i].size() && !status; e++) {
+            const int ge = eoff[i] + e;
+            bool ok = true;
+            for (int k = 0; k < d && ok; k++)
+                ok = (rel[(size_t)chosen_id[k] * words + ge / 64] >> (ge % 64)) & 1ull;
+            if (!ok) continue;
+            chosen[d] = edges[i][e];
+            chosen_id[d] = ge;
+            if (d + 1 < n) {
+                if (d >= 1 && !feasible(L, chosen.data(), d + 1)) continue;
+                walk(d + 1);
+                continue;
+            }
+            for (int k = 0; k < n; k++) sorted[chosen[k].eq] = chosen[k];
+            i128 det = 0;
+            const int ex = exact_cell(L, sorted.data(), &det, nullptr);
+            if (ex == -1) {
+                status = set_error(PHC_EINVAL, "mixed cells: lifting not in general position (a third point on a "
+                                               "cell's lower facet); draw another lifting");
+                return;
+            }
+            if (ex == -2) {
+                status = set_error(PHC_EUNSUPPORTED, "mixed cells: exact arithmetic overflows 128 bits");
+                return;
+            }
+            if (ex == 0) continue;
+            for (int k = 0; k < n; k++) {
+                pairs[2 * k] = sorted[k].a;
+                pairs[2 * k + 1] = sorted[k].b;
+            }
+            const i128 vol = det < 0 ? -det : det;
+            if (vol > (i128)INT64_MAX) {
+                status = set_error(PHC_EUNSUPPORTED, "mixed cells: cell volume above 2^63");
+                return;
+            }
+            const int r = emit(pairs.data(), (int64_t)vol);
+            if (r) status = r;
+        }
+    };
+    walk(0);
+    return status;
+}
+
+int cell_tracking_data(int n, const int32_t *tpe, const uint8_t *exps, const int32_t *lift, const int32_t *pairs,
+                       double *powers, int64_t *H, int64_t *U, int64_t *volume)
+{
+    Lifted L;
+    int rc = load(n, tpe, exps, lift, &L);
+    if (rc) return rc;
+    std::vector<Pair> P(n);
+    for (int i = 0; i < n; i++) {
+        const int a = pairs[2 * i], b = pairs[2 * i + 1];
+        if (a < L.off[i] || b < L.off[i] || a >= L.off[i] + L.m[i] || b >= L.off[i] + L.m[i] || a == b)
+            return set_error(PHC_EINVAL, "cell: a pair does not name two terms of its equation");
+        P[i] = Pair{i, std::min(a, b), std::max(a, b)};
+    }
+    i128 det = 0;
+    std::vector<i128> E;
+    const int ex = exact_cell(L, P.data(), &det, &E);
+    if (ex == -2) return set_error(PHC_EUNSUPPORTED, "cell: exact arithmetic overflows 128 bits");
+    if (ex == -1) return set_error(PHC_EINVAL, "cell: lifting not in general position");
+    if (ex == 0) return set_error(PHC_EINVAL, "cell: the pairs are not a fine mixed cell of this lifting");
+    // powers: E_t / min positive E (0 on the cell's terms)
+    i128 emin = 0;
+    for (size_t t = 0; t < E.size(); t++)
+        if (E[t] > 0 && (emin == 0 || E[t] < emin)) emin = E[t];
+    for (size_t t = 0; t < E.size(); t++) powers[t] = E[t] == 0 ? 0.0 : (double)E[t] / (double)emin;
+    // Hermite form: U D = H upper triangular with a positive diagonal, U
+    // unimodular (row operations of determinant 1 built from extended gcds)
+    std::vector<int64_t> Hm((size_t)n * n), Um((size_t)n * n, 0);
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) Hm[(size_t)i * n + j] = L.at(P[i].b, j) - L.at(P[i].a, j);
+        Um[(size_t)i * n + i] = 1;
+    }
+    auto combine = [&](std::vector<int64_t> &M, int k, int i, int64_t s, int64_t t, int64_t p, int64_t q) -> bool {
+        // row k := s row_k + t row_i, row i := p row_k + q row_i
+        for (int j = 0; j < n; j++) {
+            const int64_t rk = M[(size_t)k * n + j], ri = M[(size_t)i * n + j];
+            int64_t u, v, x, y;
+            if (__builtin_mul_overflow(s, rk, &u) || __builtin_mul_overflow(t, ri, &v) || __builtin_add_overflow(u, v, &x))
+                return false;
+            if (__builtin_mul_overflow(p, rk, &u) || __builtin_mul_overflow(q, ri, &v) || __builtin_add_overflow(u, v, &y))
+                return false;
+            M[(size_t)k * n + j] = x;
+            M[(size_t)i * n + j] = y;
+        }
+        return true;
+    };
+    for (int k = 0; k < n; k++) {
+        for (int i = k + 1; i < n; i++) {
+            const int64_t a = Hm[(size_t)k * n + k], b = Hm[(size_t)i * n + k];
+            if (b == 0) continue;
+            int64_t g, s, t;
+            if (!gcd_ext(a, b, &g, &s, &t)) return set_error(PHC_EUNSUPPORTED, "cell: Hermite form overflows");
+            // [s t; -b/g a/g] has determinant (s a + t b) / g = 1
+            const int64_t p = -(b / g), q = a / g;
+            if (!combine(Hm, k, i, s, t, p, q) || !combine(Um, k, i, s, t, p, q))
+                return set_error(PHC_EUNSUPPORTED, "cell: Hermite form overflows");
+        }
+        if (Hm[(size_t)k * n + k] == 0) return set_error(PHC_EINVAL, "cell: singular exponent matrix");
+        if (Hm[(size_t)k * n + k] < 0)
+            for (int j = 0; j < n; j++) {
+                Hm[(size_t)k * n + j] = -Hm[(size_t)k * n + j];
+                Um[(size_t)k * n + j] = -Um[(size_t)k * n + j];
+            }
+    }
+    int64_t prod = 1;
+    for (int k = 0; k < n; k++)
+        if (__builtin_mul_overflow(prod, Hm[(size_t)k * n + k], &prod))
+            return set_error(PHC_EUNSUPPORTED, "cell: volume overflows");
+    const i128 vol = det < 0 ? -det : det;
+    if ((i128)prod != vol) return set_error(PHC_EINVAL, "internal: Hermite diagonal does not multiply to the volume");
+    std::memcpy(H, Hm.data(), Hm.size() * sizeof(int64_t));
+    std::memcpy(U, Um.data(), Um.size() * sizeof(int64_t));
+    *volume = (int64_t)vol;
+    return PHC_OK;
+}
+
+}  // namespace phc
+
+extern "C" int phc_mixed_cells(int n, const int32_t *terms_per_eq, const uint8_t *exps, const int32_t *lift,
+                               int64_t max_cells, int32_t *cells_out, int64_t *volumes_out, int64_t *n_cells_out,
+                               int64_t *mixed_volume_out)
+{
+    if (!n_cells_out) return phc::set_error(PHC_EINVAL, "phc_mixed_cells: n_cells_out is NULL");
+    if (max_cells < 0) return phc::set_error(PHC_EINVAL, "phc_mixed_cells: max_cells < 0");
+    if (max_cells > 0 && !cells_out) return phc::set_error(PHC_EINVAL, "phc_mixed_cells: cells_out is NULL");
+    int64_t count = 0, mv = 0;
+    const int rc = phc::enumerate_mixed_cells(n, terms_per_eq, exps, lift, [&](const int32_t *p, int64_t vol) -> int {
+        if (count < max_cells) {
+            std::memcpy(cells_out + (size_t)count * 2 * n, p, 2 * (size_t)n * sizeof(int32_t));
+            if (volumes_out) volumes_out[count] = vol;
+        }
+        count++;
+        if (__builtin_add_overflow(mv, vol, &mv))
+            return phc::set_error(PHC_EUNSUPPORTED, "phc_mixed_cells: mixed volume above 2^63");
+        return PHC_OK;
+    });
+    if (rc) return rc;
+    *n_cells_out = count;
+    if (mixed_volume_out) *mixed_volume_out = mv;
+    return PHC_OK;
+}

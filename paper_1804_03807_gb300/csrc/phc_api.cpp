@@ -127,6 +127,16 @@ struct phc_homotopy {
     // for the classification and refinement at t = 1
     int parameter = 0;
     DeviceTable target;
+    // polyhedral homotopies (phc_make_polyhedral_homotopy): `total` holds
+    // (0, c) per term of g (so t = 1 gives g for classification and
+    // refinement); the cells' data live in one device block
+    int polyhedral = 0;
+    int n_cells = 0;
+    void *d_poly = nullptr;
+    const int64_t *d_path_off = nullptr;
+    const double *d_powers = nullptr;
+    const int64_t *d_H = nullptr, *d_U = nullptr;
+    const int32_t *d_pairs = nullptr;
     int32_t *d_deg = nullptr, *d_root_off = nullptr;
     double2 *d_roots = nullptr;
     // scratch
@@ -471,6 +481,7 @@ extern "C" void phc_destroy_homotopy(phc_homotopy *h)
     if (h->d_xfull) cudaFree(h->d_xfull);
     if (h->d_handoff) cudaFree(h->d_handoff);
     if (h->d_tailc) cudaFree(h->d_tailc);
+    if (h->d_poly) cudaFree(h->d_poly);
     delete h;
 }
 
@@ -610,6 +621,7 @@ extern "C" int phc_track_paths(phc_homotopy *h, int64_t first, int64_t n, const 
     if (!h) return fail(PHC_EINVAL, "NULL handle");
     if (h->parameter && n > 0)
         return fail(PHC_EINVAL, "a parameter homotopy has no total-degree start system (use phc_track_from)");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle is tracked by phc_track_polyhedral");
     if (n < 0 || first < 0 || first + n > h->num_paths)
         return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
                     (long long)(first + n), (long long)h->num_paths);
@@ -634,6 +646,7 @@ extern "C" int phc_track_from(phc_homotopy *h, const phc_cd *starts, int64_t n, 
                               void *stream)
 {
     if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle is tracked by phc_track_polyhedral");
     if (n < 0 || starts_per_system < 0) return fail(PHC_EINVAL, "n_starts or starts_per_system < 0");
     if (n == 0) return PHC_OK;
     if (!starts || !x_out || !cls_out) return fail(PHC_EINVAL, "NULL array");
@@ -662,6 +675,7 @@ extern "C" int phc_track_paths_dd(phc_homotopy *h, int64_t first, int64_t n, con
     if (!h) return fail(PHC_EINVAL, "NULL handle");
     if (h->parameter && n > 0)
         return fail(PHC_EINVAL, "a parameter homotopy has no total-degree start system");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle is tracked by phc_track_polyhedral");
     if (n < 0 || first < 0 || first + n > h->num_paths)
         return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
                     (long long)(first + n), (long long)h->num_paths);
@@ -716,6 +730,7 @@ extern "C" int phc_endgame(phc_homotopy *h, int64_t first, int64_t n, const phc_
     if (!h) return fail(PHC_EINVAL, "NULL handle");
     if (h->parameter && n > 0)
         return fail(PHC_EINVAL, "a parameter homotopy has no total-degree start system");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle is tracked by phc_track_polyhedral");
     if (n < 0 || first < 0 || first + n > h->num_paths)
         return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
                     (long long)(first + n), (long long)h->num_paths);
@@ -790,6 +805,7 @@ extern "C" int phc_cascade_stage(const phc_homotopy *hc, int k, const phc_cd *st
     if (!h) return fail(PHC_EINVAL, "NULL handle");
     if (k < 1 || k >= h->n) return fail(PHC_EINVAL, "cascade stage k = %d outside 1..%d", k, h->n - 1);
     if (h->n_sys != 1) return fail(PHC_EUNSUPPORTED, "cascade stages need a single-system handle");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle has no cascade");
     if (n < 0) return fail(PHC_EINVAL, "n_starts < 0");
     if (n == 0) return PHC_OK;
     if (!starts || !x_out || !cls_out || !slack_zero_out) return fail(PHC_EINVAL, "NULL array");
@@ -837,6 +853,7 @@ static int many_groups(phc_homotopy *const *hs, int n_h, const phc_opts &o, phc_
         if (!hs[i]) return fail(PHC_EINVAL, "handle %d is NULL", i);
         if (hs[i]->n_sys != 1) return fail(PHC_EUNSUPPORTED, "handle %d is a batch handle", i);
         if (hs[i]->parameter) return fail(PHC_EINVAL, "handle %d is a parameter homotopy", i);
+        if (hs[i]->polyhedral) return fail(PHC_EINVAL, "handle %d is a polyhedral handle", i);
         if (!x_out[i] || !cls_out[i]) return fail(PHC_EINVAL, "NULL output array of handle %d", i);
     }
     for (int n = 1; n <= PHC_MAX_VARS; n++) {
@@ -1140,6 +1157,7 @@ extern "C" int phc_track_pipeline(phc_homotopy *h, int k, int64_t first, int64_t
     if (!h) return fail(PHC_EINVAL, "NULL handle");
     if (k < 1 || k >= h->n) return fail(PHC_EINVAL, "cascade stage k = %d outside 1..%d", k, h->n - 1);
     if (h->n_sys != 1) return fail(PHC_EUNSUPPORTED, "the pipeline needs a single-system handle");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle has no cascade");
     if (n < 0 || first < 0 || first + n > h->num_paths)
         return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
                     (long long)(first + n), (long long)h->num_paths);
@@ -1219,6 +1237,7 @@ extern "C" int phc_cascade_from(const phc_homotopy *hc, int k, const phc_cd *x_p
     if (!h) return fail(PHC_EINVAL, "NULL handle");
     if (k < 1 || k >= h->n) return fail(PHC_EINVAL, "cascade stage k = %d outside 1..%d", k, h->n - 1);
     if (h->n_sys != 1) return fail(PHC_EUNSUPPORTED, "cascade stages need a single-system handle");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle has no cascade");
     if (n < 0) return fail(PHC_EINVAL, "n < 0");
     if (n == 0) return PHC_OK;
     if (!x_prev || !cls_prev || !x_out || !cls_out || !slack_zero_out) return fail(PHC_EINVAL, "NULL array");
@@ -1546,6 +1565,368 @@ extern "C" void phc_free_lists(phc_system_lists *L)
     delete L;
 }
 
+// ------------------------------------------------------------------ polyhedral homotopies
+
+// Host block of the cells' data (path offsets, powers, H, U, pairs; 16-byte
+// aligned parts) and the offsets of its parts.
+struct PolyBlock {
+    std::vector<char> host;
+    size_t o_pw = 0, o_H = 0, o_U = 0, o_pr = 0;
+};
+
+static PolyBlock poly_block(const std::vector<int64_t> &path_off, const std::vector<double> &powers,
+                            const std::vector<int64_t> &H, const std::vector<int64_t> &U, const int32_t *pairs,
+                            size_t n_pairs)
+{
+    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    PolyBlock B;
+    B.o_pw = al(path_off.size() * sizeof(int64_t));
+    B.o_H = al(B.o_pw + powers.size() * sizeof(double));
+    B.o_U = al(B.o_H + H.size() * sizeof(int64_t));
+    B.o_pr = al(B.o_U + U.size() * sizeof(int64_t));
+    B.host.assign(al(B.o_pr + n_pairs * sizeof(int32_t)), 0);
+    std::memcpy(B.host.data(), path_off.data(), path_off.size() * sizeof(int64_t));
+    std::memcpy(B.host.data() + B.o_pw, powers.data(), powers.size() * sizeof(double));
+    std::memcpy(B.host.data() + B.o_H, H.data(), H.size() * sizeof(int64_t));
+    std::memcpy(B.host.data() + B.o_U, U.data(), U.size() * sizeof(int64_t));
+    std::memcpy(B.host.data() + B.o_pr, pairs, n_pairs * sizeof(int32_t));
+    return B;
+}
+
+// The terms of g with (c0, c1) = (0, c): the kernels read c from c1, and the
+// classification at t = 1 sees g.
+static HostTerms poly_terms(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs)
+{
+    HostTerms ht;
+    int64_t off = 0;
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < tpe[i]; k++, off++)
+            ht.add(i, exps + off * n, n, make_double2(0.0, 0.0), make_double2(coefs[off].re, coefs[off].im));
+    return ht;
+}
+
+extern "C" int phc_make_polyhedral_homotopy(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                                            const int32_t *lift, const int32_t *cells, int64_t n_cells,
+                                            phc_homotopy **out)
+{
+    if (!out) return fail(PHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_cells < 1 || !cells || !lift) return fail(PHC_EINVAL, "polyhedral homotopy: no cells or no lifting");
+    if (n_cells > (1 << 30)) return fail(PHC_EUNSUPPORTED, "polyhedral homotopy: more than 2^30 cells");
+    std::vector<int32_t> deg;
+    int rc = validate_lists(n, n, tpe, exps, coefs, true, &deg);
+    if (rc) return rc;
+    int64_t T = 0;
+    for (int i = 0; i < n; i++) T += tpe[i];
+    const size_t nn = (size_t)n * n;
+    std::vector<int64_t> path_off(n_cells + 1, 0), H(n_cells * nn), U(n_cells * nn);
+    std::vector<double> powers((size_t)n_cells * T);
+    for (int64_t c = 0; c < n_cells; c++) {
+        const int32_t *pr = cells + (size_t)c * 2 * n;
+        for (int i = 0; i < 2 * n; i++)
+            if (pr[i] < 0 || pr[i] >= T) return fail(PHC_EINVAL, "cell %lld names a term outside the lists", (long long)c);
+        int64_t vol = 0;
+        rc = phc::cell_tracking_data(n, tpe, exps, lift, pr, &powers[(size_t)c * T], &H[c * nn], &U[c * nn], &vol);
+        if (rc) return rc;
+        for (int i = 0; i < 2 * n; i++)
+            if (coefs[pr[i]].re == 0.0 && coefs[pr[i]].im == 0.0)
+                return fail(PHC_EINVAL, "cell %lld: a term of its binomial system has a zero coefficient",
+                            (long long)c);
+        if (__builtin_add_overflow(path_off[c], vol, &path_off[c + 1]))
+            return fail(PHC_EUNSUPPORTED, "polyhedral homotopy: more than 2^63 paths");
+    }
+    phc_homotopy *h = new (std::nothrow) phc_homotopy();
+    if (!h) return fail(PHC_ENOMEM, "host allocation");
+    h->n = n;
+    h->n_sys = 1;
+    h->polyhedral = 1;
+    h->n_cells = (int)n_cells;
+    h->tpe.assign(tpe, tpe + n);
+    h->exps.assign(exps, exps + T * n);
+    h->coefs.assign(coefs, coefs + T);
+    h->deg = deg;
+    h->num_paths = path_off[n_cells];
+    h->paths_per_system = h->num_paths;
+    cudaGetDevice(&h->device);
+    const PolyBlock B = poly_block(path_off, powers, H, U, cells, (size_t)n_cells * 2 * n);
+    cudaStream_t ps = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return fail(PHC_ECUDA, "cudaStreamCreateWithFlags");
+    }
+    rc = upload_table(poly_terms(n, tpe, exps, coefs), n, h->total, ps);
+    if (!rc && cudaMalloc(&h->d_poly, B.host.size()) != cudaSuccess) rc = fail(PHC_ENOMEM, "cudaMalloc of the cell data");
+    if (!rc && (cudaMemcpyAsync(h->d_poly, B.host.data(), B.host.size(), cudaMemcpyHostToDevice, ps) != cudaSuccess ||
+                cudaStreamSynchronize(ps) != cudaSuccess))
+        rc = fail(PHC_ECUDA, "upload of the cell data");
+    cudaStreamDestroy(ps);
+    if (!rc && cudaMalloc(&h->d_qhead, sizeof(unsigned long long)) != cudaSuccess)
+        rc = fail(PHC_ENOMEM, "cudaMalloc of the path counter");
+    if (rc) {
+        phc_destroy_homotopy(h);
+        return rc;
+    }
+    char *b = static_cast<char *>(h->d_poly);
+    h->d_path_off = reinterpret_cast<const int64_t *>(b);
+    h->d_powers = reinterpret_cast<const double *>(b + B.o_pw);
+    h->d_H = reinterpret_cast<const int64_t *>(b + B.o_H);
+    h->d_U = reinterpret_cast<const int64_t *>(b + B.o_U);
+    h->d_pairs = reinterpret_cast<const int32_t *>(b + B.o_pr);
+    *out = h;
+    return PHC_OK;
+}
+
+static phc::PolyLaunch poly_launch(const DevTables &tab, int n_cells, const char *block, const PolyBlock &B,
+                                   int64_t first, int64_t n, double2 *x_out)
+{
+    phc::PolyLaunch L{};
+    L.tab = tab;
+    L.tab.f32 = 0;
+    L.n_cells = n_cells;
+    L.path_off = reinterpret_cast<const int64_t *>(block);
+    L.powers = reinterpret_cast<const double *>(block + B.o_pw);
+    L.H = reinterpret_cast<const int64_t *>(block + B.o_H);
+    L.U = reinterpret_cast<const int64_t *>(block + B.o_U);
+    L.pairs = reinterpret_cast<const int32_t *>(block + B.o_pr);
+    L.first = first;
+    L.n_paths = n;
+    L.x_out = x_out;
+    return L;
+}
+
+static phc::PolyLaunch handle_poly_launch(const phc_homotopy *h, int64_t first, int64_t n, double2 *x_out)
+{
+    phc::PolyLaunch L{};
+    L.tab = h->total.view;
+    L.tab.f32 = 0;
+    L.n_cells = h->n_cells;
+    L.path_off = h->d_path_off;
+    L.powers = h->d_powers;
+    L.H = h->d_H;
+    L.U = h->d_U;
+    L.pairs = h->d_pairs;
+    L.first = first;
+    L.n_paths = n;
+    L.x_out = x_out;
+    return L;
+}
+
+extern "C" int phc_polyhedral_starts(const phc_homotopy *h, int64_t first, int64_t n, phc_cd *x_out, void *stream)
+{
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (!h->polyhedral) return fail(PHC_EINVAL, "not a polyhedral handle");
+    if (n < 0 || first < 0 || first + n > h->num_paths)
+        return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + n), (long long)h->num_paths);
+    if (n == 0) return PHC_OK;
+    if (!x_out) return fail(PHC_EINVAL, "NULL output array");
+    const phc::PolyLaunch L = handle_poly_launch(h, first, n, reinterpret_cast<double2 *>(x_out));
+    cudaError_t e = phc::launch_poly_starts(L, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "start solution kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+static int classify_poly(const DevTables &tab, int64_t n, const double2 *x, int64_t x_ld, phc_path_stats *st,
+                         int8_t *cls, const phc_opts &o, cudaStream_t s)
+{
+    phc::ClassifyLaunch C{};
+    C.tab = tab;
+    C.tab.f32 = 0;
+    C.n_paths = n;
+    C.x = x;
+    C.x_ld = x_ld;
+    C.stats = st;
+    C.cls = cls;
+    C.o = o;
+    cudaError_t e = phc::launch_classify(C, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "classify kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
+extern "C" int phc_track_polyhedral(phc_homotopy *h, int64_t first, int64_t n, const phc_opts *opts, phc_cd *x_out,
+                                    int8_t *cls_out, phc_path_stats *stats_out, void *stream)
+{
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (!h->polyhedral) return fail(PHC_EINVAL, "not a polyhedral handle");
+    if (n < 0 || first < 0 || first + n > h->num_paths)
+        return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + n), (long long)h->num_paths);
+    if (n == 0) return PHC_OK;
+    if (!x_out || !cls_out) return fail(PHC_EINVAL, "NULL output array");
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    phc_path_stats *st = stats_out;
+    if (!st) {
+        rc = ensure_stats(h, n, s);
+        if (rc) return rc;
+        st = h->d_stats;
+    }
+    CU(cudaMemsetAsync(h->d_qhead, 0, sizeof(unsigned long long), s));
+    if (h->d_tailc) CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));  // no hand-off here
+    phc::PolyLaunch L = handle_poly_launch(h, first, n, reinterpret_cast<double2 *>(x_out));
+    L.stats = st;
+    L.qhead = h->d_qhead;
+    L.o = o;
+    cudaError_t e = phc::launch_track_poly(L, o.block_threads, o.max_blocks, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "polyhedral track kernel launch: %s", cudaGetErrorString(e));
+    return classify_poly(h->total.view, n, L.x_out, 0, st, cls_out, o, s);
+}
+
+// The two-stage pipeline of Section 2.2 (Figure 2): this thread makes the
+// cells one after the other (the first stage) while the GPU tracks the paths
+// of the cells made so far (the second stage).  Cells are gathered into
+// batches of growing size (the first small, so that tracking starts early);
+// each batch is uploaded and launched on one of a few helper streams, so
+// batches overlap on the GPU, and its cell data are freed in stream order.
+extern "C" int phc_solve_polyhedral(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                                    const int32_t *lift, const phc_opts *opts, int64_t max_paths, phc_cd *x_out,
+                                    int8_t *cls_out, phc_path_stats *stats_out, int64_t *n_paths_out,
+                                    int64_t *n_cells_out, void *stream)
+{
+    if (!n_paths_out) return fail(PHC_EINVAL, "n_paths_out is NULL");
+    *n_paths_out = 0;
+    if (n_cells_out) *n_cells_out = 0;
+    if (max_paths < 0) return fail(PHC_EINVAL, "max_paths < 0");
+    if (max_paths > 0 && (!x_out || !cls_out)) return fail(PHC_EINVAL, "NULL output array");
+    if (!lift) return fail(PHC_EINVAL, "NULL lifting");
+    std::vector<int32_t> deg;
+    int rc = validate_lists(n, n, tpe, exps, coefs, true, &deg);
+    if (rc) return rc;
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    rc = check_opts(o);
+    if (rc) return rc;
+    int64_t T = 0;
+    for (int i = 0; i < n; i++) T += tpe[i];
+    const size_t nn = (size_t)n * n;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    constexpr int K = 8;  // helper streams
+    DeviceTable tab;
+    cudaStream_t hs[K] = {};
+    cudaEvent_t ev[K + 1] = {};
+    unsigned long long *counters = nullptr;
+    phc_path_stats *st = stats_out;
+    bool own_stats = false;
+    auto cleanup = [&]() {
+        free_table(tab);
+        if (counters) cudaFree(counters);
+        if (own_stats && st) cudaFree(st);
+        for (int k = 0; k < K; k++)
+            if (hs[k]) cudaStreamDestroy(hs[k]);
+        for (int k = 0; k <= K; k++)
+            if (ev[k]) cudaEventDestroy(ev[k]);
+    };
+    {
+        cudaStream_t ps = nullptr;
+        if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(PHC_ECUDA, "cudaStreamCreateWithFlags");
+        rc = upload_table(poly_terms(n, tpe, exps, coefs), n, tab, ps);
+        cudaStreamDestroy(ps);
+        if (rc) return rc;
+    }
+    int prio = 0;
+    if (cudaStreamGetPriority(s, &prio) != cudaSuccess) prio = 0;
+    for (int k = 0; k < K && !rc; k++)
+        if (cudaStreamCreateWithPriority(&hs[k], cudaStreamNonBlocking, prio) != cudaSuccess)
+            rc = fail(PHC_ECUDA, "cudaStreamCreateWithPriority");
+    for (int k = 0; k <= K && !rc; k++)
+        if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess)
+            rc = fail(PHC_ECUDA, "cudaEventCreateWithFlags");
+    if (!rc && cudaMalloc(&counters, K * sizeof(unsigned long long)) != cudaSuccess)
+        rc = fail(PHC_ENOMEM, "cudaMalloc of the path counters");
+    if (!rc && !st && max_paths > 0) {
+        if (cudaMalloc(&st, (size_t)max_paths * sizeof(phc_path_stats)) != cudaSuccess)
+            rc = fail(PHC_ENOMEM, "cudaMalloc of the path records");
+        own_stats = true;
+    }
+    // fork: the helper streams start after the work already on the caller's stream
+    if (!rc && cudaEventRecord(ev[K], s) != cudaSuccess) rc = fail(PHC_ECUDA, "cudaEventRecord");
+    for (int k = 0; k < K && !rc; k++)
+        if (cudaStreamWaitEvent(hs[k], ev[K], 0) != cudaSuccess) rc = fail(PHC_ECUDA, "cudaStreamWaitEvent");
+    if (rc) {
+        cudaStreamSynchronize(s);
+        cleanup();
+        return rc;
+    }
+
+    std::vector<int64_t> b_off(1, 0), b_H, b_U;
+    std::vector<double> b_pw;
+    std::vector<int32_t> b_pairs;
+    int64_t launched = 0, mv = 0, cells = 0, limit = 64;
+    int next = 0;
+    bool overflow = false;
+    auto flush = [&]() -> int {
+        const int64_t paths = b_off.back();
+        const int64_t nc = (int64_t)b_off.size() - 1;
+        if (nc == 0) return PHC_OK;
+        if (launched + paths > max_paths) overflow = true;
+        if (!overflow) {
+            const PolyBlock B = poly_block(b_off, b_pw, b_H, b_U, b_pairs.data(), b_pairs.size());
+            cudaStream_t hk = hs[next];
+            void *blk = nullptr;
+            CU(cudaMallocAsync(&blk, B.host.size(), hk));
+            // pageable source: staged before the call returns, so B may go
+            CU(cudaMemcpyAsync(blk, B.host.data(), B.host.size(), cudaMemcpyHostToDevice, hk));
+            phc::PolyLaunch L = poly_launch(tab.view, (int)nc, static_cast<const char *>(blk), B, 0, paths,
+                                            reinterpret_cast<double2 *>(x_out) + launched);
+            L.x_ld = max_paths;
+            L.stats = st + launched;
+            L.qhead = counters + next;
+            L.o = o;
+            CU(cudaMemsetAsync(counters + next, 0, sizeof(unsigned long long), hk));
+            cudaError_t e = phc::launch_track_poly(L, o.block_threads, o.max_blocks, hk);
+            if (e != cudaSuccess) return fail(PHC_ECUDA, "polyhedral track kernel launch: %s", cudaGetErrorString(e));
+            CU(cudaFreeAsync(blk, hk));
+            launched += paths;
+            next = (next + 1) % K;
+        }
+        b_off.assign(1, 0);
+        b_H.clear();
+        b_U.clear();
+        b_pw.clear();
+        b_pairs.clear();
+        if (limit < 16384) limit *= 2;
+        return PHC_OK;
+    };
+    rc = phc::enumerate_mixed_cells(n, tpe, exps, lift, [&](const int32_t *pairs, int64_t) -> int {
+        const size_t c = b_off.size() - 1;
+        b_H.resize((c + 1) * nn);
+        b_U.resize((c + 1) * nn);
+        b_pw.resize((c + 1) * (size_t)T);
+        int64_t vol = 0;
+        const int r = phc::cell_tracking_data(n, tpe, exps, lift, pairs, &b_pw[c * T], &b_H[c * nn], &b_U[c * nn], &vol);
+        if (r) return r;
+        for (int i = 0; i < 2 * n; i++)
+            if (coefs[pairs[i]].re == 0.0 && coefs[pairs[i]].im == 0.0)
+                return fail(PHC_EINVAL, "a cell's binomial system has a zero coefficient");
+        b_pairs.insert(b_pairs.end(), pairs, pairs + 2 * n);
+        b_off.push_back(b_off.back() + vol);
+        cells++;
+        if (__builtin_add_overflow(mv, vol, &mv)) return fail(PHC_EUNSUPPORTED, "mixed volume above 2^63");
+        return b_off.back() >= limit ? flush() : PHC_OK;
+    });
+    if (!rc) rc = flush();
+    // join, then classify every path at t = 1 on the caller's stream
+    for (int k = 0; k < K; k++)
+        if ((cudaEventRecord(ev[k], hs[k]) != cudaSuccess || cudaStreamWaitEvent(s, ev[k], 0) != cudaSuccess) && !rc)
+            rc = fail(PHC_ECUDA, "joining the helper streams");
+    if (!rc && !overflow && launched > 0)
+        rc = classify_poly(tab.view, launched, reinterpret_cast<const double2 *>(x_out), max_paths, st, cls_out, o, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (!rc && e != cudaSuccess) rc = fail(PHC_ECUDA, "polyhedral pipeline: %s", cudaGetErrorString(e));
+    cleanup();
+    if (rc) return rc;
+    *n_paths_out = mv;
+    if (n_cells_out) *n_cells_out = cells;
+    if (overflow)
+        return fail(PHC_EINVAL, "the mixed volume %lld exceeds max_paths %lld", (long long)mv, (long long)max_paths);
+    return PHC_OK;
+}
+
 // ------------------------------------------------------------------ internal accessors (noalloc.cu)
 
 namespace phc {
@@ -1565,6 +1946,7 @@ int handle_num_paths(const phc_homotopy *h, int64_t *out)
 // precision copies staged only for FP32_INTERIOR).
 int handle_track_view(phc_homotopy *h, const phc_opts &o, TrackLaunch *L)
 {
+    if (h->parameter || h->polyhedral) return fail(PHC_EINVAL, "the handle has no total-degree start system");
     L->tab = h->total.view;
     L->tab.f32 = o.precision == PHC_PREC_FP32_INTERIOR;
     L->deg = h->d_deg;

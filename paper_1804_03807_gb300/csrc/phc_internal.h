@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <cuda_runtime.h>
 
 #include "../../include/phc.h"
@@ -180,7 +181,8 @@ __host__ __device__ inline size_t warp_table_bytes(int T, int V, bool f32)
 struct ClassifyLaunch {
     DevTables tab;
     int64_t n_paths;
-    const double2 *x;         // SoA [n][n_paths]
+    const double2 *x;         // SoA [n][x_ld] (x_ld 0: n_paths)
+    int64_t x_ld;
     phc_path_stats *stats;    // [n_paths] in/out
     int8_t *cls;              // [n_paths] out
     phc_opts o;
@@ -263,6 +265,39 @@ cudaError_t launch_match_points(const double2 *x, const int8_t *cls, int N, int6
 cudaError_t launch_tile_starts(const double2 *starts, int N, int64_t m, int64_t p, double2 *out, cudaStream_t s);
 cudaError_t launch_drop_last(const double2 *x_full, int n_full, int64_t n_paths, double2 *x_out,
                              uint8_t *slack_zero, int has_next_slack, double slack_tol, cudaStream_t s);
+
+// Polyhedral homotopies of one system g (track_poly.cu): tab holds g's terms
+// with the coefficients in c1 (c0 = 0); path p belongs to the cell c with
+// path_off[c] <= p < path_off[c + 1].
+struct PolyLaunch {
+    DevTables tab;
+    int n_cells;
+    const int64_t *path_off;  // [n_cells + 1]
+    const double *powers;     // [n_cells][n_terms] power of t per term
+    const int64_t *H, *U;     // [n_cells][n][n] Hermite form U D = H
+    const int32_t *pairs;     // [n_cells][n][2] the cell's terms per equation
+    int64_t first, n_paths;
+    double2 *x_out;           // SoA [n][x_ld] (x_ld 0: n_paths)
+    int64_t x_ld;
+    phc_path_stats *stats;    // [n_paths]
+    unsigned long long *qhead;
+    phc_opts o;
+};
+cudaError_t launch_poly_starts(const PolyLaunch &L, cudaStream_t s);
+cudaError_t launch_track_poly(const PolyLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
+
+// Fine mixed cells of the supports under an integer lifting (mixed_cells.cpp,
+// host): emit(pairs, volume) once per cell as it is found, pairs = the 2n
+// global term indices (a_i, b_i), a_i < b_i, per equation; a nonzero return
+// of emit stops the enumeration and is returned.
+int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const int32_t *lift,
+                          const std::function<int(const int32_t *pairs, int64_t volume)> &emit);
+// The polyhedral homotopy data of one cell: powers [T] (power of t per term,
+// 0 on the cell's terms, the others divided by the smallest positive one),
+// the Hermite form H (upper triangular, positive diagonal) and the unimodular
+// U with U D = H (D rows b_i - a_i), both n x n row-major, and the volume.
+int cell_tracking_data(int n, const int32_t *tpe, const uint8_t *exps, const int32_t *lift, const int32_t *pairs,
+                       double *powers, int64_t *H, int64_t *U, int64_t *volume);
 
 // Threads per block the tracker uses for n unknowns and a table of the given
 // size (fills up to the opt-in shared memory of one block).

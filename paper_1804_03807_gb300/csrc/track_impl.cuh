@@ -570,11 +570,11 @@ __global__ void __launch_bounds__(256) classify_kernel(const ClassifyLaunch L, s
     const SmTab tb = stage_table(L.tab, smem);
     const int bt = blockDim.x;
     const ThreadArrays A = thread_arrays<N>(smem, table_bytes, bt, false);
-    const int64_t np = L.n_paths;
+    const int64_t np = L.n_paths, xld = L.x_ld ? L.x_ld : np;
     for (int64_t q = (int64_t)blockIdx.x * bt + threadIdx.x; q < np; q += (int64_t)gridDim.x * bt) {
         phc_path_stats s = L.stats[q];
 #pragma unroll
-        for (int j = 0; j < N; j++) SL(A.xe, j) = L.x[(int64_t)j * np + q];
+        for (int j = 0; j < N; j++) SL(A.xe, j) = L.x[(int64_t)j * xld + q];
         const int8_t cls = classify_one<N>(tb, A, s, L.o, bt);
         L.stats[q] = s;
         L.cls[q] = cls;
