@@ -21,7 +21,8 @@ launch count.
 on the same workload instead.  ``--gpus N`` under torchrun runs N
 independent replicas (paths are independent; nothing is exchanged).
 ``--workload serving`` runs the serving workload alone; ``--workload
-configs`` measures all five workloads, one line each.
+configs`` measures all five workloads, one line each (``--configs 9,10,11``:
+cyclic 9 D=2 stages, double double tracking, polyhedral homotopies).
 """
 from __future__ import annotations
 
@@ -83,6 +84,19 @@ def unit_flops(tab_terms, n: int) -> float:
         f += (m + 1) + 6 + 6 * m + 8 * m * m
     f += 8 * n * (n - 1) + 6 * n
     return f
+
+
+def poly_unit_flops(sys_) -> float:
+    """FP64 flops of one unit of the polyhedral tracker: the terms of the
+    system itself (no start system), each with the coefficient c t^p and
+    c p t^(p-1) (6 flops; the exponential is not counted), and the LU and
+    solve of unit_flops."""
+    exps = np.asarray(sys_.exps, dtype=np.int64).reshape(-1, sys_.n_var)
+    terms = []
+    for e in exps:
+        nz = e[e > 0]
+        terms.append((len(nz), int((nz - 1).sum())))
+    return unit_flops(terms, sys_.n_var) + 2 * len(terms)
 
 
 def homotopy_terms(sys_):
@@ -691,6 +705,50 @@ def run_configs(args):
                 "classes": np.bincount(r.cls.cpu().numpy(), minlength=4).tolist(),
                 "fp64": {"paths_per_s": 5040 / (ms64 / 1e3), "ms": ms64}}
 
+    def config11():
+        """Polyhedral homotopies (Section 2.2) on random-coefficient cyclic
+        n systems (n = 7, 8, 9): the mixed cells on the host, the polyhedral
+        paths on the GPU (one launch for all cells), the two-stage pipeline
+        (cells made while the paths of the cells made so far are tracked),
+        and the total-degree homotopy of the same system for comparison."""
+        from workloads import cyclic, random_lifting, rng_for, unit_gamma, with_random_coefficients
+        res = []
+        for n in (7, 8, 9):
+            g = with_random_coefficients(cyclic(n), rng_for(600 + n))
+            lift = random_lifting(rng_for(610 + n), g.n_terms)
+            t0 = time.perf_counter()
+            cells, vols, mv = P.phc_mixed_cells(g, lift)
+            t_cells = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            h = P.phc_make_polyhedral_homotopy(g, lift, cells)
+            t_handle = time.perf_counter() - t0
+            ms = _timed(lambda: out.__setitem__("r", P.track_polyhedral(h)), 3, 1)
+            r = out["r"]
+            st = P.stats_numpy(r.stats)
+            units = int(st["n_solve"].sum())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = P.solve_polyhedral(g, lift, mv)
+            torch.cuda.synchronize()
+            t_pipe = time.perf_counter() - t0
+            same = bool(torch.equal(s.x, r.x))
+            ht = P.phc_make_homotopy(g, unit_gamma(rng_for(620 + n)))
+            mst = _timed(lambda: out.__setitem__("t", P.track(ht)), 1, 1)
+            ct = out["t"].cls.cpu().numpy()
+            stt = P.stats_numpy(out["t"].stats)
+            res.append({
+                "system": f"cyclic {n}, random coefficients", "mixed_volume": mv, "cells": int(cells.shape[0]),
+                "cells_s": t_cells, "handle_s": t_handle,
+                "track_ms": ms, "paths_per_s": mv / (ms / 1e3), "units": units,
+                "newton_steps_per_s": int(st["n_newton"].sum()) / (ms / 1e3),
+                "fp64_frac": units * poly_unit_flops(g) / (ms / 1e3) / peak,
+                "classes": np.bincount(r.cls.cpu().numpy(), minlength=4).tolist(),
+                "pipeline_s": t_pipe, "pipeline_equals_one_launch": same,
+                "total_degree": {"paths": int(ct.shape[0]), "ms": mst, "regular": int((ct == 0).sum()),
+                                 "units": int(stt["n_solve"].sum())},
+            })
+        return {"config": "polyhedral", "systems": res}
+
     def config5():
         sv, reqs = serving_session(args.requests, not args.no_big, args.slots, args.batch_paths)
         d = {"config": 5, "workload": f"{args.requests} Poisson (200/s) sparse requests"
@@ -703,7 +761,7 @@ def run_configs(args):
         return d
 
     want = [int(c) for c in args.configs.split(",")] if args.configs else [1, 2, 3, 4, 5]
-    table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9, 10: config10}
+    table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9, 10: config10, 11: config11}
     for c in want:
         print(json.dumps(table[c]()), flush=True)
     return 0
@@ -757,7 +815,8 @@ def main(argv=None):
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the cyclic 9 request")
     ap.add_argument("--batch-paths", type=int, default=60_000, help="serving: most paths per batch of small requests")
     ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default 1-5; 9 = the "
-                    "cyclic 9 D=2 request of the serving workload alone; 10 = double double tracking)")
+                    "cyclic 9 D=2 request of the serving workload alone; 10 = double double tracking; "
+                    "11 = polyhedral homotopies)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",

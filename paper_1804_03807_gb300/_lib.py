@@ -240,13 +240,15 @@ def phc_mixed_cells(sys, lift):
     w = np.ascontiguousarray(np.asarray(lift).reshape(-1), dtype=np.int32)
     n = int(sys.n_var)
     count, mv = ctypes.c_int64(), ctypes.c_int64()
-    _check(L.phc_mixed_cells(n, tpe.ctypes.data, exps.ctypes.data, w.ctypes.data, 0, None, None, ctypes.byref(count),
-                             ctypes.byref(mv)))
-    cells = np.zeros((max(count.value, 1), n, 2), dtype=np.int32)
-    vols = np.zeros(max(count.value, 1), dtype=np.int64)
-    _check(L.phc_mixed_cells(n, tpe.ctypes.data, exps.ctypes.data, w.ctypes.data, int(cells.shape[0]),
-                             cells.ctypes.data, vols.ctypes.data, ctypes.byref(count), ctypes.byref(mv)))
-    return cells[:count.value], vols[:count.value], int(mv.value)
+    cap = 1 << 16
+    while True:  # a second enumeration only when the first buffer was too small
+        cells = np.zeros((cap, n, 2), dtype=np.int32)
+        vols = np.zeros(cap, dtype=np.int64)
+        _check(L.phc_mixed_cells(n, tpe.ctypes.data, exps.ctypes.data, w.ctypes.data, cap, cells.ctypes.data,
+                                 vols.ctypes.data, ctypes.byref(count), ctypes.byref(mv)))
+        if count.value <= cap:
+            return cells[:count.value].copy(), vols[:count.value].copy(), int(mv.value)
+        cap = int(count.value)
 
 
 def phc_make_polyhedral_homotopy(sys, lift, cells) -> Homotopy:

@@ -19,7 +19,10 @@
 // problem of all pairs chosen so far feasible.  Complete choices are checked
 // exactly in 128-bit integer arithmetic.  The feasibility problems are linear
 // programs in double precision that only drop choices whose optimum is clearly
-// infeasible, so rounding can cost time but never a cell.
+// infeasible, so rounding can cost time but never a cell.  The edge tests,
+// the relation table and the subtrees below the first few equations run on
+// the host's threads; the cells come out in the order of the sequential
+// search whatever the number of threads.
 //
 // Feasibility of the chosen pairs P: maximize tau over (v, tau) with
 //   <a - b, v> = w(b) - w(a)                    for every pair (a, b) in P,
@@ -32,9 +35,13 @@
 // dense two-phase simplex below (Bland's rule) solves; an unbounded dual
 // means inconsistent equalities.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "phc_internal.h"
@@ -55,8 +62,10 @@ typedef __int128 i128;
 int simplex(int R, int C, const double *M, const double *b, const double *cost, double *val)
 {
     const int W = C + R + 1;
-    std::vector<double> T((size_t)(R + 1) * W, 0.0);
-    std::vector<int> basis(R);
+    thread_local std::vector<double> T;
+    thread_local std::vector<int> basis;
+    T.assign((size_t)(R + 1) * W, 0.0);
+    basis.assign(R, 0);
     double cmax = 0.0;
     for (int j = 0; j < C; j++) cmax = std::max(cmax, std::fabs(cost[j]));
     for (int i = 0; i < R; i++) {
@@ -162,7 +171,9 @@ bool feasible(const Lifted &L, const Pair *P, int np)
 {
     const int n = L.n;
     const int R = n + 1;
-    std::vector<double> cols, cost;  // column-major build, C columns of R
+    thread_local std::vector<double> cols, cost, M, rhs;  // cols: column-major, C columns of R
+    cols.clear();
+    cost.clear();
     for (int p = 0; p < np; p++) {
         const int i = P[p].eq, a = P[p].a, b = P[p].b;
         for (int c = L.off[i]; c < L.off[i] + L.m[i]; c++) {
@@ -184,7 +195,8 @@ bool feasible(const Lifted &L, const Pair *P, int np)
         }
     }
     const int C = (int)cost.size();
-    std::vector<double> M((size_t)R * C), rhs(R, 0.0);
+    M.resize((size_t)R * C);
+    rhs.assign(R, 0.0);
     for (int c = 0; c < C; c++)
         for (int r = 0; r < R; r++) M[(size_t)r * C + c] = cols[(size_t)c * R + r];
     rhs[n] = 1.0;
@@ -349,91 +361,211 @@ bool gcd_ext(int64_t a, int64_t b, int64_t *g, int64_t *s, int64_t *t)
 
 }  // namespace
 
+namespace {
+
+// Runs fn(k) for k = 0 .. count-1 on the host threads (each k once).
+void parallel_for(int64_t count, int threads, const std::function<void(int64_t)> &fn)
+{
+    std::atomic<int64_t> next(0);
+    auto body = [&]() {
+        for (int64_t k = next++; k < count; k = next++) fn(k);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; t++) pool.emplace_back(body);
+    body();
+    for (auto &th : pool) th.join();
+}
+
+int host_threads()
+{
+    unsigned h = std::thread::hardware_concurrency();
+    if (h < 1) h = 1;
+    if (h > 64) h = 64;
+    return (int)h;
+}
+
+// Depth-first search below a fixed prefix of pairs; the cells of one task.
+struct Walker {
+    const Lifted &L;
+    const std::vector<std::vector<Pair>> &edges;
+    const std::vector<int> &order, &eoff;
+    const std::vector<uint64_t> &rel;
+    int words;
+    std::vector<Pair> chosen, sorted;
+    std::vector<int> chosen_id;
+    std::vector<int32_t> cells;   // 2n term indices per cell
+    std::vector<int64_t> volumes;
+    int status = PHC_OK;          // error messages are set on the calling thread
+    const char *message = "";
+
+    Walker(const Lifted &l, const std::vector<std::vector<Pair>> &e, const std::vector<int> &o,
+           const std::vector<int> &eo, const std::vector<uint64_t> &r, int w)
+        : L(l), edges(e), order(o), eoff(eo), rel(r), words(w), chosen(l.n), sorted(l.n), chosen_id(l.n)
+    {
+    }
+    bool related(int a, int b) const { return (rel[(size_t)a * words + b / 64] >> (b % 64)) & 1ull; }
+    // chosen[0..d] is set and pairwise related
+    void visit(int d)
+    {
+        const int n = L.n;
+        if (d + 1 < n) {
+            if (d >= 1 && !feasible(L, chosen.data(), d + 1)) return;
+            walk(d + 1);
+            return;
+        }
+        for (int k = 0; k < n; k++) sorted[chosen[k].eq] = chosen[k];
+        i128 det = 0;
+        const int ex = exact_cell(L, sorted.data(), &det, nullptr);
+        if (ex == -1) {
+            status = PHC_EINVAL;
+            message = "mixed cells: lifting not in general position (a third point on a cell's lower facet); "
+                      "draw another lifting";
+            return;
+        }
+        if (ex == -2) {
+            status = PHC_EUNSUPPORTED;
+            message = "mixed cells: exact arithmetic overflows 128 bits";
+            return;
+        }
+        if (ex == 0) return;
+        const i128 vol = det < 0 ? -det : det;
+        if (vol > (i128)INT64_MAX) {
+            status = PHC_EUNSUPPORTED;
+            message = "mixed cells: cell volume above 2^63";
+            return;
+        }
+        for (int k = 0; k < n; k++) {
+            cells.push_back(sorted[k].a);
+            cells.push_back(sorted[k].b);
+        }
+        volumes.push_back((int64_t)vol);
+    }
+    void walk(int d)
+    {
+        const int i = order[d];
+        for (int e = 0; e < (int)edges[i].size() && !status; e++) {
+            const int ge = eoff[i] + e;
+            bool ok = true;
+            for (int k = 0; k < d && ok; k++) ok = related(chosen_id[k], ge);
+            if (!ok) continue;
+            chosen[d] = edges[i][e];
+            chosen_id[d] = ge;
+            visit(d);
+        }
+    }
+};
+
+}  // namespace
+
+// The search is split into tasks, one per related choice of edges of the
+// first equations of the order, run on the host threads; every task keeps its
+// cells, and the tasks' cells are emitted in task order from the calling
+// thread as the tasks finish -- the order, and so the cells' order, of the
+// sequential search.
 int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const int32_t *lift,
                           const std::function<int(const int32_t *pairs, int64_t volume)> &emit)
 {
     Lifted L;
     int rc = load(n, tpe, exps, lift, &L);
     if (rc) return rc;
+    const int threads = host_threads();
     // (1) lower edges of every lifted support on its own
-    std::vector<std::vector<Pair>> edges(n);
+    std::vector<Pair> all;
     for (int i = 0; i < n; i++)
         for (int a = L.off[i]; a < L.off[i] + L.m[i]; a++)
-            for (int b = a + 1; b < L.off[i] + L.m[i]; b++) {
-                const Pair p{i, a, b};
-                if (feasible(L, &p, 1)) edges[i].push_back(p);
-            }
+            for (int b = a + 1; b < L.off[i] + L.m[i]; b++) all.push_back(Pair{i, a, b});
+    std::vector<char> lower(all.size(), 0);
+    parallel_for((int64_t)all.size(), threads, [&](int64_t k) { lower[k] = feasible(L, &all[k], 1); });
+    std::vector<std::vector<Pair>> edges(n);
+    for (size_t k = 0; k < all.size(); k++)
+        if (lower[k]) edges[all[k].eq].push_back(all[k]);
     for (int i = 0; i < n; i++)
         if (edges[i].empty()) return PHC_OK;  // a support of one point: no cell, mixed volume 0
     std::vector<int> order(n);
     for (int i = 0; i < n; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return edges[x].size() < edges[y].size(); });
-    // (2) relation table: edge e of one equation and f of another, feasible together
+    // (2) relation table: edge e of one equation and f of a later one, feasible
+    // together (rows computed in parallel, then mirrored)
     std::vector<int> eoff(n + 1, 0);
     for (int i = 0; i < n; i++) eoff[i + 1] = eoff[i] + (int)edges[i].size();
     const int NE = eoff[n];
     const int words = (NE + 63) / 64;
     std::vector<uint64_t> rel((size_t)NE * words, 0);
+    std::vector<int> eq_of(NE);
     for (int i = 0; i < n; i++)
-        for (int e = 0; e < (int)edges[i].size(); e++) {
-            const int ge = eoff[i] + e;
-            for (int j = i + 1; j < n; j++)
-                for (int f = 0; f < (int)edges[j].size(); f++) {
-                    const Pair two[2] = {edges[i][e], edges[j][f]};
-                    if (!feasible(L, two, 2)) continue;
-                    const int gf = eoff[j] + f;
-                    rel[(size_t)ge * words + gf / 64] |= 1ull << (gf % 64);
-                    rel[(size_t)gf * words + ge / 64] |= 1ull << (ge % 64);
-                }
+        for (int e = eoff[i]; e < eoff[i + 1]; e++) eq_of[e] = i;
+    parallel_for(NE, threads, [&](int64_t ge) {
+        const int i = eq_of[ge];
+        const Pair &pe = edges[i][ge - eoff[i]];
+        for (int gf = eoff[i + 1]; gf < NE; gf++) {
+            const int j = eq_of[gf];
+            const Pair two[2] = {pe, edges[j][gf - eoff[j]]};
+            if (feasible(L, two, 2)) rel[(size_t)ge * words + gf / 64] |= 1ull << (gf % 64);
         }
-    // (3) depth first
-    std::vector<Pair> chosen(n), sorted(n);
-    std::vector<int> chosen_id(n);
-    std::vector<int32_t> pairs(2 * n);
-    int status = PHC_OK;
-    std::function<void(int)> walk = [&](int d) {
-        if (status) return;
-        const int i = order[d];
-        for (int e = 0; e < (int)edges[i].size() && !status; e++) {
-            const int ge = eoff[i] + e;
+    });
+    for (int ge = 0; ge < NE; ge++)
+        for (int gf = eoff[eq_of[ge] + 1]; gf < NE; gf++)
+            if ((rel[(size_t)ge * words + gf / 64] >> (gf % 64)) & 1ull) rel[(size_t)gf * words + ge / 64] |= 1ull << (ge % 64);
+    // (3) tasks: the related prefixes of the first P equations of the order,
+    // P the smallest depth that gives 32 tasks per thread (or n), in the
+    // order of the sequential search
+    std::vector<std::vector<int>> prefixes;
+    for (int e0 = eoff[order[0]]; e0 < eoff[order[0] + 1]; e0++) prefixes.push_back({e0});
+    int P = 1;
+    while (P < n && prefixes.size() < (size_t)32 * threads) {
+        std::vector<std::vector<int>> longer;
+        const int i = order[P];
+        for (const auto &pre : prefixes)
+            for (int ge = eoff[i]; ge < eoff[i + 1]; ge++) {
+                bool ok = true;
+                for (int x : pre) ok = ok && ((rel[(size_t)x * words + ge / 64] >> (ge % 64)) & 1ull);
+                if (!ok) continue;
+                longer.push_back(pre);
+                longer.back().push_back(ge);
+            }
+        prefixes.swap(longer);
+        P++;
+    }
+    const int64_t NT = (int64_t)prefixes.size();
+    std::vector<Walker *> done(NT, nullptr);
+    std::mutex mu;
+    std::condition_variable cv;
+    std::atomic<int64_t> next(0);
+    std::atomic<bool> stop(false);
+    auto worker = [&]() {
+        for (int64_t k = next++; k < NT && !stop; k = next++) {
+            Walker *w = new Walker(L, edges, order, eoff, rel, words);
+            const auto &pre = prefixes[k];
+            for (int d = 0; d < P; d++) {
+                const int i = order[d];
+                w->chosen[d] = edges[i][pre[d] - eoff[i]];
+                w->chosen_id[d] = pre[d];
+            }
+            // the tests the sequential search makes on the way to depth P - 1
             bool ok = true;
-            for (int k = 0; k < d && ok; k++)
-                ok = (rel[(size_t)chosen_id[k] * words + ge / 64] >> (ge % 64)) & 1ull;
-            if (!ok) continue;
-            chosen[d] = edges[i][e];
-            chosen_id[d] = ge;
-            if (d + 1 < n) {
-                if (d >= 1 && !feasible(L, chosen.data(), d + 1)) continue;
-                walk(d + 1);
-                continue;
-            }
-            for (int k = 0; k < n; k++) sorted[chosen[k].eq] = chosen[k];
-            i128 det = 0;
-            const int ex = exact_cell(L, sorted.data(), &det, nullptr);
-            if (ex == -1) {
-                status = set_error(PHC_EINVAL, "mixed cells: lifting not in general position (a third point on a "
-                                               "cell's lower facet); draw another lifting");
-                return;
-            }
-            if (ex == -2) {
-                status = set_error(PHC_EUNSUPPORTED, "mixed cells: exact arithmetic overflows 128 bits");
-                return;
-            }
-            if (ex == 0) continue;
-            for (int k = 0; k < n; k++) {
-                pairs[2 * k] = sorted[k].a;
-                pairs[2 * k + 1] = sorted[k].b;
-            }
-            const i128 vol = det < 0 ? -det : det;
-            if (vol > (i128)INT64_MAX) {
-                status = set_error(PHC_EUNSUPPORTED, "mixed cells: cell volume above 2^63");
-                return;
-            }
-            const int r = emit(pairs.data(), (int64_t)vol);
-            if (r) status = r;
+            for (int d = 1; d + 1 < P && ok; d++) ok = feasible(L, w->chosen.data(), d + 1);
+            if (ok) w->visit(P - 1);
+            std::lock_guard<std::mutex> lock(mu);
+            done[k] = w;
+            cv.notify_all();
         }
     };
-    walk(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; t++) pool.emplace_back(worker);
+    int status = PHC_OK;
+    for (int64_t k = 0; k < NT && !status; k++) {
+        Walker *w = nullptr;
+        {
+            std::unique_lock<std::mutex> lock(mu);
+            cv.wait(lock, [&] { return done[k] != nullptr; });
+            w = done[k];
+        }
+        if (w->status) status = set_error(w->status, w->message);
+        for (size_t c = 0; c < w->volumes.size() && !status; c++) status = emit(&w->cells[c * 2 * n], w->volumes[c]);
+    }
+    stop = true;
+    for (auto &th : pool) th.join();
+    for (Walker *w : done) delete w;
     return status;
 }
 
