@@ -707,13 +707,13 @@ def run_configs(args):
 
     def config11():
         """Polyhedral homotopies (Section 2.2) on random-coefficient cyclic
-        n systems (n = 7, 8, 9): the mixed cells on the host, the polyhedral
+        n systems (n = 7 .. 10): the mixed cells on the host, the polyhedral
         paths on the GPU (one launch for all cells), the two-stage pipeline
         (cells made while the paths of the cells made so far are tracked),
         and the total-degree homotopy of the same system for comparison."""
         from workloads import cyclic, random_lifting, rng_for, unit_gamma, with_random_coefficients
         res = []
-        for n in (7, 8, 9):
+        for n in (7, 8, 9, 10):
             g = with_random_coefficients(cyclic(n), rng_for(600 + n))
             lift = random_lifting(rng_for(610 + n), g.n_terms)
             t0 = time.perf_counter()
@@ -722,6 +722,11 @@ def run_configs(args):
             t0 = time.perf_counter()
             h = P.phc_make_polyhedral_homotopy(g, lift, cells)
             t_handle = time.perf_counter() - t0
+            variants = {}
+            for name, o in (("one_thread_per_path", P.phc_default_opts(group_paths=-1)),
+                            ("group_32", P.phc_default_opts(group_paths=1, tail_threads=32)),
+                            ("group_16", P.phc_default_opts(group_paths=1, tail_threads=16))):
+                variants[name] = _timed(lambda: P.track_polyhedral(h, opts=o), 3, 1)
             ms = _timed(lambda: out.__setitem__("r", P.track_polyhedral(h)), 3, 1)
             r = out["r"]
             st = P.stats_numpy(r.stats)
@@ -732,20 +737,23 @@ def run_configs(args):
             torch.cuda.synchronize()
             t_pipe = time.perf_counter() - t0
             same = bool(torch.equal(s.x, r.x))
-            ht = P.phc_make_homotopy(g, unit_gamma(rng_for(620 + n)))
-            mst = _timed(lambda: out.__setitem__("t", P.track(ht)), 1, 1)
-            ct = out["t"].cls.cpu().numpy()
-            stt = P.stats_numpy(out["t"].stats)
+            td = None
+            if n <= 9:  # cyclic 10: 3,628,800 total-degree paths, left out
+                ht = P.phc_make_homotopy(g, unit_gamma(rng_for(620 + n)))
+                mst = _timed(lambda: out.__setitem__("t", P.track(ht)), 1, 1)
+                ct = out["t"].cls.cpu().numpy()
+                stt = P.stats_numpy(out["t"].stats)
+                td = {"paths": int(ct.shape[0]), "ms": mst, "regular": int((ct == 0).sum()),
+                      "units": int(stt["n_solve"].sum())}
             res.append({
                 "system": f"cyclic {n}, random coefficients", "mixed_volume": mv, "cells": int(cells.shape[0]),
                 "cells_s": t_cells, "handle_s": t_handle,
-                "track_ms": ms, "paths_per_s": mv / (ms / 1e3), "units": units,
+                "track_ms": ms, "track_ms_variants": variants, "paths_per_s": mv / (ms / 1e3), "units": units,
                 "newton_steps_per_s": int(st["n_newton"].sum()) / (ms / 1e3),
                 "fp64_frac": units * poly_unit_flops(g) / (ms / 1e3) / peak,
                 "classes": np.bincount(r.cls.cpu().numpy(), minlength=4).tolist(),
                 "pipeline_s": t_pipe, "pipeline_equals_one_launch": same,
-                "total_degree": {"paths": int(ct.shape[0]), "ms": mst, "regular": int((ct == 0).sum()),
-                                 "units": int(stt["n_solve"].sum())},
+                "total_degree": td,
             })
         return {"config": "polyhedral", "systems": res}
 

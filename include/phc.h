@@ -133,6 +133,11 @@ typedef struct {
                                 paths to its lowest threads, so that warps without a path stop
                                 issuing (the arithmetic of a path does not change).  1 (default) on,
                                 0 off */
+    int32_t group_paths;     /* phc_track_polyhedral, phc_solve_polyhedral: 1 a group of threads per
+                                path (tail_threads of them; 0: 32 for up to 7 unknowns, else 16), -1
+                                one thread per path, 0 (default) a group per path unless the call's
+                                paths exceed 32 waves of the groups resident on the GPU at once (the
+                                same results either way) */
 } phc_opts;
 
 /* Per-path statistics (device array of these, optional). */

@@ -55,7 +55,7 @@ class phc_opts(ctypes.Structure):
         ("cond_regular", ctypes.c_double), ("res_regular", ctypes.c_double), ("slack_tol", ctypes.c_double),
         ("precision", ctypes.c_int32), ("fp32_t_max", ctypes.c_double), ("fp32_pivot_ratio", ctypes.c_double),
         ("block_threads", ctypes.c_int32), ("max_blocks", ctypes.c_int32), ("tail_drain", ctypes.c_double),
-        ("tail_threads", ctypes.c_int32), ("compact", ctypes.c_int32),
+        ("tail_threads", ctypes.c_int32), ("compact", ctypes.c_int32), ("group_paths", ctypes.c_int32),
     ]
 
 

@@ -75,6 +75,7 @@ extern "C" int phc_default_opts(phc_opts *o)
     o->tail_drain = 0.8;
     o->tail_threads = 0;
     o->compact = 1;
+    o->group_paths = 0;
     return PHC_OK;
 }
 
@@ -96,6 +97,7 @@ static int check_opts(const phc_opts &o)
     if (o.tail_threads != 0 && o.tail_threads != 8 && o.tail_threads != 16 && o.tail_threads != 32)
         return fail(PHC_EINVAL, "tail_threads must be 0, 8, 16 or 32");
     if (o.compact != 0 && o.compact != 1) return fail(PHC_EINVAL, "compact must be 0 or 1");
+    if (o.group_paths < -1 || o.group_paths > 1) return fail(PHC_EINVAL, "group_paths must be -1, 0 or 1");
     return PHC_OK;
 }
 

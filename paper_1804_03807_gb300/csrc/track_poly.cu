@@ -16,9 +16,11 @@
 // step logic of track_kernel's readings (RK4 predictor, Newton corrector,
 // step control, end Newton at t = 1); classification in classify_kernel at
 // t = 1, where every cell's homotopy is g.  For coefficients in general
-// position no polyhedral path diverges, so there is no tail hand-off: the
-// paths are few compared with a total-degree homotopy of the same system.
-#include "track_impl.cuh"
+// position no polyhedral path diverges, and the paths are few compared with a
+// total-degree homotopy of the same system: a launch whose paths fit in one
+// wave of groups runs a group of lanes per path instead (poly_group_kernel,
+// the tail kernels' tail_path), with the same results bit for bit.
+#include "tail_impl.cuh"
 
 namespace phc {
 
@@ -96,6 +98,42 @@ __global__ void __launch_bounds__(256) poly_starts_kernel(const PolyLaunch L)
     }
 }
 
+// Term q's coefficient in the cell's homotopy at t: c t^p in H and H_x, and
+// in the right-hand side c p t^(p-1) (H_t, dt) or c t^p (H); 0^0 = 1 and
+// p >= 1 when p != 0; lt = log t (unused at t = 0).
+__device__ __forceinline__ void poly_coef(double2 c, double p, double t, double lt, bool dt, double2 &ct, double2 &cr)
+{
+    double tp, dtp;
+    if (p == 0.0) {
+        tp = 1.0;
+        dtp = 0.0;
+    } else if (t == 0.0) {
+        tp = 0.0;
+        dtp = p == 1.0 ? 1.0 : 0.0;
+    } else {
+        tp = exp(p * lt);
+        dtp = p * tp / t;
+    }
+    ct = make_double2(c.x * tp, c.y * tp);
+    cr = dt ? make_double2(c.x * dtp, c.y * dtp) : ct;
+}
+
+// The same coefficients for tail_path (the grouped tracker), log t taken
+// once per t.
+struct PolyCoef {
+    const double2 *C;
+    const double *pw;
+    double last_t, lt;
+    __device__ __forceinline__ void operator()(int q, double te, bool dt, double2 &ct, double2 &cr)
+    {
+        if (te != last_t) {
+            last_t = te;
+            lt = te > 0.0 ? log(te) : 0.0;
+        }
+        poly_coef(C[q], __ldg(pw + q), te, lt, dt, ct, cr);
+    }
+};
+
 // J = H_x (row-major N x N) and R = H_t (dt) or H (!dt) at (X, t) for the
 // cell's homotopy sum_q c_q t^{p_q} y^{a_q}; lt = log t (unused at t = 0).
 template <int N>
@@ -109,21 +147,8 @@ __device__ __forceinline__ void evaluate_poly(const SmTab &tb, const double *pw,
     for (int i = 0; i < N * N; i++) st(J, i, bt, zero);
     for (int q = 0; q < tb.n_terms; q++) {
         const TermRec r = tb.terms[q];
-        const double2 c = tb.c1[q];
-        const double p = __ldg(pw + q);
-        double tp, dtp;  // t^p and p t^(p-1), with 0^0 = 1 (p >= 1 when p != 0)
-        if (p == 0.0) {
-            tp = 1.0;
-            dtp = 0.0;
-        } else if (t == 0.0) {
-            tp = 0.0;
-            dtp = p == 1.0 ? 1.0 : 0.0;
-        } else {
-            tp = exp(p * lt);
-            dtp = p * tp / t;
-        }
-        const double2 ct = make_double2(c.x * tp, c.y * tp);
-        const double2 cr = dt ? make_double2(c.x * dtp, c.y * dtp) : ct;
+        double2 ct, cr;
+        poly_coef(tb.c1[q], __ldg(pw + q), t, lt, dt, ct, cr);
         if (r.k == 0) {
             st(R, r.eq, bt, cadd(ld<double2>(R, r.eq, bt), cr));
             continue;
@@ -329,6 +354,52 @@ __global__ void __launch_bounds__(256) track_poly_kernel(const PolyLaunch L, siz
     }
 }
 
+// A group of G lanes per path (tail_path of tail_impl.cuh with the cell's
+// coefficients): the same operations in the same order as track_poly_kernel,
+// at a fraction of the latency per unit, for launches of few paths.
+template <int N, int G>
+__global__ void __launch_bounds__(128) poly_group_kernel(const PolyLaunch L, size_t table_bytes, size_t plan_bytes)
+{
+    extern __shared__ __align__(16) char smem[];
+    const SmTab tb = stage_table(L.tab, smem);
+    const TailPlan plan = plan_layout<N>(tb, smem + table_bytes);
+    if (threadIdx.x == 0) plan_fill<N>(tb, plan);
+    __syncthreads();
+    const int S = tail_store_slots(tb.n_terms, L.tab.n_ve);
+    const int lane = threadIdx.x & 31;
+    const int r = lane % G;  // the row this lane owns in the LU and the solves (r < N)
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - r));
+    const int group = threadIdx.x / G;
+    double2 *base = reinterpret_cast<double2 *>(smem + table_bytes + plan_bytes) +
+                    (size_t)group * tail_group_slots(N, S);
+    const int64_t np = L.n_paths, xld = L.x_ld ? L.x_ld : np;
+    for (;;) {
+        unsigned long long c = 0;
+        if (r == 0) c = atomicAdd(L.qhead, 1ull);
+        c = __shfl_sync(gmask, c, 0, G);
+        if (c >= (unsigned long long)np) break;
+        const int64_t q = (int64_t)c;
+        // a fresh path: t = 0 at the cell's binomial solution
+        Handoff hd;
+        double2 y[N];
+        const int cell = poly_start<N>(L, L.first + q, y);
+#pragma unroll
+        for (int j = 0; j < N; j++) hd.x0[j] = y[j];
+        hd.t = 0.0;
+        hd.h = L.o.h_init;
+        hd.next_s = 0.1;
+        hd.nx0 = hd.r0 = hd.r1 = hd.r2 = hd.r3 = hd.r4 = 0.0;
+        hd.q = q;
+        hd.sys = hd.streak = hd.steps = hd.since_ck = hd.nck = 0;
+        hd.n_acc = hd.n_rej = hd.n_newt = hd.n_solve = hd.n_f32 = hd.stage = 0;
+        const PolyCoef coef{tb.c1, L.powers + (size_t)cell * tb.n_terms, -1.0, 0.0};
+        tail_path<N, G>(hd, tb, plan, coef, base, L.o, r, gmask, [&](double2 x0r, const phc_path_stats &rec, int) {
+            if (r < N) L.x_out[(int64_t)r * xld + q] = x0r;
+            if (r == 0) L.stats[q] = rec;
+        });
+    }
+}
+
 template <int N>
 static cudaError_t launch_poly_starts_n(const PolyLaunch &L, cudaStream_t s)
 {
@@ -370,10 +441,97 @@ static cudaError_t launch_track_poly_n(const PolyLaunch &L, int block_threads, i
     return cudaGetLastError();
 }
 
+// The grouped launch: groups of G lanes in blocks of up to 128 threads, as
+// many blocks as are resident; *capacity = the groups resident at once (the
+// paths one wave takes).  launch = false only computes the capacity.
+template <int N, int G>
+static cudaError_t launch_poly_group_n(const PolyLaunch &L_in, int max_blocks, cudaStream_t s, bool launch,
+                                       int64_t *capacity)
+{
+    PolyLaunch L = L_in;
+    L.tab.coef_smem = 1;
+    size_t tb = table_smem_bytes(L.tab);
+    const size_t pb = tail_plan_bytes(N, L.tab.n_terms, L.tab.n_ve);
+    const size_t per_group = (size_t)tail_group_slots(N, tail_store_slots(L.tab.n_terms, L.tab.n_ve)) * sizeof(double2);
+    int groups = 128 / G;
+    if (tb + pb + groups * per_group > (size_t)g_smem_optin) {
+        L.tab.coef_smem = 0;  // coefficients through L1
+        tb = table_smem_bytes(L.tab);
+    }
+    while (groups > 1 && tb + pb + groups * per_group > (size_t)g_smem_optin) groups /= 2;
+    const size_t smem = tb + pb + groups * per_group;
+    if (smem > (size_t)g_smem_optin) return cudaErrorInvalidConfiguration;
+    const int bt = groups * G;
+    cudaError_t e = cudaFuncSetAttribute(poly_group_kernel<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, poly_group_kernel<N, G>, bt, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = (int64_t)g_num_sms * per_sm;
+    if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+    *capacity = grid * groups;
+    if (!launch) return cudaSuccess;
+    const int64_t want = (L.n_paths + groups - 1) / groups;
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    poly_group_kernel<N, G><<<(unsigned)grid, bt, smem, s>>>(L, tb, pb);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_poly_group_g(const PolyLaunch &L, int group, int max_blocks, cudaStream_t s, bool launch,
+                                       int64_t *capacity)
+{
+    if (group == 8 && N <= 8) return launch_poly_group_n<N, (N <= 8 ? 8 : 16)>(L, max_blocks, s, launch, capacity);
+    if (group == 16) return launch_poly_group_n<N, 16>(L, max_blocks, s, launch, capacity);
+    return launch_poly_group_n<N, 32>(L, max_blocks, s, launch, capacity);
+}
+
+// opts.group_paths: 1 a group per path, -1 one thread per path, 0 a group
+// per path unless the paths exceed 32 waves of the resident groups.  A group
+// runs a unit several times faster than one thread (the latency of the
+// longest paths sets the time of a launch of few paths), and measured faster
+// at every size tried (random cyclic 7 .. 10, 924 to 35,940 paths: 15 against
+// 95 ms, 20 against 94, 97 against 193, 546 against 610).  The group has
+// opts.tail_threads lanes, or by default 32 for N <= 7 and 16 above (the
+// faster of the two on those systems).
 cudaError_t launch_track_poly(const PolyLaunch &L, int block_threads, int max_blocks, cudaStream_t s)
 {
     device_limits();
     if (L.n_paths <= 0) return cudaSuccess;
+    const int gp = L.o.group_paths;
+    const int group = L.o.tail_threads ? L.o.tail_threads : (L.tab.n <= 7 ? 32 : 16);
+    const bool fits = tail_supported(L.tab);
+    bool grouped = gp == 1 && fits;
+    if (gp == 0 && fits) {
+        int64_t cap = 0;
+        cudaError_t e = cudaErrorInvalidValue;
+#define PHC_CALL_CAP(NN) launch_poly_group_g<NN>(L, group, max_blocks, s, false, &cap)
+        switch (L.tab.n) {
+        case 1: e = PHC_CALL_CAP(1); break;
+        case 2: e = PHC_CALL_CAP(2); break;
+        case 3: e = PHC_CALL_CAP(3); break;
+        case 4: e = PHC_CALL_CAP(4); break;
+        case 5: e = PHC_CALL_CAP(5); break;
+        case 6: e = PHC_CALL_CAP(6); break;
+        case 7: e = PHC_CALL_CAP(7); break;
+        case 8: e = PHC_CALL_CAP(8); break;
+        case 9: e = PHC_CALL_CAP(9); break;
+        case 10: e = PHC_CALL_CAP(10); break;
+        case 11: e = PHC_CALL_CAP(11); break;
+        case 12: e = PHC_CALL_CAP(12); break;
+        default: break;
+        }
+#undef PHC_CALL_CAP
+        grouped = e == cudaSuccess && L.n_paths <= 32 * cap;
+    }
+    if (grouped) {
+        int64_t cap = 0;
+#define PHC_CALL_TG(NN) launch_poly_group_g<NN>(L, group, max_blocks, s, true, &cap)
+        PHC_DISPATCH_N(L.tab.n, PHC_CALL_TG)
+#undef PHC_CALL_TG
+    }
 #define PHC_CALL_TP(NN) launch_track_poly_n<NN>(L, block_threads, max_blocks, s)
     PHC_DISPATCH_N(L.tab.n, PHC_CALL_TP)
 #undef PHC_CALL_TP

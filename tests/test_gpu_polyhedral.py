@@ -151,6 +151,26 @@ def test_random_cyclic7_copy_all_924_roots():
     assert np.array_equal(s.x.cpu().numpy().T, x)
 
 
+@pytest.mark.parametrize("n,seed,G", [(5, 540, 32), (7, 541, 16), (6, 542, 8)])
+def test_grouped_and_one_thread_trackers_give_the_same_bits(n, seed, G):
+    """A group of G lanes per path (tail_path) and one thread per path run
+    the same operations in the same order."""
+    g = with_random_coefficients(cyclic(n), rng_for(seed))
+    lift = random_lifting(rng_for(seed + 1), g.n_terms)
+    cells, _, mv = P.phc_mixed_cells(g, lift)
+    h = P.phc_make_polyhedral_homotopy(g, lift, cells)
+    one = P.track_polyhedral(h, opts=P.phc_default_opts(group_paths=-1))
+    grp = P.track_polyhedral(h, opts=P.phc_default_opts(group_paths=1, tail_threads=G))
+    auto = P.track_polyhedral(h)
+    for r in (grp, auto):
+        assert np.array_equal(r.x.cpu().numpy(), one.x.cpu().numpy())
+        assert np.array_equal(r.cls.cpu().numpy(), one.cls.cpu().numpy())
+        a, b = P.stats_numpy(r.stats), P.stats_numpy(one.stats)
+        for f in ("n_solve", "n_accept", "n_reject", "stop"):
+            assert np.array_equal(a[f], b[f]), f
+    assert np.all(one.cls.cpu().numpy() == P.PHC_REGULAR)
+
+
 def test_polyhedral_handle_edges():
     import torch
     g = with_random_coefficients(cyclic(4), rng_for(530))
