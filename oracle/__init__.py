@@ -83,6 +83,7 @@ def lib():
             build()
             L = ctypes.CDLL(_LIB_PATH)
             L.orc_track.restype = ctypes.c_int
+            L.orc_track_qd.restype = ctypes.c_int
             L.orc_num_paths.restype = ctypes.c_int64
             L.orc_refine.restype = ctypes.c_int
             assert L.orc_stats_size() == STATS_DTYPE.itemsize
@@ -232,6 +233,44 @@ def track_dd(h: Homotopy, starts: np.ndarray | None = None, first: int = 0, n_pa
     if rc != 0:
         raise ValueError(f"orc_track_dd failed: {rc}")
     return xh, xl, cls, stats
+
+
+def track_qd(h: Homotopy, starts: np.ndarray | None = None, first: int = 0, n_paths: int | None = None,
+             opts: Opts | None = None, threads: int | None = None):
+    """Track paths in complex quad double (Section 5, Table 2: the solver in
+    quad double arithmetic); returns (x [P, n, 4] complex128: the four parts
+    of every coordinate, cls, stats)."""
+    L = lib()
+    if starts is not None:
+        starts = np.ascontiguousarray(starts, dtype=np.complex128).reshape(-1, h.n)
+        n_paths = starts.shape[0]
+        sbuf = starts.view(np.float64).ctypes.data_as(ctypes.c_void_p)
+    else:
+        if n_paths is None:
+            n_paths = num_paths(h) - first
+        sbuf = None
+    x = np.zeros((n_paths, h.n, 4), dtype=np.complex128)
+    cls = np.zeros(n_paths, dtype=np.int8)
+    stats = np.zeros(n_paths, dtype=STATS_DTYPE)
+    o = opts if opts is not None else default_opts()
+    rc = L.orc_track_qd(h.ref(), sbuf, ctypes.c_int64(first), ctypes.c_int64(n_paths), ctypes.byref(o),
+                        int(threads or host_threads()), x.view(np.float64).ctypes.data_as(ctypes.c_void_p),
+                        cls.ctypes.data_as(ctypes.c_void_p), stats.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError(f"orc_track_qd failed: {rc}")
+    return x, cls, stats
+
+
+def qd_op(name: str, a, b):
+    """Quad double primitives for the exact-rational tests: name in qd_add,
+    qd_mul, qd_div; a, b and the result are four doubles."""
+    L = lib()
+    out = np.zeros(4)
+    ab = np.ascontiguousarray(a, dtype=np.float64)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    getattr(L, "orc_" + name)(ab.ctypes.data_as(ctypes.c_void_p), bb.ctypes.data_as(ctypes.c_void_p),
+                              out.ctypes.data_as(ctypes.c_void_p))
+    return out
 
 
 def endgame(h: Homotopy, first: int = 0, n_paths: int | None = None, opts: Opts | None = None):

@@ -1383,6 +1383,455 @@ int orc_track_dd(const orc_homotopy *h, const double *starts, int64_t first, int
     return 0;
 }
 
+/* ================================================================ quad double
+ * Quad double arithmetic (the paper runs the solver in double double and in
+ * quad double, Section 5 and Table 2, with the arithmetic of [HLB00]): a
+ * value is an unevaluated sum of four doubles x0 + x1 + x2 + x3 of
+ * decreasing magnitude.  Every operation here writes an expansion whose sum
+ * is the exact result (TwoSum and TwoProduct pairs; the partial products of
+ * order u^4 relative in plain double), and qd_from_expansion turns it into
+ * four components: sort the terms by decreasing magnitude and run TwoSum
+ * from the bottom up twice (the top term becomes the sum, rounded, and the
+ * others hold the exact rest), keep the top term, repeat on the rest.  Every
+ * step is error free, so the only error is the rest after the fourth term. */
+
+typedef struct { double x[4]; } qd;
+typedef struct { qd re, im; } cqd;
+
+#define QD_MAXTERMS 40
+#define END_TOL_QD 1e-58
+
+static void sort_by_magnitude(double *e, int m)
+{
+    for (int i = 1; i < m; i++) {
+        double v = e[i];
+        int k = i - 1;
+        while (k >= 0 && fabs(e[k]) < fabs(v)) { e[k + 1] = e[k]; k--; }
+        e[k + 1] = v;
+    }
+}
+
+static void sum_up(double *e, int m)
+{
+    for (int i = m - 1; i > 0; i--) {
+        dd s = two_sum(e[i - 1], e[i]);
+        e[i - 1] = s.hi;
+        e[i] = s.lo;
+    }
+}
+
+static qd qd_from_expansion(double *e, int m)
+{
+    qd r = {{0.0, 0.0, 0.0, 0.0}};
+    int lo = 0;
+    for (int k = 0; k < 4 && lo < m; k++) {
+        for (int pass = 0; pass < 2; pass++) {
+            sort_by_magnitude(e + lo, m - lo);
+            sum_up(e + lo, m - lo);
+        }
+        r.x[k] = e[lo];
+        lo++;
+    }
+    return r;
+}
+
+static qd qd_from(double a) { qd r = {{a, 0.0, 0.0, 0.0}}; return r; }
+static qd qd_neg(qd a) { qd r = {{-a.x[0], -a.x[1], -a.x[2], -a.x[3]}}; return r; }
+
+static qd qd_add(qd a, qd b)
+{
+    double e[8];
+    for (int i = 0; i < 4; i++) { e[2 * i] = a.x[i]; e[2 * i + 1] = b.x[i]; }
+    return qd_from_expansion(e, 8);
+}
+
+static qd qd_sub(qd a, qd b) { return qd_add(a, qd_neg(b)); }
+
+static qd qd_mul(qd a, qd b)
+{
+    double e[QD_MAXTERMS];
+    int m = 0;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            if (i + j <= 3) {
+                dd p = two_prod(a.x[i], b.x[j]);
+                e[m++] = p.hi;
+                e[m++] = p.lo;
+            } else if (i + j == 4) {
+                e[m++] = a.x[i] * b.x[j];
+            }
+        }
+    return qd_from_expansion(e, m);
+}
+
+static qd qd_mul_d(qd a, double b)
+{
+    double e[8];
+    for (int i = 0; i < 4; i++) {
+        dd p = two_prod(a.x[i], b);
+        e[2 * i] = p.hi;
+        e[2 * i + 1] = p.lo;
+    }
+    return qd_from_expansion(e, 8);
+}
+
+/* Long division: q_k = r_0 / b_0, r <- r - q_k b, five quotient digits. */
+static qd qd_div(qd a, qd b)
+{
+    double q[5];
+    qd r = a;
+    for (int k = 0; k < 5; k++) {
+        q[k] = r.x[0] / b.x[0];
+        if (k < 4) r = qd_sub(r, qd_mul_d(b, q[k]));
+    }
+    return qd_from_expansion(q, 5);
+}
+
+void orc_qd_add(const double *a, const double *b, double *out)
+{
+    qd x, y;
+    memcpy(x.x, a, sizeof x.x);
+    memcpy(y.x, b, sizeof y.x);
+    qd r = qd_add(x, y);
+    memcpy(out, r.x, sizeof r.x);
+}
+void orc_qd_mul(const double *a, const double *b, double *out)
+{
+    qd x, y;
+    memcpy(x.x, a, sizeof x.x);
+    memcpy(y.x, b, sizeof y.x);
+    qd r = qd_mul(x, y);
+    memcpy(out, r.x, sizeof r.x);
+}
+void orc_qd_div(const double *a, const double *b, double *out)
+{
+    qd x, y;
+    memcpy(x.x, a, sizeof x.x);
+    memcpy(y.x, b, sizeof y.x);
+    qd r = qd_div(x, y);
+    memcpy(out, r.x, sizeof r.x);
+}
+
+static cqd cqd_from(cplx z) { cqd r = { qd_from(creal(z)), qd_from(cimag(z)) }; return r; }
+static cqd cqd_add(cqd a, cqd b) { cqd r = { qd_add(a.re, b.re), qd_add(a.im, b.im) }; return r; }
+static cqd cqd_sub(cqd a, cqd b) { cqd r = { qd_sub(a.re, b.re), qd_sub(a.im, b.im) }; return r; }
+static cqd cqd_mul(cqd a, cqd b)
+{
+    cqd r = { qd_sub(qd_mul(a.re, b.re), qd_mul(a.im, b.im)), qd_add(qd_mul(a.re, b.im), qd_mul(a.im, b.re)) };
+    return r;
+}
+static cqd cqd_div(cqd a, cqd b)
+{
+    qd d = qd_add(qd_mul(b.re, b.re), qd_mul(b.im, b.im));
+    cqd num = { qd_add(qd_mul(a.re, b.re), qd_mul(a.im, b.im)), qd_sub(qd_mul(a.im, b.re), qd_mul(a.re, b.im)) };
+    cqd r = { qd_div(num.re, d), qd_div(num.im, d) };
+    return r;
+}
+static cqd cqd_scale(double a, cqd z) { cqd r = { qd_mul_d(z.re, a), qd_mul_d(z.im, a) }; return r; }
+static cqd cqd_ipow(cqd x, int e)
+{
+    cqd r = cqd_from(1.0);
+    for (int k = 0; k < e; k++) r = cqd_mul(r, x);
+    return r;
+}
+static double cqd_abs1(cqd a) { return fabs(a.re.x[0]) + fabs(a.im.x[0]); }
+static double cqd_absinf(cqd a) { double x = fabs(a.re.x[0]), y = fabs(a.im.x[0]); return x > y ? x : y; }
+
+/* H(x,t), H_x(x,t), H_t(x,t) in complex quad double, every monomial and
+ * partial derivative from scratch (as eval_homotopy); kinds 0..2. */
+static void eval_homotopy_qd(const orc_homotopy *h, const cqd *x, double t, cqd *H, cqd *Hx, cqd *Ht)
+{
+    const int n = h->n;
+    const cqd gamma = cqd_from(h->gamma_re + I * h->gamma_im);
+    const cqd one = cqd_from(1.0), zero = cqd_from(0.0);
+    const cqd w1 = { qd_sub(qd_from(1.0), qd_from(t)), qd_from(0.0) }; /* 1 - t, exact */
+    const cqd tt = cqd_from(t);
+    int off = 0;
+    for (int i = 0; i < n; i++) {
+        cqd f = zero, ft = zero;
+        for (int j = 0; j < n; j++) Hx[i * n + j] = zero;
+        for (int k = 0; k < h->terms_per_eq[i]; k++) {
+            const uint8_t *a = h->exps + (size_t)(off + k) * n;
+            const cqd c = cqd_from(coef_of(h, off + k));
+            cqd ct, dct;
+            if (h->kind == 0) {
+                ct = cqd_mul(tt, c);
+                dct = c;
+            } else if (h->kind == 2) {
+                const cqd c0 = cqd_from(h->coefs0[2 * (off + k)] + I * h->coefs0[2 * (off + k) + 1]);
+                const cqd gc0 = cqd_mul(gamma, c0);
+                ct = cqd_add(cqd_mul(w1, gc0), cqd_mul(tt, c));
+                dct = cqd_sub(c, gc0);
+            } else if (i == h->row && !is_unit(a, n, h->slack)) {
+                ct = cqd_mul(w1, c);
+                dct = cqd_sub(zero, c);
+            } else {
+                ct = c;
+                dct = zero;
+            }
+            cqd m = one;
+            for (int j = 0; j < n; j++) m = cqd_mul(m, cqd_ipow(x[j], a[j]));
+            f = cqd_add(f, cqd_mul(ct, m));
+            ft = cqd_add(ft, cqd_mul(dct, m));
+            for (int j = 0; j < n; j++) {
+                if (a[j] == 0) continue;
+                cqd d = cqd_scale((double)a[j], cqd_ipow(x[j], a[j] - 1));
+                for (int q = 0; q < n; q++)
+                    if (q != j) d = cqd_mul(d, cqd_ipow(x[q], a[q]));
+                Hx[i * n + j] = cqd_add(Hx[i * n + j], cqd_mul(ct, d));
+            }
+        }
+        if (h->kind == 0) {
+            /* start system g_i = x_i^{d_i} - 1, weighted by (1-t) gamma */
+            const int d = eq_degree(h, i, off);
+            const cqd g = cqd_sub(cqd_ipow(x[i], d), one);
+            const cqd w = cqd_mul(w1, gamma);
+            f = cqd_add(f, cqd_mul(w, g));
+            ft = cqd_sub(ft, cqd_mul(gamma, g));
+            Hx[i * n + i] = cqd_add(Hx[i * n + i], cqd_mul(w, cqd_scale((double)d, cqd_ipow(x[i], d - 1))));
+        }
+        H[i] = f;
+        Ht[i] = ft;
+        off += h->terms_per_eq[i];
+    }
+}
+
+/* Solves A y = b in place (b := y) by LU with partial pivoting by the largest
+ * |.|_1 of the leading parts (the first row on ties).  Returns -1 on a zero
+ * pivot. */
+static int lu_solve_qd(int n, cqd *A, cqd *b)
+{
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        double best = cqd_abs1(A[k * n + k]);
+        for (int i = k + 1; i < n; i++) {
+            double a = cqd_abs1(A[i * n + k]);
+            if (a > best) { best = a; p = i; }
+        }
+        if (!(best > 0.0)) return -1;
+        if (p != k) {
+            for (int j = 0; j < n; j++) { cqd tmp = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = tmp; }
+            cqd tmp = b[k]; b[k] = b[p]; b[p] = tmp;
+        }
+        for (int i = k + 1; i < n; i++) {
+            cqd l = cqd_div(A[i * n + k], A[k * n + k]);
+            for (int j = k + 1; j < n; j++) A[i * n + j] = cqd_sub(A[i * n + j], cqd_mul(l, A[k * n + j]));
+            b[i] = cqd_sub(b[i], cqd_mul(l, b[k]));
+        }
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        cqd s = b[i];
+        for (int j = i + 1; j < n; j++) s = cqd_sub(s, cqd_mul(A[i * n + j], b[j]));
+        b[i] = cqd_div(s, A[i * n + i]);
+    }
+    return 0;
+}
+
+static double vnorm_qd(int n, const cqd *v)
+{
+    double m = 0.0;
+    for (int j = 0; j < n; j++) {
+        double a = cqd_absinf(v[j]);
+        if (!(a <= m)) m = a;
+    }
+    return m;
+}
+
+static int all_finite_qd(int n, const cqd *x)
+{
+    for (int j = 0; j < n; j++)
+        for (int k = 0; k < 4; k++)
+            if (!isfinite(x[j].re.x[k]) || !isfinite(x[j].im.x[k])) return 0;
+    return 1;
+}
+
+static int tangent_qd(const orc_homotopy *h, const cqd *x, double t, cqd *v, orc_stats *st)
+{
+    cqd H[NMAX], Hx[NMAX * NMAX];
+    eval_homotopy_qd(h, x, t, H, Hx, v);
+    st->n_solve++;
+    if (lu_solve_qd(h->n, Hx, v)) return -1;
+    for (int j = 0; j < h->n; j++) v[j] = cqd_sub(cqd_from(0.0), v[j]);
+    return 0;
+}
+
+static double newton_step_qd(const orc_homotopy *h, cqd *x, double t, orc_stats *st)
+{
+    cqd H[NMAX], Hx[NMAX * NMAX], Ht[NMAX];
+    eval_homotopy_qd(h, x, t, H, Hx, Ht);
+    st->n_solve++;
+    st->n_newton++;
+    if (lu_solve_qd(h->n, Hx, H)) return NAN;
+    for (int j = 0; j < h->n; j++) x[j] = cqd_sub(x[j], H[j]);
+    return vnorm_qd(h->n, H);
+}
+
+/* track_one in complex quad double (the readings of track_one, step for
+ * step); the end Newton at t = 1 stops at ||dx|| <= END_TOL_QD (1 + ||x||). */
+static void track_one_qd(const orc_homotopy *h, const orc_opts *o, cqd *x, orc_stats *st)
+{
+    const int n = h->n;
+    cqd x0[NMAX], xs[NMAX], k1[NMAX], k2[NMAX], k3[NMAX], k4[NMAX];
+    double t = 0.0, step = o->h_init;
+    int streak = 0, steps = 0;
+    double ck[5];
+    int nck = 0;
+    double next_s = 0.1;
+    int since_ck = 0;
+    memset(st, 0, sizeof *st);
+    while (t < 1.0) {
+        double he = step;
+        double t1 = t + he;
+        if (he >= 1.0 - t) { he = 1.0 - t; t1 = 1.0; }
+        memcpy(x0, x, sizeof(cqd) * n);
+        const cqd hh = cqd_from(0.5 * he), hf = cqd_from(he), h6 = cqd_from(he / 6.0), two = cqd_from(2.0);
+        int ok = 1;
+        ok = ok && !tangent_qd(h, x0, t, k1, st);
+        for (int j = 0; j < n; j++) xs[j] = cqd_add(x0[j], cqd_mul(hh, k1[j]));
+        ok = ok && !tangent_qd(h, xs, t + 0.5 * he, k2, st);
+        for (int j = 0; j < n; j++) xs[j] = cqd_add(x0[j], cqd_mul(hh, k2[j]));
+        ok = ok && !tangent_qd(h, xs, t + 0.5 * he, k3, st);
+        for (int j = 0; j < n; j++) xs[j] = cqd_add(x0[j], cqd_mul(hf, k3[j]));
+        ok = ok && !tangent_qd(h, xs, t1, k4, st);
+        if (ok)
+            for (int j = 0; j < n; j++) {
+                cqd acc = cqd_add(cqd_add(k1[j], cqd_mul(two, k2[j])), cqd_add(cqd_mul(two, k3[j]), k4[j]));
+                x[j] = cqd_add(x0[j], cqd_mul(h6, acc));
+            }
+        int conv = 0;
+        double prev = INFINITY;
+        for (int it = 0; ok && it < o->max_corr_iters; it++) {
+            double d = newton_step_qd(h, x, t1, st);
+            if (!(d == d) || !all_finite_qd(n, x)) break;
+            if (d <= o->corr_tol * (1.0 + vnorm_qd(n, x))) { conv = 1; break; }
+            if (it > 0 && d > o->corr_contract * prev) break;
+            prev = d;
+        }
+        steps++;
+        if (conv) {
+            t = t1;
+            st->n_accept++;
+            while (1.0 - t <= next_s && next_s > 0.0) {
+                ck[nck % 5] = vnorm_qd(n, x);
+                nck++;
+                since_ck = 0;
+                next_s *= 0.1;
+                if (nck >= 40) next_s = 0.0;
+            }
+            if (vnorm_qd(n, x) > o->diverge_norm) { st->stop = 1; break; }
+            if (++streak >= o->expand_after) {
+                streak = 0;
+                step = step * o->expand;
+                if (step > o->h_max) step = o->h_max;
+            }
+        } else {
+            memcpy(x, x0, sizeof(cqd) * n);
+            st->n_reject++;
+            streak = 0;
+            step = he * o->shrink;
+            if (step < o->h_min) { st->stop = 2; break; }
+        }
+        if (steps >= o->max_steps) { st->stop = 3; break; }
+        if (++since_ck >= o->max_steps_decade && t < 1.0) { st->stop = 3; break; }
+    }
+    st->t = t;
+    st->h = step;
+    int grew = 0;
+    st->growth = 0.0;
+    if (nck >= 2) {
+        int l = nck - 1, m = l < 4 ? l : 4;
+        double a = ck[l % 5], b = ck[(l - m) % 5], g = 1.0;
+        for (int k = 0; k < m; k++) g *= o->growth_inf;
+        grew = a > b * g;
+        st->growth = log10(a / b) / m;
+    }
+    cplx xh[NMAX];
+    if (!all_finite_qd(n, x)) { st->stop = 4; st->cls = ORC_FAILED; st->norm_x = NAN; st->cond = NAN; st->relres = NAN; return; }
+    st->norm_x = vnorm_qd(n, x);
+    if (st->stop == 1) { st->cls = ORC_AT_INFINITY; st->cond = INFINITY; st->relres = NAN; return; }
+    if (st->stop != 0) {
+        for (int j = 0; j < n; j++) xh[j] = x[j].re.x[0] + I * x[j].im.x[0];
+        end_measures(h, xh, &st->cond, &st->relres);
+        if (st->norm_x > o->endpoint_inf_norm || (t >= o->end_zone && grew)) st->cls = ORC_AT_INFINITY;
+        else if (t < o->end_zone) st->cls = ORC_FAILED;
+        else st->cls = ORC_SINGULAR;
+        return;
+    }
+    for (int it = 0; it < o->end_iters; it++) {
+        double d = newton_step_qd(h, x, 1.0, st);
+        if (!(d == d) || !all_finite_qd(n, x)) break;
+        if (d <= END_TOL_QD * (1.0 + vnorm_qd(n, x))) break;
+    }
+    if (!all_finite_qd(n, x)) { st->stop = 4; st->cls = ORC_FAILED; st->norm_x = NAN; st->cond = NAN; st->relres = NAN; return; }
+    st->norm_x = vnorm_qd(n, x);
+    for (int j = 0; j < n; j++) xh[j] = x[j].re.x[0] + I * x[j].im.x[0];
+    end_measures(h, xh, &st->cond, &st->relres);
+    if (st->norm_x > o->endpoint_inf_norm) st->cls = ORC_AT_INFINITY;
+    else if (st->cond <= o->cond_regular && st->relres <= o->res_regular) st->cls = ORC_REGULAR;
+    else st->cls = ORC_SINGULAR;
+}
+
+typedef struct {
+    const orc_homotopy *h;
+    const orc_opts *o;
+    const double *starts; /* [n_paths][n][2] or NULL */
+    int64_t first, n_paths;
+    double *x_out;        /* [n_paths][n][4][2] */
+    int8_t *cls_out;
+    orc_stats *stats_out;
+    atomic_llong next;
+} crew_qd_t;
+
+static void *crew_qd_worker(void *arg)
+{
+    crew_qd_t *c = (crew_qd_t *)arg;
+    const int n = c->h->n;
+    cqd x[NMAX];
+    cplx xs[NMAX];
+    orc_stats st;
+    for (;;) {
+        int64_t q = atomic_fetch_add(&c->next, 1);
+        if (q >= c->n_paths) break;
+        if (c->starts)
+            for (int j = 0; j < n; j++) xs[j] = c->starts[(q * n + j) * 2] + I * c->starts[(q * n + j) * 2 + 1];
+        else
+            start_solution(c->h, c->first + q, xs);
+        for (int j = 0; j < n; j++) x[j] = cqd_from(xs[j]);
+        track_one_qd(c->h, c->o, x, &st);
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < 4; k++) {
+                c->x_out[((q * n + j) * 4 + k) * 2] = x[j].re.x[k];
+                c->x_out[((q * n + j) * 4 + k) * 2 + 1] = x[j].im.x[k];
+            }
+        if (c->cls_out) c->cls_out[q] = (int8_t)st.cls;
+        if (c->stats_out) c->stats_out[q] = st;
+    }
+    return NULL;
+}
+
+/* Track paths in complex quad double (see track_one_qd); x_out receives the
+ * four parts of every endpoint coordinate, [n_paths][n][4] complex. */
+int orc_track_qd(const orc_homotopy *h, const double *starts, int64_t first, int64_t n_paths, const orc_opts *o_in,
+                 int n_threads, double *x_out, int8_t *cls_out, orc_stats *stats_out)
+{
+    orc_opts o;
+    if (o_in) o = *o_in; else orc_default_opts(&o);
+    if (h->n < 1 || h->n > NMAX || n_paths < 0) return -1;
+    if (!starts && h->kind != 0) return -1;
+    if (h->kind == 3) return -1; /* quad double tracking covers kinds 0..2 */
+    crew_qd_t c;
+    c.h = h; c.o = &o; c.starts = starts; c.first = first; c.n_paths = n_paths;
+    c.x_out = x_out; c.cls_out = cls_out; c.stats_out = stats_out;
+    atomic_init(&c.next, 0);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads == 1) { crew_qd_worker(&c); return 0; }
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * n_threads);
+    for (int k = 0; k < n_threads; k++) pthread_create(&th[k], NULL, crew_qd_worker, &c);
+    for (int k = 0; k < n_threads; k++) pthread_join(th[k], NULL);
+    free(th);
+    return 0;
+}
+
 /* Size of the stats record, so the Python side can check its mirror. */
 int orc_stats_size(void) { return (int)sizeof(orc_stats); }
 int orc_opts_size(void) { return (int)sizeof(orc_opts); }

@@ -144,3 +144,28 @@ def term_scales(sys, x: np.ndarray) -> np.ndarray:
             out[i] += (abs(c.real) + abs(c.imag)) * (abs(v.real) + abs(v.imag))
         off += m
     return out
+
+
+def exact_residual_parts(sys, parts: np.ndarray) -> float:
+    """exact_residual at the point sum_k parts[:, k] (complex [n, K], the
+    parts of a multiple-double number), every part taken exactly."""
+    xs = [(sum(Fraction(float(v.real)) for v in row), sum(Fraction(float(v.imag)) for v in row)) for row in parts]
+    worst = 0.0
+    off = 0
+    for i in range(sys.n_eq):
+        m = int(sys.terms_per_eq[i])
+        acc = (Fraction(0), Fraction(0))
+        scale = 0.0
+        for k in range(m):
+            c = frac_complex(complex(sys.coefs[off + k]))
+            mon = (Fraction(1), Fraction(0))
+            for j, a in enumerate(sys.exps[off + k]):
+                for _ in range(int(a)):
+                    mon = _cmul(mon, xs[j])
+            term = _cmul(c, mon)
+            acc = (acc[0] + term[0], acc[1] + term[1])
+            scale += abs(complex(sys.coefs[off + k])) * abs(complex(float(mon[0]), float(mon[1])))
+        val = abs(complex(float(acc[0]), float(acc[1])))
+        worst = max(worst, val / (1.0 + scale))
+        off += m
+    return worst
