@@ -237,6 +237,20 @@ int phc_track_paths(phc_homotopy *h, int64_t first_path, int64_t n_paths, const 
 int phc_track_paths_dd(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_hi,
                        phc_cd *x_lo, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
 
+/* Track paths first_path .. first_path+n_paths-1 of a total-degree handle in
+ * complex quad double (Section 5 and Table 2 run the solver in quad double;
+ * its arithmetic is [HLB00]'s): the readings of phc_track_paths with the
+ * point, the predictor stages, H, H_x, H_t, the LU and the solves in quad
+ * double (t, step sizes and norms in double, from the leading parts); the end
+ * Newton at t = 1 stops at ||dx|| <= 1e-58 (1 + ||x||).  x_out: device SoA
+ * [4][n_var][n_paths], part k of coordinate j of entry q at
+ * x_out[(k * n_var + j) * n_paths + q], the parts of decreasing magnitude and
+ * their sum the endpoint; cls_out and stats_out as phc_track_paths (the
+ * class from the leading parts).  One thread per path, its arrays in local
+ * memory; no tail hand-off.  Errors: as phc_track_paths_dd. */
+int phc_track_paths_qd(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts, phc_cd *x_out,
+                       int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
+
 /* The Cauchy endgame for singular endpoints (the paper distinguishes
  * isolated multiple solutions from regular ones, Section 4; Example 4.1's
  * point (2, 0) has multiplicity two).  A path converging to a singular

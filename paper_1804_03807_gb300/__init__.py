@@ -34,7 +34,7 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square,
                    phc_many_plan_create, phc_many_plan_run, ManyPlan, phc_track_paths_dd, phc_endgame,
                    phc_mixed_cells, phc_make_polyhedral_homotopy, phc_polyhedral_starts, phc_track_polyhedral,
-                   phc_solve_polyhedral)
+                   phc_solve_polyhedral, phc_track_paths_qd)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -49,6 +49,7 @@ __all__ = [
     "phc_track_paths_dd", "track_dd", "phc_endgame", "endgame",
     "phc_mixed_cells", "phc_make_polyhedral_homotopy", "phc_polyhedral_starts", "phc_track_polyhedral",
     "phc_solve_polyhedral", "polyhedral_starts", "track_polyhedral", "solve_polyhedral",
+    "phc_track_paths_qd", "track_qd",
 ]
 
 
@@ -216,3 +217,15 @@ def solve_polyhedral(sys, lift, max_paths: int, opts=None, stream=None, device="
     x, cls, st = _alloc(sys.n_var, max(max_paths, 1), device)
     mv, _ = phc_solve_polyhedral(sys, lift, opts, max_paths, x, cls, st, stream)
     return Tracked(x[:, :mv], cls[:mv], st[:mv])
+
+
+def track_qd(h: Homotopy, first: int = 0, n_paths: int | None = None, opts=None, stream=None, device="cuda"):
+    """Total-degree paths tracked in complex quad double; returns (Tracked
+    with the leading parts in x, the parts complex128 [4, n_var, P])."""
+    import torch
+    if n_paths is None:
+        n_paths = phc_num_paths(h) - first
+    parts = torch.empty((4, h.n, n_paths), dtype=torch.complex128, device=device)
+    _, cls, st = _alloc(h.n, n_paths, device)
+    phc_track_paths_qd(h, first, n_paths, opts, parts, cls, st, stream)
+    return Tracked(parts[0], cls, st), parts

@@ -96,6 +96,7 @@ def load() -> ctypes.CDLL:
                             ctypes.POINTER(ctypes.POINTER(phc_system_lists))]
     L.phc_track_paths_dd.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp, vp]
     L.phc_endgame.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
+    L.phc_track_paths_qd.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_many_plan_create.argtypes = [vp, i32, ctypes.POINTER(phc_opts), vp, vp, vp, vp, ctypes.POINTER(vp)]
     L.phc_many_plan_run.argtypes = [vp, vp]
     L.phc_many_plan_destroy.argtypes = [vp]
@@ -131,7 +132,7 @@ def load() -> ctypes.CDLL:
                  "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
                  "phc_square", "phc_many_plan_create", "phc_many_plan_run", "phc_track_paths_dd", "phc_endgame",
                  "phc_mixed_cells", "phc_make_polyhedral_homotopy", "phc_polyhedral_starts",
-                 "phc_track_polyhedral", "phc_solve_polyhedral"):
+                 "phc_track_polyhedral", "phc_solve_polyhedral", "phc_track_paths_qd"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
         raise ImportError("phc_opts layout mismatch between phc.h and the binding")
@@ -344,6 +345,14 @@ def phc_track_paths_dd(h: Homotopy, first_path: int, n_paths: int, opts, x_hi, x
     _check(load().phc_track_paths_dd(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
                                      ctypes.byref(opts) if opts is not None else None, _ptr(x_hi), _ptr(x_lo),
                                      _ptr(cls_out), _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_track_paths_qd(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls_out, stats_out=None,
+                       stream=None):
+    """x_out: complex128 CUDA tensor [4, n_var, n_paths] (the four parts)."""
+    _check(load().phc_track_paths_qd(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
+                                     ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cls_out),
+                                     _ptr(stats_out), _stream_ptr(stream)))
 
 
 def phc_endgame(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cycle_out, stats_out=None, stream=None):

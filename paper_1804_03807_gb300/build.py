@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["track.cu", "track_pipe.cu", "track_multi.cu", "track_tail.cu", "track_dd.cu", "endgame.cu", "track_poly.cu", "refine.cu",
+SOURCES = ["track.cu", "track_pipe.cu", "track_multi.cu", "track_tail.cu", "track_dd.cu", "track_qd.cu", "endgame.cu", "track_poly.cu", "refine.cu",
            "noalloc.cu", "mixed_cells.cpp", "phc_api.cpp"]
 
 

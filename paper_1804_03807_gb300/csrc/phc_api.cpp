@@ -726,6 +726,60 @@ extern "C" int phc_track_paths_dd(phc_homotopy *h, int64_t first, int64_t n, con
     return PHC_OK;
 }
 
+extern "C" int phc_track_paths_qd(phc_homotopy *h, int64_t first, int64_t n, const phc_opts *opts, phc_cd *x_out,
+                                  int8_t *cls_out, phc_path_stats *stats_out, void *stream)
+{
+    if (!h) return fail(PHC_EINVAL, "NULL handle");
+    if (h->parameter && n > 0)
+        return fail(PHC_EINVAL, "a parameter homotopy has no total-degree start system");
+    if (h->polyhedral) return fail(PHC_EINVAL, "a polyhedral handle is tracked by phc_track_polyhedral");
+    if (n < 0 || first < 0 || first + n > h->num_paths)
+        return fail(PHC_EINVAL, "path range [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + n), (long long)h->num_paths);
+    if (n == 0) return PHC_OK;
+    if (!x_out || !cls_out) return fail(PHC_EINVAL, "NULL output array");
+    phc_opts o;
+    if (opts) o = *opts; else phc_default_opts(&o);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    phc_path_stats *st = stats_out;
+    if (!st) {
+        rc = ensure_stats(h, n, s);
+        if (rc) return rc;
+        st = h->d_stats;
+    }
+    CU(cudaMemsetAsync(h->d_qhead, 0, sizeof(unsigned long long), s));
+    if (h->d_tailc) CU(cudaMemsetAsync(h->d_tailc, 0, 4 * sizeof(unsigned long long), s));  // no hand-off here
+    phc::TrackLaunch L{};
+    L.tab = h->total.view;
+    L.tab.f32 = 0;
+    L.start_mode = 0;
+    L.deg = h->d_deg;
+    L.root_off = h->d_root_off;
+    L.roots = h->d_roots;
+    L.first = first;
+    L.n_paths = n;
+    L.paths_per_system = h->paths_per_system > 0 ? h->paths_per_system : 1;
+    L.x_out = reinterpret_cast<double2 *>(x_out);
+    L.stats = st;
+    L.qhead = h->d_qhead;
+    L.o = o;
+    cudaError_t e = phc::launch_track_qd(L, o.block_threads, o.max_blocks, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "quad double track kernel launch: %s", cudaGetErrorString(e));
+    phc::ClassifyLaunch C{};
+    C.tab = end_table(h);
+    C.tab.f32 = 0;
+    C.n_paths = n;
+    C.x = L.x_out;  // the leading parts
+    C.stats = st;
+    C.cls = cls_out;
+    C.o = o;
+    e = phc::launch_classify(C, s);
+    if (e != cudaSuccess) return fail(PHC_ECUDA, "classify kernel launch: %s", cudaGetErrorString(e));
+    return PHC_OK;
+}
+
 extern "C" int phc_endgame(phc_homotopy *h, int64_t first, int64_t n, const phc_opts *opts, phc_cd *x_out,
                            int32_t *cycle_out, phc_path_stats *stats_out, void *stream)
 {

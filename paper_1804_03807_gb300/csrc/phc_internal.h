@@ -251,6 +251,10 @@ cudaError_t launch_classify(const ClassifyLaunch &L, cudaStream_t s);
 // Total-degree paths of L tracked in complex double double (track_dd.cu):
 // double parts to L.x_out, low parts to L.x_out2, records to L.stats.
 cudaError_t launch_track_dd(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
+// Total-degree paths of L tracked in complex quad double (track_qd.cu): the
+// four parts of every coordinate to L.x_out, SoA [4][n][n_paths] (part-major),
+// records to L.stats.
+cudaError_t launch_track_qd(const TrackLaunch &L, int block_threads, int max_blocks, cudaStream_t s);
 // The Cauchy endgame of the total-degree paths of L (endgame.cu): estimates
 // to L.x_out, records to L.stats, cycle numbers (0: no estimate) to cycle_out.
 cudaError_t launch_endgame(const TrackLaunch &L, int32_t *cycle_out, int block_threads, int max_blocks, cudaStream_t s);
