@@ -705,6 +705,27 @@ def run_configs(args):
                 "classes": np.bincount(r.cls.cpu().numpy(), minlength=4).tolist(),
                 "fp64": {"paths_per_s": 5040 / (ms64 / 1e3), "ms": ms64}}
 
+    def config12():
+        """The precision ladder of Section 5 and Table 2 (the solver in double,
+        double double and quad double): the total-degree paths of one
+        random-coefficient cyclic 7 copy (5040 paths) tracked in each."""
+        w = configs.cyclic7_batch()
+        h = P.phc_make_homotopy(w.systems[1], w.gammas[1])
+        P.track_qd(h, n_paths=64)  # first launch: module and local memory set-up
+        ms_qd = _timed(lambda: out.__setitem__("q", P.track_qd(h)), 1, 0)
+        r, _ = out["q"]
+        ms_dd = _timed(lambda: out.__setitem__("d", P.track_dd(h)), 1, 1)
+        ms64 = _timed(lambda: out.__setitem__("f", P.track(h)), 3, 1)
+        st = P.stats_numpy(r.stats)
+        cls = {k: np.bincount(out[k][0].cls.cpu().numpy() if k != "f" else out[k].cls.cpu().numpy(),
+                              minlength=4).tolist() for k in ("q", "d", "f")}
+        return {"config": "precision ladder", "workload": "cyclic 7 random copy 1, 5040 total-degree paths",
+                "double": {"ms": ms64, "paths_per_s": 5040 / (ms64 / 1e3), "classes": cls["f"]},
+                "double_double": {"ms": ms_dd, "paths_per_s": 5040 / (ms_dd / 1e3), "classes": cls["d"]},
+                "quad_double": {"ms": ms_qd, "paths_per_s": 5040 / (ms_qd / 1e3), "classes": cls["q"],
+                                "units": int(st["n_solve"].sum())},
+                "ratios": {"dd_over_d": ms_dd / ms64, "qd_over_d": ms_qd / ms64, "qd_over_dd": ms_qd / ms_dd}}
+
     def config11():
         """Polyhedral homotopies (Section 2.2) on random-coefficient cyclic
         n systems (n = 7 .. 10): the mixed cells on the host, the polyhedral
@@ -769,7 +790,8 @@ def run_configs(args):
         return d
 
     want = [int(c) for c in args.configs.split(",")] if args.configs else [1, 2, 3, 4, 5]
-    table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9, 10: config10, 11: config11}
+    table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9, 10: config10, 11: config11,
+             12: config12}
     for c in want:
         print(json.dumps(table[c]()), flush=True)
     return 0
@@ -824,7 +846,7 @@ def main(argv=None):
     ap.add_argument("--batch-paths", type=int, default=60_000, help="serving: most paths per batch of small requests")
     ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default 1-5; 9 = the "
                     "cyclic 9 D=2 request of the serving workload alone; 10 = double double tracking; "
-                    "11 = polyhedral homotopies)")
+                    "11 = polyhedral homotopies; 12 = double, double double and quad double tracking)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",
