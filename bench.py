@@ -799,11 +799,24 @@ def run_configs(args):
 
 def profile_case(which: str = "cyclic7"):
     """A small case of a bench kernel, run twice: one random-coefficient
-    cyclic 7 system (5040 paths, track_kernel single mode) or 40 systems of
-    the sparse batch (track_kernel multi-system mode)."""
+    cyclic 7 system (5040 paths, track_kernel single mode), 40 systems of
+    the sparse batch (track_kernel multi-system mode), or the polyhedral
+    paths of a random cyclic 7 system (924 paths, poly_group_kernel)."""
     import torch
     import paper_1804_03807_gb300 as P
     from workloads import configs
+    if which == "polyhedral":
+        from workloads import cyclic, random_lifting, rng_for, with_random_coefficients
+        g = with_random_coefficients(cyclic(7), rng_for(607))
+        lift = random_lifting(rng_for(617), g.n_terms)
+        cells, _, mv = P.phc_mixed_cells(g, lift)
+        h = P.phc_make_polyhedral_homotopy(g, lift, cells)
+        for _ in range(2):
+            r = P.track_polyhedral(h)
+            torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "polyhedral cyclic7", "paths": mv,
+                          "units": int(P.stats_numpy(r.stats)["n_solve"].sum())}))
+        return 0
     if which == "sparse":
         w = configs.sparse_batch(count=40, seed=4)
         hs = [P.phc_make_homotopy(s, g) for s, g in zip(w.systems, w.gammas)]
@@ -851,7 +864,8 @@ def main(argv=None):
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",
                     help="default workload: leave out the batching numbers (256 sparse systems)")
-    ap.add_argument("--profile-case", nargs="?", const="cyclic7", default=None, choices=["cyclic7", "sparse"],
+    ap.add_argument("--profile-case", nargs="?", const="cyclic7", default=None,
+                    choices=["cyclic7", "sparse", "polyhedral"],
                     help="run a small case of a bench kernel twice (for ncu) and exit")
     args = ap.parse_args(argv)
     if args.profile_case:
