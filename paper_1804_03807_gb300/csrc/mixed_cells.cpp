@@ -12,8 +12,9 @@
 //       <a, v> + w(a) = beta_i  on the pair,  > beta_i  on the rest of A_i.
 //   Its volume is |det D|, D the integer matrix with rows b_i - a_i.
 //
-// Enumeration: depth first over the equations, the one with the fewest lower
-// edges first.  A pair of the next equation must (1) be a lower edge of its own
+// Enumeration: depth first over the equations, at every node the equation
+// with the fewest edges related to all edges chosen so far (a node where one
+// has none is a dead end).  A pair of the next equation must (1) be a lower edge of its own
 // lifted support, (2) be compatible with every pair chosen so far (a relation
 // table of two-pair feasibility problems, solved once) and (3) keep the
 // problem of all pairs chosen so far feasible.  Complete choices are checked
@@ -207,6 +208,211 @@ bool feasible(const Lifted &L, const Pair *P, int np)
     return val > -1e-7 * (1.0 + L.wmax);
 }
 
+// The same dual problem kept along the depth-first search: a node's problem
+// is its parent's with the columns of one more pair, so the parent's final
+// basis stays feasible and the simplex continues from it (a few pivots)
+// instead of starting over.  The state holds the columns in the current
+// basis' coordinates (B^-1 M), B^-1 itself, B^-1 r, the reduced costs and
+// the multipliers.
+struct DualLP {
+    int R = 0, C = 0;
+    std::vector<double> A;     // column j at A[j * R ..]: B^-1 M_j
+    std::vector<double> Binv;  // R x R row-major
+    std::vector<double> rhs;   // B^-1 r
+    std::vector<double> d;     // reduced costs of the real columns
+    std::vector<double> cost;  // costs of the real columns
+    std::vector<double> pi;    // multipliers c_B^T B^-1
+    std::vector<int> basis;    // column of each row; -1 - k for the artificial of row k
+    double z = 0.0, cmax = 0.0;
+    int status = 0;            // 0 optimal, 1 unbounded, 2 infeasible, 3 no answer
+
+    void pivot(int r, int e)
+    {
+        const double p = A[(size_t)e * R + r];
+        for (int j = 0; j < C; j++) A[(size_t)j * R + r] /= p;
+        for (int k = 0; k < R; k++) Binv[(size_t)r * R + k] /= p;
+        rhs[r] /= p;
+        for (int i = 0; i < R; i++) {
+            if (i == r) continue;
+            const double f = A[(size_t)e * R + i];
+            if (f == 0.0) continue;
+            for (int j = 0; j < C; j++) A[(size_t)j * R + i] -= f * A[(size_t)j * R + r];
+            for (int k = 0; k < R; k++) Binv[(size_t)i * R + k] -= f * Binv[(size_t)r * R + k];
+            rhs[i] -= f * rhs[r];
+        }
+        const double f = d[e];
+        if (f != 0.0) {
+            for (int j = 0; j < C; j++) d[j] -= f * A[(size_t)j * R + r];
+            for (int k = 0; k < R; k++) pi[k] += f * Binv[(size_t)r * R + k];
+            z += f * rhs[r];
+        }
+        basis[r] = e;
+    }
+    // Primal simplex on the reduced costs d (Bland's rule; artificial
+    // columns never enter).  0 optimal, 1 unbounded, 3 iteration limit.
+    int run(double eps)
+    {
+        const int limit = 64 * (R + C) + 256;
+        for (int it = 0; it < limit; it++) {
+            int e = -1;
+            for (int j = 0; j < C; j++)
+                if (d[j] < -eps) {
+                    e = j;
+                    break;
+                }
+            if (e < 0) return 0;
+            int r = -1;
+            double best = 0.0;
+            for (int i = 0; i < R; i++) {
+                const double a = A[(size_t)e * R + i];
+                if (a <= 1e-11) continue;
+                const double ratio = rhs[i] / a;
+                const int bi = basis[i] >= 0 ? basis[i] : C + (-1 - basis[i]);
+                const int br = r < 0 ? 0 : (basis[r] >= 0 ? basis[r] : C + (-1 - basis[r]));
+                if (r < 0 || ratio < best - 1e-13 || (ratio <= best + 1e-13 && bi < br)) {
+                    r = i;
+                    best = ratio;
+                }
+            }
+            if (r < 0) return 1;
+            pivot(r, e);
+        }
+        return 3;
+    }
+    // Appends an original column m (R entries) of cost c.
+    void add_column(const double *m, double c)
+    {
+        A.resize((size_t)(C + 1) * R);
+        double *a = &A[(size_t)C * R];
+        double red = c;
+        for (int i = 0; i < R; i++) {
+            double s = 0.0;
+            for (int k = 0; k < R; k++) s += Binv[(size_t)i * R + k] * m[k];
+            a[i] = s;
+            red -= pi[i] * m[i];
+        }
+        d.push_back(red);
+        cost.push_back(c);
+        cmax = std::max(cmax, std::fabs(c));
+        C++;
+    }
+};
+
+// The dual problem's columns of pair (i, a, b): one per other point c of
+// support i, (a - c, 1) of cost w(c) - w(a), and the pair's equality as two
+// columns +-(a - b, 0) of costs +-(w(b) - w(a)).
+void pair_columns(const Lifted &L, const Pair &P, std::vector<double> &cols, std::vector<double> &costs)
+{
+    const int n = L.n, i = P.eq, a = P.a, b = P.b;
+    for (int c = L.off[i]; c < L.off[i] + L.m[i]; c++) {
+        if (c == a || c == b) continue;
+        for (int j = 0; j < n; j++) cols.push_back((double)(L.at(a, j) - L.at(c, j)));
+        cols.push_back(1.0);
+        costs.push_back((double)(L.w[c] - L.w[a]));
+    }
+    for (int s = 1; s >= -1; s -= 2) {
+        for (int j = 0; j < n; j++) cols.push_back((double)(s * (L.at(a, j) - L.at(b, j))));
+        cols.push_back(0.0);
+        costs.push_back((double)(s * (L.w[b] - L.w[a])));
+    }
+}
+
+// The problem of one pair, from scratch: the y_0 column and the pair's,
+// two phases (the artificial basis, then the costs).
+void lp_start(const Lifted &L, const Pair &P, DualLP &lp)
+{
+    const int n = L.n, R = n + 1;
+    std::vector<double> cols, costs;
+    for (int j = 0; j < n; j++) cols.push_back(0.0);  // y_0 (tau <= 1)
+    cols.push_back(1.0);
+    costs.push_back(1.0);
+    pair_columns(L, P, cols, costs);
+    lp.R = R;
+    lp.C = (int)costs.size();
+    lp.A = cols;  // the artificial basis is the identity: B^-1 M = M
+    lp.cost = costs;
+    lp.cmax = 0.0;
+    for (double c : costs) lp.cmax = std::max(lp.cmax, std::fabs(c));
+    lp.Binv.assign((size_t)R * R, 0.0);
+    for (int k = 0; k < R; k++) lp.Binv[(size_t)k * R + k] = 1.0;
+    lp.rhs.assign(R, 0.0);
+    lp.rhs[n] = 1.0;
+    lp.basis.resize(R);
+    for (int k = 0; k < R; k++) lp.basis[k] = -1 - k;
+    // phase 1: minimise the sum of the artificials (multipliers all 1)
+    lp.pi.assign(R, 1.0);
+    lp.d.resize(lp.C);
+    for (int j = 0; j < lp.C; j++) {
+        double s = 0.0;
+        for (int i = 0; i < R; i++) s += lp.A[(size_t)j * R + i];
+        lp.d[j] = -s;
+    }
+    lp.z = 1.0;
+    int rc = lp.run(1e-10);
+    if (rc == 3 || lp.z > 1e-9) {
+        lp.status = rc == 3 ? 3 : 2;
+        return;
+    }
+    for (int i = 0; i < R; i++) {  // artificials out of the basis where a real column can replace them
+        if (lp.basis[i] >= 0) continue;
+        for (int j = 0; j < lp.C; j++)
+            if (std::fabs(lp.A[(size_t)j * R + i]) > 1e-9) {
+                lp.pivot(i, j);
+                break;
+            }
+    }
+    // phase 2: the real costs
+    lp.pi.assign(R, 0.0);
+    lp.z = 0.0;
+    for (int i = 0; i < R; i++) {
+        const double cb = lp.basis[i] >= 0 ? lp.cost[lp.basis[i]] : 0.0;
+        if (cb == 0.0) continue;
+        for (int k = 0; k < R; k++) lp.pi[k] += cb * lp.Binv[(size_t)i * R + k];
+        lp.z += cb * lp.rhs[i];
+    }
+    for (int j = 0; j < lp.C; j++) {
+        double s = lp.cost[j];
+        for (int i = 0; i < R; i++) {
+            const double cb = lp.basis[i] >= 0 ? lp.cost[lp.basis[i]] : 0.0;
+            s -= cb * lp.A[(size_t)j * R + i];
+        }
+        lp.d[j] = s;
+    }
+    rc = lp.run(1e-10 * (1.0 + lp.cmax));
+    lp.status = rc;
+}
+
+// The parent's problem with the columns of one more pair, continued from the
+// parent's basis.
+void lp_extend(const Lifted &L, const DualLP &parent, const Pair &P, DualLP &lp)
+{
+    lp = parent;
+    std::vector<double> cols, costs;
+    pair_columns(L, P, cols, costs);
+    const int R = lp.R;
+    for (size_t c = 0; c < costs.size(); c++) lp.add_column(&cols[c * R], costs[c]);
+    // an artificial left in the basis (at 0) holds a row no parent column
+    // touched; a new column that touches it replaces it (a degenerate pivot:
+    // the basis stays feasible), before the simplex may move that row
+    for (int i = 0; i < R; i++) {
+        if (lp.basis[i] >= 0) continue;
+        for (int j = 0; j < lp.C; j++)
+            if (std::fabs(lp.A[(size_t)j * R + i]) > 1e-9) {
+                lp.pivot(i, j);
+                break;
+            }
+    }
+    lp.status = lp.run(1e-10 * (1.0 + lp.cmax));
+}
+
+// Feasibility from a solved problem (as feasible()).
+bool lp_feasible(const Lifted &L, const DualLP &lp)
+{
+    if (lp.status == 1 || lp.status == 2) return false;
+    if (lp.status != 0) return true;
+    return lp.z > -1e-7 * (1.0 + L.wmax);
+}
+
 // ------------------------------------------------------------------ exact arithmetic
 
 bool mul_ok(i128 a, i128 b, i128 *out) { return !__builtin_mul_overflow(a, b, out); }
@@ -384,32 +590,82 @@ int host_threads()
     return (int)h;
 }
 
-// Depth-first search below a fixed prefix of pairs; the cells of one task.
+// The edges related to every chosen edge, and the equation the search takes
+// next: of the equations not chosen yet, the one with the fewest such edges
+// (the first on ties), so that dead ends show early; -1 when some equation
+// has none left (no cell below the chosen edges).
+struct Picker {
+    int n = 0, words = 0;
+    const std::vector<int> *eoff = nullptr, *eq_of = nullptr;
+    const std::vector<uint64_t> *rel = nullptr;
+    int pick(const int *ids, int d, uint64_t *cand) const
+    {
+        const int NE = (*eoff)[n];
+        for (int w = 0; w < words; w++) cand[w] = ~0ull;
+        if (NE % 64) cand[words - 1] = (1ull << (NE % 64)) - 1ull;
+        unsigned used = 0;
+        for (int k = 0; k < d; k++) {
+            const uint64_t *row = &(*rel)[(size_t)ids[k] * words];
+            for (int w = 0; w < words; w++) cand[w] &= row[w];
+            used |= 1u << (*eq_of)[ids[k]];
+        }
+        int best = -1, best_count = 0;
+        for (int i = 0; i < n; i++) {
+            if (used & (1u << i)) continue;
+            int count = 0;
+            for (int ge = (*eoff)[i]; ge < (*eoff)[i + 1]; ge++) count += (int)((cand[ge / 64] >> (ge % 64)) & 1ull);
+            if (count == 0) return -1;
+            if (best < 0 || count < best_count) {
+                best = i;
+                best_count = count;
+            }
+        }
+        return best;
+    }
+};
+
+// Depth-first search below a fixed prefix of edges; the cells of one task.
 struct Walker {
     const Lifted &L;
     const std::vector<std::vector<Pair>> &edges;
-    const std::vector<int> &order, &eoff;
-    const std::vector<uint64_t> &rel;
+    const std::vector<int> &eoff, &eq_of;
+    const Picker &picker;
     int words;
     std::vector<Pair> chosen, sorted;
     std::vector<int> chosen_id;
+    std::vector<uint64_t> cand;   // one candidate mask per depth
+    std::vector<DualLP> lps;      // the problem of chosen[0..d] per depth d
     std::vector<int32_t> cells;   // 2n term indices per cell
     std::vector<int64_t> volumes;
     int status = PHC_OK;          // error messages are set on the calling thread
     const char *message = "";
 
-    Walker(const Lifted &l, const std::vector<std::vector<Pair>> &e, const std::vector<int> &o,
-           const std::vector<int> &eo, const std::vector<uint64_t> &r, int w)
-        : L(l), edges(e), order(o), eoff(eo), rel(r), words(w), chosen(l.n), sorted(l.n), chosen_id(l.n)
+    Walker(const Lifted &l, const std::vector<std::vector<Pair>> &e, const std::vector<int> &eo,
+           const std::vector<int> &eq, const Picker &p, int w)
+        : L(l), edges(e), eoff(eo), eq_of(eq), picker(p), words(w), chosen(l.n), sorted(l.n), chosen_id(l.n),
+          cand((size_t)l.n * w), lps(l.n)
     {
     }
-    bool related(int a, int b) const { return (rel[(size_t)a * words + b / 64] >> (b % 64)) & 1ull; }
+    // solves the problem of chosen[0..d] (from depth d - 1's when that one
+    // was solved to the end); true when it is feasible
+    bool solve(int d)
+    {
+        if (d == 0 || lps[d - 1].status != 0) {
+            lp_start(L, chosen[0], lps[0]);
+            for (int k = 1; k <= d; k++) lp_extend(L, lps[k - 1], chosen[k], lps[k]);
+        } else {
+            lp_extend(L, lps[d - 1], chosen[d], lps[d]);
+        }
+        return lp_feasible(L, lps[d]);
+    }
+    const Pair &edge(int ge) const { return edges[eq_of[ge]][ge - eoff[eq_of[ge]]]; }
     // chosen[0..d] is set and pairwise related
     void visit(int d)
     {
         const int n = L.n;
         if (d + 1 < n) {
-            if (d >= 1 && !feasible(L, chosen.data(), d + 1)) return;
+            const bool ok = solve(d);
+            if (d >= 1 && !ok) return;
             walk(d + 1);
             return;
         }
@@ -442,13 +698,12 @@ struct Walker {
     }
     void walk(int d)
     {
-        const int i = order[d];
-        for (int e = 0; e < (int)edges[i].size() && !status; e++) {
-            const int ge = eoff[i] + e;
-            bool ok = true;
-            for (int k = 0; k < d && ok; k++) ok = related(chosen_id[k], ge);
-            if (!ok) continue;
-            chosen[d] = edges[i][e];
+        uint64_t *c = &cand[(size_t)d * words];
+        const int i = picker.pick(chosen_id.data(), d, c);
+        if (i < 0) return;
+        for (int ge = eoff[i]; ge < eoff[i + 1] && !status; ge++) {
+            if (!((c[ge / 64] >> (ge % 64)) & 1ull)) continue;
+            chosen[d] = edge(ge);
             chosen_id[d] = ge;
             visit(d);
         }
@@ -457,8 +712,8 @@ struct Walker {
 
 }  // namespace
 
-// The search is split into tasks, one per related choice of edges of the
-// first equations of the order, run on the host threads; every task keeps its
+// The search is split into tasks, one per choice of its first edges, run on
+// the host threads; every task keeps its
 // cells, and the tasks' cells are emitted in task order from the calling
 // thread as the tasks finish -- the order, and so the cells' order, of the
 // sequential search.
@@ -481,9 +736,6 @@ int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const 
         if (lower[k]) edges[all[k].eq].push_back(all[k]);
     for (int i = 0; i < n; i++)
         if (edges[i].empty()) return PHC_OK;  // a support of one point: no cell, mixed volume 0
-    std::vector<int> order(n);
-    for (int i = 0; i < n; i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return edges[x].size() < edges[y].size(); });
     // (2) relation table: edge e of one equation and f of a later one, feasible
     // together (rows computed in parallel, then mirrored)
     std::vector<int> eoff(n + 1, 0);
@@ -506,27 +758,34 @@ int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const 
     for (int ge = 0; ge < NE; ge++)
         for (int gf = eoff[eq_of[ge] + 1]; gf < NE; gf++)
             if ((rel[(size_t)ge * words + gf / 64] >> (gf % 64)) & 1ull) rel[(size_t)gf * words + ge / 64] |= 1ull << (ge % 64);
-    // (3) tasks: the related prefixes of the first P equations of the order,
-    // P the smallest depth that gives 32 tasks per thread (or n), in the
-    // order of the sequential search
-    std::vector<std::vector<int>> prefixes;
-    for (int e0 = eoff[order[0]]; e0 < eoff[order[0] + 1]; e0++) prefixes.push_back({e0});
-    int P = 1;
+    // (3) tasks: the choices of the first P edges the search makes (its
+    // ordering by fewest related edges, without the linear programs), P the
+    // smallest depth that gives 32 tasks per thread (or n), in the order of
+    // the sequential search
+    Picker picker;
+    picker.n = n;
+    picker.words = words;
+    picker.eoff = &eoff;
+    picker.eq_of = &eq_of;
+    picker.rel = &rel;
+    std::vector<std::vector<int>> prefixes(1);
+    int P = 0;
+    std::vector<uint64_t> cmask(words);
     while (P < n && prefixes.size() < (size_t)32 * threads) {
         std::vector<std::vector<int>> longer;
-        const int i = order[P];
-        for (const auto &pre : prefixes)
-            for (int ge = eoff[i]; ge < eoff[i + 1]; ge++) {
-                bool ok = true;
-                for (int x : pre) ok = ok && ((rel[(size_t)x * words + ge / 64] >> (ge % 64)) & 1ull);
-                if (!ok) continue;
-                longer.push_back(pre);
-                longer.back().push_back(ge);
-            }
+        for (const auto &pre : prefixes) {
+            const int i = picker.pick(pre.data(), P, cmask.data());
+            if (i < 0) continue;
+            for (int ge = eoff[i]; ge < eoff[i + 1]; ge++)
+                if ((cmask[ge / 64] >> (ge % 64)) & 1ull) {
+                    longer.push_back(pre);
+                    longer.back().push_back(ge);
+                }
+        }
         prefixes.swap(longer);
         P++;
     }
-    const int64_t NT = (int64_t)prefixes.size();
+    const int64_t NT = P == 0 ? 0 : (int64_t)prefixes.size();
     std::vector<Walker *> done(NT, nullptr);
     std::mutex mu;
     std::condition_variable cv;
@@ -534,16 +793,15 @@ int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const 
     std::atomic<bool> stop(false);
     auto worker = [&]() {
         for (int64_t k = next++; k < NT && !stop; k = next++) {
-            Walker *w = new Walker(L, edges, order, eoff, rel, words);
+            Walker *w = new Walker(L, edges, eoff, eq_of, picker, words);
             const auto &pre = prefixes[k];
             for (int d = 0; d < P; d++) {
-                const int i = order[d];
-                w->chosen[d] = edges[i][pre[d] - eoff[i]];
+                w->chosen[d] = w->edge(pre[d]);
                 w->chosen_id[d] = pre[d];
             }
             // the tests the sequential search makes on the way to depth P - 1
             bool ok = true;
-            for (int d = 1; d + 1 < P && ok; d++) ok = feasible(L, w->chosen.data(), d + 1);
+            for (int d = 0; d + 1 < P && ok; d++) ok = w->solve(d) || d == 0;
             if (ok) w->visit(P - 1);
             std::lock_guard<std::mutex> lock(mu);
             done[k] = w;
