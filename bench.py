@@ -776,7 +776,41 @@ def run_configs(args):
                 "pipeline_s": t_pipe, "pipeline_equals_one_launch": same,
                 "total_degree": td,
             })
-        return {"config": "polyhedral", "systems": res}
+        # the paper's solve of a top dimensional system (Sections 2.2, 2.3):
+        # polyhedral paths to a random-coefficient system with the embedded
+        # system's supports, then the coefficient-parameter homotopy to the
+        # embedded system; against the total-degree homotopy of the same
+        w = configs.cyclic8_d1()
+        e = w.embed
+        E_lists = P.phc_embed(w.systems[0], e["top_dim"], e["gammas"], e["hyper"])
+        from workloads import PolySystem
+        E = PolySystem(E_lists.n_eq, E_lists.n_var, E_lists.terms_per_eq, E_lists.exps, E_lists.coefs, name="c8E1")
+        g = with_random_coefficients(E, rng_for(630))
+        lift = random_lifting(rng_for(631), g.n_terms)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sp = P.solve_polyhedral(g, lift, 1 << 16)
+        hp = P.phc_make_parameter_homotopy(E, g.coefs, unit_gamma(rng_for(632)))
+        rp = P.track_from(hp, sp.x)
+        torch.cuda.synchronize()
+        t_poly = time.perf_counter() - t0
+        ht = P.phc_make_homotopy(E, w.gammas[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rt = P.track(ht)
+        torch.cuda.synchronize()
+        t_td = time.perf_counter() - t0
+
+        def split(r):
+            x, c = r.x.cpu().numpy().T, r.cls.cpu().numpy()
+            fin = (c == 0) | (c == 1)
+            z = np.abs(x[:, -1])
+            return {"classes": np.bincount(c, minlength=4).tolist(), "regular_z0": int(((c == 0) & (z < 1e-8)).sum()),
+                    "regular_z_nonzero": int(((c == 0) & (z >= 1e-8)).sum()), "finite": int(fin.sum())}
+        emb = {"system": "cyclic 8 embedded for D = 1 (9 unknowns)", "mixed_volume": int(sp.x.shape[1]),
+               "polyhedral_then_parameter_s": t_poly, "polyhedral_then_parameter": split(rp),
+               "total_degree_paths": int(rt.cls.shape[0]), "total_degree_s": t_td, "total_degree": split(rt)}
+        return {"config": "polyhedral", "systems": res, "embedded": emb}
 
     def config5():
         sv, reqs = serving_session(args.requests, not args.no_big, args.slots, args.batch_paths)
