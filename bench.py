@@ -719,7 +719,23 @@ def run_configs(args):
         st = P.stats_numpy(r.stats)
         cls = {k: np.bincount(out[k][0].cls.cpu().numpy() if k != "f" else out[k].cls.cpu().numpy(),
                               minlength=4).tolist() for k in ("q", "d", "f")}
-        return {"config": "precision ladder", "workload": "cyclic 7 random copy 1, 5040 total-degree paths",
+        # the oracle beside it: the same copy's first 32 paths in each precision
+        oh = oracle.total_degree(w.systems[1], w.gammas[1])
+        ncores = oracle.host_threads()
+        t0 = time.perf_counter()
+        oracle.track(oh, first=0, n_paths=32, threads=ncores)
+        t_d = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.track_dd(oh, first=0, n_paths=32, threads=ncores)
+        t_dd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.track_qd(oh, first=0, n_paths=32, threads=ncores)
+        t_qd = time.perf_counter() - t0
+        orc = {"sample": "paths 0..31 of the same copy", "cores": ncores, "double_paths_per_s": 32 / t_d,
+               "double_double_paths_per_s": 32 / t_dd, "quad_double_paths_per_s": 32 / t_qd,
+               "ratios": {"dd_over_d": t_dd / t_d, "qd_over_d": t_qd / t_d}}
+        return {"config": "precision ladder", "oracle": orc,
+                "workload": "cyclic 7 random copy 1, 5040 total-degree paths",
                 "double": {"ms": ms64, "paths_per_s": 5040 / (ms64 / 1e3), "classes": cls["f"]},
                 "double_double": {"ms": ms_dd, "paths_per_s": 5040 / (ms_dd / 1e3), "classes": cls["d"]},
                 "quad_double": {"ms": ms_qd, "paths_per_s": 5040 / (ms_qd / 1e3), "classes": cls["q"],
@@ -810,7 +826,24 @@ def run_configs(args):
         emb = {"system": "cyclic 8 embedded for D = 1 (9 unknowns)", "mixed_volume": int(sp.x.shape[1]),
                "polyhedral_then_parameter_s": t_poly, "polyhedral_then_parameter": split(rp),
                "total_degree_paths": int(rt.cls.shape[0]), "total_degree_s": t_td, "total_degree": split(rt)}
-        return {"config": "polyhedral", "systems": res, "embedded": emb}
+        # the oracle beside it, on a bounded case it finishes in seconds: its own
+        # cells (exact search in Python) and polyhedral paths of random cyclic 6
+        from oracle import mixed as OM
+        g6 = with_random_coefficients(cyclic(6), rng_for(606))
+        lift6 = random_lifting(rng_for(616), g6.n_terms)
+        t0 = time.perf_counter()
+        oc = OM.mixed_cells(g6, lift6)
+        t_oc = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, _, ocls, _, _ = OM.track_polyhedral(g6, lift6, oc, threads=oracle.host_threads())
+        t_ot = time.perf_counter() - t0
+        cells6, _, mv6 = P.phc_mixed_cells(g6, lift6)
+        h6 = P.phc_make_polyhedral_homotopy(g6, lift6, cells6)
+        ms6 = _timed(lambda: P.track_polyhedral(h6), 5, 2)
+        orc = {"system": "cyclic 6, random coefficients (mixed volume 156)", "cores": oracle.host_threads(),
+               "oracle_cells_s": t_oc, "oracle_track_s": t_ot, "oracle_paths_per_s": mv6 / t_ot,
+               "oracle_regular": int((ocls == 0).sum()), "gpu_track_ms": ms6, "gpu_paths_per_s": mv6 / (ms6 / 1e3)}
+        return {"config": "polyhedral", "systems": res, "embedded": emb, "oracle": orc}
 
     def config5():
         sv, reqs = serving_session(args.requests, not args.no_big, args.slots, args.batch_paths)
