@@ -211,3 +211,59 @@ def test_polyhedral_handle_edges():
                     P.phc_make_polyhedral_homotopy(g, lift, bad)
                 return
     pytest.fail("every pair of equation 0 completes the cell")
+
+
+@pytest.mark.parametrize("n", [7, 8])
+def test_polyhedral_full_size_against_the_stored_oracle(n):
+    """The random cyclic 7 and 8 systems of the polyhedral benchmark, whole:
+    the library's cells are the oracle's (stored by
+    tests/golden/make_polyhedral_expected.py, which calls only the oracle),
+    and the pipelined solver's endpoints are the oracle's polyhedral
+    endpoints one to one within 1e-10, all regular."""
+    from scipy.spatial import cKDTree
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "polyhedral_expected.npz"))
+    g = with_random_coefficients(cyclic(n), rng_for(600 + n))
+    lift = random_lifting(rng_for(610 + n), g.n_terms)
+    cells, vols, mv = P.phc_mixed_cells(g, lift)
+    assert mv == int(gold[f"mixed_volume_{n}"])
+    mine = sorted(tuple(tuple(int(t) for t in pr) for pr in c) for c in cells)
+    theirs = sorted(tuple(tuple(int(t) for t in pr) for pr in c) for c in gold[f"pairs_{n}"])
+    assert mine == theirs
+    r = P.solve_polyhedral(g, lift, mv)
+    x, cls = r.x.cpu().numpy().T, r.cls.cpu().numpy()
+    assert np.array_equal(np.bincount(cls, minlength=4), gold[f"counts_{n}"])
+    xo = gold[f"x_{n}"]
+    tree = cKDTree(np.concatenate([xo.real, xo.imag], axis=1))
+    d, idx = tree.query(np.concatenate([x.real, x.imag], axis=1), k=1)
+    rel = d / (1.0 + np.abs(xo[idx]).max(axis=1))
+    assert rel.max() <= 1e-10, rel.max()
+    assert len(np.unique(idx)) == mv  # one to one
+
+
+def test_polyhedral_one_and_two_unknowns():
+    """One unknown: the cells are the lower hull's edges of the lifted
+    exponents and the paths end at the polynomial's roots (companion matrix
+    eigenvalues); two unknowns, sparse: the total-degree homotopy's roots."""
+    from workloads import univariate
+    rng = rng_for(550)
+    c = rng.normal(size=7) + 1j * rng.normal(size=7)
+    s = univariate(c)
+    lift = random_lifting(rng_for(551), s.n_terms)
+    r = P.solve_polyhedral(s, lift, 6)
+    x, cls = r.x.cpu().numpy().T, r.cls.cpu().numpy()
+    assert x.shape[0] == 6 and np.all(cls == P.PHC_REGULAR)
+    _, _, d = match_sets(x, np.roots(c[::-1])[:, None])
+    assert d.max() <= 1e-12
+    from workloads import PolySystem
+    exps = np.array([[0, 0], [2, 1], [1, 3], [0, 2], [0, 0], [3, 0], [1, 1], [0, 1]], dtype=np.uint8)
+    s2 = PolySystem(2, 2, np.array([4, 4]), exps, rng.normal(size=8) + 1j * rng.normal(size=8))
+    lift2 = random_lifting(rng_for(552), s2.n_terms)
+    cells, _, mv = P.phc_mixed_cells(s2, lift2)
+    assert mv == M.mixed_volume(M.mixed_cells(s2, lift2))
+    r2 = P.solve_polyhedral(s2, lift2, mv)
+    x2, c2 = r2.x.cpu().numpy().T, r2.cls.cpu().numpy()
+    xt, ct, _ = oracle.track(oracle.total_degree(s2, unit_gamma(rng_for(553))))
+    reg = xt[ct == 0]
+    assert np.all(c2 == P.PHC_REGULAR) and reg.shape[0] == mv
+    _, _, d2 = match_sets(x2, reg)
+    assert d2.max() <= 1e-9
