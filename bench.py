@@ -593,6 +593,10 @@ def run_configs(args):
             o = P.phc_default_opts(tail_drain=drain)
             msd = _timed(lambda: P.track(h, opts=o), 50)
             d[f"tail_drain_{drain}"] = {"ms": msd, "paths_per_s": 16 / (msd / 1e3)}
+        for g in (8, 16):
+            o = P.phc_default_opts(tail_threads=g)
+            msg = _timed(lambda: P.track(h, opts=o), 50)
+            d[f"tail_threads_{g}"] = {"ms": msg, "paths_per_s": 16 / (msg / 1e3)}
         d["oracle"] = oracle_part(w.systems * 200, w.gammas * 200, 16, "paths")
         return d
 
