@@ -746,6 +746,38 @@ def run_configs(args):
                                 "units": int(st["n_solve"].sum())},
                 "ratios": {"dd_over_d": ms_dd / ms64, "qd_over_d": ms_qd / ms64, "qd_over_dd": ms_qd / ms_dd}}
 
+    def config13():
+        """The pipelined polyhedral solve against the number of host threads
+        that make the cells (Section 2.2, Figure 2; the paper's tables of the
+        pipelined polyhedral homotopies time 2 to 64 tasks): random cyclic 10
+        (35,940 paths), the cells made by p threads while the GPU tracks."""
+        from workloads import cyclic, random_lifting, rng_for, with_random_coefficients
+        g = with_random_coefficients(cyclic(10), rng_for(610))
+        lift = random_lifting(rng_for(620), g.n_terms)
+        rows, base = [], None
+        old = os.environ.get("PHC_HOST_THREADS")
+        try:
+            for p in (1, 2, 4, 8, 16):
+                os.environ["PHC_HOST_THREADS"] = str(p)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s = P.solve_polyhedral(g, lift, 40000)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                P.phc_mixed_cells(g, lift)
+                dc = time.perf_counter() - t0
+                base = base or dt
+                rows.append({"threads": p, "pipeline_s": dt, "speedup": base / dt, "cells_alone_s": dc,
+                             "paths": int(s.x.shape[1])})
+        finally:
+            if old is None:
+                os.environ.pop("PHC_HOST_THREADS", None)
+            else:
+                os.environ["PHC_HOST_THREADS"] = old
+        return {"config": "pipelined polyhedral vs host threads", "system": "cyclic 10, random coefficients",
+                "rows": rows}
+
     def config11():
         """Polyhedral homotopies (Section 2.2) on random-coefficient cyclic
         n systems (n = 7 .. 10): the mixed cells on the host, the polyhedral
@@ -862,7 +894,7 @@ def run_configs(args):
 
     want = [int(c) for c in args.configs.split(",")] if args.configs else [1, 2, 3, 4, 5]
     table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9, 10: config10, 11: config11,
-             12: config12}
+             12: config12, 13: config13}
     for c in want:
         print(json.dumps(table[c]()), flush=True)
     return 0
@@ -930,7 +962,8 @@ def main(argv=None):
     ap.add_argument("--batch-paths", type=int, default=60_000, help="serving: most paths per batch of small requests")
     ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default 1-5; 9 = the "
                     "cyclic 9 D=2 request of the serving workload alone; 10 = double double tracking; "
-                    "11 = polyhedral homotopies; 12 = double, double double and quad double tracking)")
+                    "11 = polyhedral homotopies; 12 = double, double double and quad double tracking; "
+                    "13 = the pipelined polyhedral solve against the host threads)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",

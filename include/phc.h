@@ -511,6 +511,9 @@ int phc_track_paths_noalloc(phc_homotopy *h, int64_t first_path, int64_t n_paths
  * exps[b_i] - exps[a_i].  The mixed volume (the sum of the volumes) counts
  * the isolated roots in (C*)^n of a system with these supports and
  * coefficients in general position (Bernstein).
+ * The search runs on the host's threads (PHC_HOST_THREADS in the
+ * environment, 1..64, sets their number; the cells and their order do not
+ * depend on it).
  * Outputs: *n_cells_out (every cell) and *mixed_volume_out (may be NULL);
  * the first min(n_cells, max_cells) cells to cells_out [max_cells][n][2]
  * (a_i, b_i per equation) and their volumes to volumes_out [max_cells] (may

@@ -40,6 +40,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -582,9 +583,13 @@ void parallel_for(int64_t count, int threads, const std::function<void(int64_t)>
     for (auto &th : pool) th.join();
 }
 
+// The host threads of the search: PHC_HOST_THREADS from the environment
+// when set (1..64), else the hardware's.
 int host_threads()
 {
-    unsigned h = std::thread::hardware_concurrency();
+    long h = 0;
+    if (const char *e = std::getenv("PHC_HOST_THREADS")) h = std::strtol(e, nullptr, 10);
+    if (h < 1) h = (long)std::thread::hardware_concurrency();
     if (h < 1) h = 1;
     if (h > 64) h = 64;
     return (int)h;
