@@ -42,6 +42,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -570,17 +571,41 @@ bool gcd_ext(int64_t a, int64_t b, int64_t *g, int64_t *s, int64_t *t)
 
 namespace {
 
-// Runs fn(k) for k = 0 .. count-1 on the host threads (each k once).
-void parallel_for(int64_t count, int threads, const std::function<void(int64_t)> &fn)
+// Joins the threads of a pool on every way out of a scope (an exception
+// included), after telling them to stop.
+struct PoolGuard {
+    std::vector<std::thread> &pool;
+    std::atomic<bool> *stop;
+    ~PoolGuard()
+    {
+        if (stop) *stop = true;
+        for (auto &th : pool)
+            if (th.joinable()) th.join();
+    }
+};
+
+// Runs fn(k) for k = 0 .. count-1 on the host threads (each k once); false
+// when an fn threw (out of host memory).
+bool parallel_for(int64_t count, int threads, const std::function<void(int64_t)> &fn)
 {
     std::atomic<int64_t> next(0);
+    std::atomic<bool> failed(false);
     auto body = [&]() {
-        for (int64_t k = next++; k < count; k = next++) fn(k);
+        for (int64_t k = next++; k < count && !failed; k = next++) {
+            try {
+                fn(k);
+            } catch (...) {
+                failed = true;
+            }
+        }
     };
     std::vector<std::thread> pool;
-    for (int t = 1; t < threads; t++) pool.emplace_back(body);
-    body();
-    for (auto &th : pool) th.join();
+    {
+        PoolGuard guard{pool, nullptr};
+        for (int t = 1; t < threads; t++) pool.emplace_back(body);
+        body();
+    }
+    return !failed;
 }
 
 // The host threads of the search: PHC_HOST_THREADS from the environment
@@ -735,7 +760,8 @@ int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const 
         for (int a = L.off[i]; a < L.off[i] + L.m[i]; a++)
             for (int b = a + 1; b < L.off[i] + L.m[i]; b++) all.push_back(Pair{i, a, b});
     std::vector<char> lower(all.size(), 0);
-    parallel_for((int64_t)all.size(), threads, [&](int64_t k) { lower[k] = feasible(L, &all[k], 1); });
+    if (!parallel_for((int64_t)all.size(), threads, [&](int64_t k) { lower[k] = feasible(L, &all[k], 1); }))
+        return set_error(PHC_ENOMEM, "mixed cells: host allocation failed");
     std::vector<std::vector<Pair>> edges(n);
     for (size_t k = 0; k < all.size(); k++)
         if (lower[k]) edges[all[k].eq].push_back(all[k]);
@@ -751,7 +777,7 @@ int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const 
     std::vector<int> eq_of(NE);
     for (int i = 0; i < n; i++)
         for (int e = eoff[i]; e < eoff[i + 1]; e++) eq_of[e] = i;
-    parallel_for(NE, threads, [&](int64_t ge) {
+    const bool rel_ok = parallel_for(NE, threads, [&](int64_t ge) {
         const int i = eq_of[ge];
         const Pair &pe = edges[i][ge - eoff[i]];
         for (int gf = eoff[i + 1]; gf < NE; gf++) {
@@ -760,6 +786,7 @@ int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const 
             if (feasible(L, two, 2)) rel[(size_t)ge * words + gf / 64] |= 1ull << (gf % 64);
         }
     });
+    if (!rel_ok) return set_error(PHC_ENOMEM, "mixed cells: host allocation failed");
     for (int ge = 0; ge < NE; ge++)
         for (int gf = eoff[eq_of[ge] + 1]; gf < NE; gf++)
             if ((rel[(size_t)ge * words + gf / 64] >> (gf % 64)) & 1ull) rel[(size_t)gf * words + ge / 64] |= 1ull << (ge % 64);
@@ -791,44 +818,56 @@ int enumerate_mixed_cells(int n, const int32_t *tpe, const uint8_t *exps, const 
         P++;
     }
     const int64_t NT = P == 0 ? 0 : (int64_t)prefixes.size();
-    std::vector<Walker *> done(NT, nullptr);
+    std::vector<std::unique_ptr<Walker>> done(NT);
+    std::vector<char> finished(NT, 0);  // 1 done, 2 out of host memory
     std::mutex mu;
     std::condition_variable cv;
     std::atomic<int64_t> next(0);
     std::atomic<bool> stop(false);
     auto worker = [&]() {
         for (int64_t k = next++; k < NT && !stop; k = next++) {
-            Walker *w = new Walker(L, edges, eoff, eq_of, picker, words);
-            const auto &pre = prefixes[k];
-            for (int d = 0; d < P; d++) {
-                w->chosen[d] = w->edge(pre[d]);
-                w->chosen_id[d] = pre[d];
+            std::unique_ptr<Walker> w;
+            char how = 1;
+            try {
+                w.reset(new Walker(L, edges, eoff, eq_of, picker, words));
+                const auto &pre = prefixes[k];
+                for (int d = 0; d < P; d++) {
+                    w->chosen[d] = w->edge(pre[d]);
+                    w->chosen_id[d] = pre[d];
+                }
+                // the tests the sequential search makes on the way to depth P - 1
+                bool ok = true;
+                for (int d = 0; d + 1 < P && ok; d++) ok = w->solve(d) || d == 0;
+                if (ok) w->visit(P - 1);
+            } catch (...) {
+                how = 2;
             }
-            // the tests the sequential search makes on the way to depth P - 1
-            bool ok = true;
-            for (int d = 0; d + 1 < P && ok; d++) ok = w->solve(d) || d == 0;
-            if (ok) w->visit(P - 1);
             std::lock_guard<std::mutex> lock(mu);
-            done[k] = w;
+            done[k] = std::move(w);
+            finished[k] = how;
             cv.notify_all();
         }
     };
     std::vector<std::thread> pool;
-    for (int t = 0; t < threads; t++) pool.emplace_back(worker);
     int status = PHC_OK;
-    for (int64_t k = 0; k < NT && !status; k++) {
-        Walker *w = nullptr;
-        {
-            std::unique_lock<std::mutex> lock(mu);
-            cv.wait(lock, [&] { return done[k] != nullptr; });
-            w = done[k];
+    {
+        PoolGuard guard{pool, &stop};
+        for (int t = 0; t < threads; t++) pool.emplace_back(worker);
+        for (int64_t k = 0; k < NT && !status; k++) {
+            {
+                std::unique_lock<std::mutex> lock(mu);
+                cv.wait(lock, [&] { return finished[k] != 0; });
+            }
+            if (finished[k] == 2) {
+                status = set_error(PHC_ENOMEM, "mixed cells: host allocation failed");
+                break;
+            }
+            const Walker &w = *done[k];
+            if (w.status) status = set_error(w.status, w.message);
+            for (size_t c = 0; c < w.volumes.size() && !status; c++) status = emit(&w.cells[c * 2 * n], w.volumes[c]);
+            done[k].reset();
         }
-        if (w->status) status = set_error(w->status, w->message);
-        for (size_t c = 0; c < w->volumes.size() && !status; c++) status = emit(&w->cells[c * 2 * n], w->volumes[c]);
     }
-    stop = true;
-    for (auto &th : pool) th.join();
-    for (Walker *w : done) delete w;
     return status;
 }
 
@@ -909,9 +948,9 @@ int cell_tracking_data(int n, const int32_t *tpe, const uint8_t *exps, const int
 
 }  // namespace phc
 
-extern "C" int phc_mixed_cells(int n, const int32_t *terms_per_eq, const uint8_t *exps, const int32_t *lift,
-                               int64_t max_cells, int32_t *cells_out, int64_t *volumes_out, int64_t *n_cells_out,
-                               int64_t *mixed_volume_out)
+static int mixed_cells_impl(int n, const int32_t *terms_per_eq, const uint8_t *exps, const int32_t *lift,
+                            int64_t max_cells, int32_t *cells_out, int64_t *volumes_out, int64_t *n_cells_out,
+                            int64_t *mixed_volume_out)
 {
     if (!n_cells_out) return phc::set_error(PHC_EINVAL, "phc_mixed_cells: n_cells_out is NULL");
     if (max_cells < 0) return phc::set_error(PHC_EINVAL, "phc_mixed_cells: max_cells < 0");
@@ -931,4 +970,16 @@ extern "C" int phc_mixed_cells(int n, const int32_t *terms_per_eq, const uint8_t
     *n_cells_out = count;
     if (mixed_volume_out) *mixed_volume_out = mv;
     return PHC_OK;
+}
+
+extern "C" int phc_mixed_cells(int n, const int32_t *terms_per_eq, const uint8_t *exps, const int32_t *lift,
+                               int64_t max_cells, int32_t *cells_out, int64_t *volumes_out, int64_t *n_cells_out,
+                               int64_t *mixed_volume_out)
+{
+    try {
+        return mixed_cells_impl(n, terms_per_eq, exps, lift, max_cells, cells_out, volumes_out, n_cells_out,
+                                mixed_volume_out);
+    } catch (...) {
+        return phc::set_error(PHC_ENOMEM, "phc_mixed_cells: host allocation failed");
+    }
 }

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -1661,9 +1662,8 @@ static HostTerms poly_terms(int n, const int32_t *tpe, const uint8_t *exps, cons
     return ht;
 }
 
-extern "C" int phc_make_polyhedral_homotopy(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
-                                            const int32_t *lift, const int32_t *cells, int64_t n_cells,
-                                            phc_homotopy **out)
+static int make_polyhedral_homotopy(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                                    const int32_t *lift, const int32_t *cells, int64_t n_cells, phc_homotopy **out)
 {
     if (!out) return fail(PHC_EINVAL, "out is NULL");
     *out = nullptr;
@@ -1691,8 +1691,8 @@ extern "C" int phc_make_polyhedral_homotopy(int n, const int32_t *tpe, const uin
         if (__builtin_add_overflow(path_off[c], vol, &path_off[c + 1]))
             return fail(PHC_EUNSUPPORTED, "polyhedral homotopy: more than 2^63 paths");
     }
-    phc_homotopy *h = new (std::nothrow) phc_homotopy();
-    if (!h) return fail(PHC_ENOMEM, "host allocation");
+    std::unique_ptr<phc_homotopy> own(new phc_homotopy());
+    phc_homotopy *h = own.get();
     h->n = n;
     h->n_sys = 1;
     h->polyhedral = 1;
@@ -1705,12 +1705,12 @@ extern "C" int phc_make_polyhedral_homotopy(int n, const int32_t *tpe, const uin
     h->paths_per_system = h->num_paths;
     cudaGetDevice(&h->device);
     const PolyBlock B = poly_block(path_off, powers, H, U, cells, (size_t)n_cells * 2 * n);
+    const HostTerms terms = poly_terms(n, tpe, exps, coefs);
     cudaStream_t ps = nullptr;
-    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
-        delete h;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess)
         return fail(PHC_ECUDA, "cudaStreamCreateWithFlags");
-    }
-    rc = upload_table(poly_terms(n, tpe, exps, coefs), n, h->total, ps);
+    own.release();  // from here phc_destroy_homotopy frees h and its device memory
+    rc = upload_table(terms, n, h->total, ps);
     if (!rc && cudaMalloc(&h->d_poly, B.host.size()) != cudaSuccess) rc = fail(PHC_ENOMEM, "cudaMalloc of the cell data");
     if (!rc && (cudaMemcpyAsync(h->d_poly, B.host.data(), B.host.size(), cudaMemcpyHostToDevice, ps) != cudaSuccess ||
                 cudaStreamSynchronize(ps) != cudaSuccess))
@@ -1730,6 +1730,17 @@ extern "C" int phc_make_polyhedral_homotopy(int n, const int32_t *tpe, const uin
     h->d_pairs = reinterpret_cast<const int32_t *>(b + B.o_pr);
     *out = h;
     return PHC_OK;
+}
+
+extern "C" int phc_make_polyhedral_homotopy(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                                            const int32_t *lift, const int32_t *cells, int64_t n_cells,
+                                            phc_homotopy **out)
+{
+    try {
+        return make_polyhedral_homotopy(n, tpe, exps, coefs, lift, cells, n_cells, out);
+    } catch (...) {
+        return fail(PHC_ENOMEM, "phc_make_polyhedral_homotopy: host allocation failed");
+    }
 }
 
 static phc::PolyLaunch poly_launch(const DevTables &tab, int n_cells, const char *block, const PolyBlock &B,
@@ -1837,10 +1848,9 @@ extern "C" int phc_track_polyhedral(phc_homotopy *h, int64_t first, int64_t n, c
 // batches of growing size (the first small, so that tracking starts early);
 // each batch is uploaded and launched on one of a few helper streams, so
 // batches overlap on the GPU, and its cell data are freed in stream order.
-extern "C" int phc_solve_polyhedral(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
-                                    const int32_t *lift, const phc_opts *opts, int64_t max_paths, phc_cd *x_out,
-                                    int8_t *cls_out, phc_path_stats *stats_out, int64_t *n_paths_out,
-                                    int64_t *n_cells_out, void *stream)
+static int solve_polyhedral(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs, const int32_t *lift,
+                            const phc_opts *opts, int64_t max_paths, phc_cd *x_out, int8_t *cls_out,
+                            phc_path_stats *stats_out, int64_t *n_paths_out, int64_t *n_cells_out, void *stream)
 {
     if (!n_paths_out) return fail(PHC_EINVAL, "n_paths_out is NULL");
     *n_paths_out = 0;
@@ -1909,63 +1919,69 @@ extern "C" int phc_solve_polyhedral(int n, const int32_t *tpe, const uint8_t *ex
         return rc;
     }
 
-    std::vector<int64_t> b_off(1, 0), b_H, b_U;
-    std::vector<double> b_pw;
-    std::vector<int32_t> b_pairs;
     int64_t launched = 0, mv = 0, cells = 0, limit = 64;
-    int next = 0;
     bool overflow = false;
-    auto flush = [&]() -> int {
-        const int64_t paths = b_off.back();
-        const int64_t nc = (int64_t)b_off.size() - 1;
-        if (nc == 0) return PHC_OK;
-        if (launched + paths > max_paths) overflow = true;
-        if (!overflow) {
-            const PolyBlock B = poly_block(b_off, b_pw, b_H, b_U, b_pairs.data(), b_pairs.size());
-            cudaStream_t hk = hs[next];
-            void *blk = nullptr;
-            CU(cudaMallocAsync(&blk, B.host.size(), hk));
-            // pageable source: staged before the call returns, so B may go
-            CU(cudaMemcpyAsync(blk, B.host.data(), B.host.size(), cudaMemcpyHostToDevice, hk));
-            phc::PolyLaunch L = poly_launch(tab.view, (int)nc, static_cast<const char *>(blk), B, 0, paths,
-                                            reinterpret_cast<double2 *>(x_out) + launched);
-            L.x_ld = max_paths;
-            L.stats = st + launched;
-            L.qhead = counters + next;
-            L.o = o;
-            CU(cudaMemsetAsync(counters + next, 0, sizeof(unsigned long long), hk));
-            cudaError_t e = phc::launch_track_poly(L, o.block_threads, o.max_blocks, hk);
-            if (e != cudaSuccess) return fail(PHC_ECUDA, "polyhedral track kernel launch: %s", cudaGetErrorString(e));
-            CU(cudaFreeAsync(blk, hk));
-            launched += paths;
-            next = (next + 1) % K;
-        }
-        b_off.assign(1, 0);
-        b_H.clear();
-        b_U.clear();
-        b_pw.clear();
-        b_pairs.clear();
-        if (limit < 16384) limit *= 2;
-        return PHC_OK;
-    };
-    rc = phc::enumerate_mixed_cells(n, tpe, exps, lift, [&](const int32_t *pairs, int64_t) -> int {
-        const size_t c = b_off.size() - 1;
-        b_H.resize((c + 1) * nn);
-        b_U.resize((c + 1) * nn);
-        b_pw.resize((c + 1) * (size_t)T);
-        int64_t vol = 0;
-        const int r = phc::cell_tracking_data(n, tpe, exps, lift, pairs, &b_pw[c * T], &b_H[c * nn], &b_U[c * nn], &vol);
-        if (r) return r;
-        for (int i = 0; i < 2 * n; i++)
-            if (coefs[pairs[i]].re == 0.0 && coefs[pairs[i]].im == 0.0)
-                return fail(PHC_EINVAL, "a cell's binomial system has a zero coefficient");
-        b_pairs.insert(b_pairs.end(), pairs, pairs + 2 * n);
-        b_off.push_back(b_off.back() + vol);
-        cells++;
-        if (__builtin_add_overflow(mv, vol, &mv)) return fail(PHC_EUNSUPPORTED, "mixed volume above 2^63");
-        return b_off.back() >= limit ? flush() : PHC_OK;
-    });
-    if (!rc) rc = flush();
+    // Host allocations below may throw: the GPU work already queued is still
+    // joined and synchronized before the resources go.
+    try {
+        std::vector<int64_t> b_off(1, 0), b_H, b_U;
+        std::vector<double> b_pw;
+        std::vector<int32_t> b_pairs;
+        int next = 0;
+        auto flush = [&]() -> int {
+            const int64_t paths = b_off.back();
+            const int64_t nc = (int64_t)b_off.size() - 1;
+            if (nc == 0) return PHC_OK;
+            if (launched + paths > max_paths) overflow = true;
+            if (!overflow) {
+                const PolyBlock B = poly_block(b_off, b_pw, b_H, b_U, b_pairs.data(), b_pairs.size());
+                cudaStream_t hk = hs[next];
+                void *blk = nullptr;
+                CU(cudaMallocAsync(&blk, B.host.size(), hk));
+                // pageable source: staged before the call returns, so B may go
+                CU(cudaMemcpyAsync(blk, B.host.data(), B.host.size(), cudaMemcpyHostToDevice, hk));
+                phc::PolyLaunch L = poly_launch(tab.view, (int)nc, static_cast<const char *>(blk), B, 0, paths,
+                                                reinterpret_cast<double2 *>(x_out) + launched);
+                L.x_ld = max_paths;
+                L.stats = st + launched;
+                L.qhead = counters + next;
+                L.o = o;
+                CU(cudaMemsetAsync(counters + next, 0, sizeof(unsigned long long), hk));
+                cudaError_t e = phc::launch_track_poly(L, o.block_threads, o.max_blocks, hk);
+                if (e != cudaSuccess) return fail(PHC_ECUDA, "polyhedral track kernel launch: %s", cudaGetErrorString(e));
+                CU(cudaFreeAsync(blk, hk));
+                launched += paths;
+                next = (next + 1) % K;
+            }
+            b_off.assign(1, 0);
+            b_H.clear();
+            b_U.clear();
+            b_pw.clear();
+            b_pairs.clear();
+            if (limit < 16384) limit *= 2;
+            return PHC_OK;
+        };
+        rc = phc::enumerate_mixed_cells(n, tpe, exps, lift, [&](const int32_t *pairs, int64_t) -> int {
+            const size_t c = b_off.size() - 1;
+            b_H.resize((c + 1) * nn);
+            b_U.resize((c + 1) * nn);
+            b_pw.resize((c + 1) * (size_t)T);
+            int64_t vol = 0;
+            const int r = phc::cell_tracking_data(n, tpe, exps, lift, pairs, &b_pw[c * T], &b_H[c * nn], &b_U[c * nn], &vol);
+            if (r) return r;
+            for (int i = 0; i < 2 * n; i++)
+                if (coefs[pairs[i]].re == 0.0 && coefs[pairs[i]].im == 0.0)
+                    return fail(PHC_EINVAL, "a cell's binomial system has a zero coefficient");
+            b_pairs.insert(b_pairs.end(), pairs, pairs + 2 * n);
+            b_off.push_back(b_off.back() + vol);
+            cells++;
+            if (__builtin_add_overflow(mv, vol, &mv)) return fail(PHC_EUNSUPPORTED, "mixed volume above 2^63");
+            return b_off.back() >= limit ? flush() : PHC_OK;
+        });
+        if (!rc) rc = flush();
+    } catch (...) {
+        rc = fail(PHC_ENOMEM, "polyhedral pipeline: host allocation failed");
+    }
     // join, then classify every path at t = 1 on the caller's stream
     for (int k = 0; k < K; k++)
         if ((cudaEventRecord(ev[k], hs[k]) != cudaSuccess || cudaStreamWaitEvent(s, ev[k], 0) != cudaSuccess) && !rc)
@@ -1981,6 +1997,19 @@ extern "C" int phc_solve_polyhedral(int n, const int32_t *tpe, const uint8_t *ex
     if (overflow)
         return fail(PHC_EINVAL, "the mixed volume %lld exceeds max_paths %lld", (long long)mv, (long long)max_paths);
     return PHC_OK;
+}
+
+extern "C" int phc_solve_polyhedral(int n, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
+                                    const int32_t *lift, const phc_opts *opts, int64_t max_paths, phc_cd *x_out,
+                                    int8_t *cls_out, phc_path_stats *stats_out, int64_t *n_paths_out,
+                                    int64_t *n_cells_out, void *stream)
+{
+    try {
+        return solve_polyhedral(n, tpe, exps, coefs, lift, opts, max_paths, x_out, cls_out, stats_out, n_paths_out,
+                                n_cells_out, stream);
+    } catch (...) {
+        return fail(PHC_ENOMEM, "phc_solve_polyhedral: host allocation failed");
+    }
 }
 
 // ------------------------------------------------------------------ internal accessors (noalloc.cu)
