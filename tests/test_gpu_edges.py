@@ -1,7 +1,7 @@
 """Edge cases through the C ABI on the GPU: the largest number of unknowns
-(12) in every tracker (double, double double, forced tail hand-off and
-compaction off and on), single paths at the ends of the range, and empty
-calls of every entry point."""
+(12) in every tracker (double, double double, quad double, forced tail
+hand-off and compaction off and on, polyhedral), single paths at the ends of
+the range, and empty calls of every entry point."""
 import numpy as np
 import pytest
 import torch
@@ -10,7 +10,7 @@ import oracle
 import paper_1804_03807_gb300 as P
 from workloads import PolySystem, cn01, configs, cyclic, rng_for, unit_gamma
 from workloads.systems import all_monomials
-from tests._checks import relative_residual, same_set
+from tests._checks import exact_residual_parts, match_sets, relative_residual, same_set
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +49,39 @@ def test_twelve_unknowns_every_tracker():
     assert np.array_equal(rd.cls.cpu().numpy(), c)
     ok, err = same_set(xd[c == 0], xo[co == 0], 1e-10)
     assert ok, err
+
+
+def test_twelve_unknowns_quad_double_and_polyhedral():
+    """The same system in quad double (both endpoints equal to the oracle's
+    quad double endpoints within 1e-55 and roots of f to 1e-58 in exact
+    arithmetic) and by polyhedral homotopies: the mixed volume of a dense
+    system is its Bezout number (2), and the two paths end at the oracle's
+    total-degree roots."""
+    from fractions import Fraction
+    from workloads import random_lifting
+    s = _system12()
+    g = unit_gamma(rng_for(96))
+    h = P.phc_make_homotopy(s, g)
+    r, parts = P.track_qd(h)
+    pg = np.transpose(parts.cpu().numpy(), (2, 1, 0))
+    po, co, _ = oracle.track_qd(oracle.total_degree(s, g))
+    assert np.all(r.cls.cpu().numpy() == 0) and np.all(co == 0)
+    ra, rb, rel = match_sets(pg[:, :, 0], po[:, :, 0])
+    assert len(ra) == 2 and rel.max() <= 1e-10
+    for a, b in zip(ra, rb):
+        for j in range(12):
+            for part in (np.real, np.imag):
+                d = sum(Fraction(float(part(v))) - Fraction(float(part(w))) for v, w in zip(pg[a, j], po[b, j]))
+                assert abs(float(d)) <= 1e-55 * (1 + np.abs(po[b, :, 0]).max())
+        assert exact_residual_parts(s, pg[a]) <= 1e-58
+    lift = random_lifting(rng_for(97), s.n_terms)
+    _, vols, mv = P.phc_mixed_cells(s, lift)
+    assert mv == 2
+    rp = P.solve_polyhedral(s, lift, mv)
+    xp, cp = rp.x.cpu().numpy().T, rp.cls.cpu().numpy()
+    assert np.all(cp == P.PHC_REGULAR)
+    ok, err = same_set(xp, po[:, :, 0], 1e-10)
+    assert ok and relative_residual(s, xp).max() <= 1e-12, err
 
 
 def test_single_paths_at_the_ends_and_empty_calls():
