@@ -689,8 +689,16 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
     // the owner's evaluation slots, which are free between units), and the
     // warps left without a path stop issuing.  No path's arithmetic changes.
     // Lanes then never leave the loop alone: the block leaves it together
-    // once every lane is idle and has found the queue empty.
+    // once every lane is idle and has found the queue empty.  The checks
+    // start once the queue is empty: before that no lane idles, and a block
+    // barrier would hold the warps of less loaded SM partitions (a block of
+    // 6 warps puts two on each of two partitions, each of which issues one
+    // FP64 warp instruction per ~64 cycles) at the pace of the loaded ones.
+    // Each thread passes one joining barrier when it first sees the queue
+    // empty and counts its iterations from there, so every thread passes the
+    // same sequence of barriers.
     const bool compact = COMPACT && L.compact;
+    bool joined = false;
     bool done = false;  // (compaction) this lane is idle and counted in idle_n (it found the queue
                         // empty or handed its path off); lanes the compaction empties are counted
                         // too, and a counted lane that receives a path is taken off again, so
@@ -706,7 +714,11 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
 
     for (;;) {
         if constexpr (COMPACT) {
-            if (compact && (iter++ & (COMPACT_EVERY - 1)) == 0) {
+            if (compact && !joined && *reinterpret_cast<volatile unsigned long long *>(L.qhead) >= (unsigned long long)np) {
+                __syncthreads();
+                joined = true;
+            }
+            if (compact && joined && (iter++ & (COMPACT_EVERY - 1)) == 0) {
                 // every thread of the block reaches these barriers at the same iteration
                 if (__syncthreads_and(q < 0 && done)) break;
                 const int live = __syncthreads_count(q >= 0);
