@@ -28,7 +28,9 @@
  *  - A handle keeps per-call scratch (queue and hand-off counters, records):
  *    tracking calls on one handle must not overlap on the GPU (issue them on
  *    one stream, or order the streams); different handles are independent.
- *  - The library never exits, aborts or traps on the device.
+ *  - The library never exits, aborts or traps on the device; no C++
+ *    exception leaves an entry point (a failed host allocation returns
+ *    PHC_ENOMEM; the outputs of that call are then undefined).
  */
 #ifndef PHC_H
 #define PHC_H

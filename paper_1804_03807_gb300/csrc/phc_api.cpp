@@ -281,7 +281,7 @@ static int validate_lists(int n_eq, int n_var, const int32_t *tpe, const uint8_t
 
 extern "C" int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, int n_sys,
                                        const phc_cd *coefs, const phc_cd *gammas, phc_homotopy **out)
-{
+try {
     if (!out) return fail(PHC_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_sys < 1) return fail(PHC_EINVAL, "n_systems = %d < 1", n_sys);
@@ -386,6 +386,8 @@ extern "C" int phc_make_homotopy_batch(int n_eq, int n_var, const int32_t *tpe, 
     }
     *out = h;
     return PHC_OK;
+} catch (...) {
+    return fail(PHC_ENOMEM, "phc_make_homotopy_batch: host allocation failed");
 }
 
 extern "C" int phc_make_homotopy(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
@@ -397,7 +399,7 @@ extern "C" int phc_make_homotopy(int n_eq, int n_var, const int32_t *tpe, const 
 extern "C" int phc_make_parameter_homotopy(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps,
                                            int n_sys, const phc_cd *coefs_start, const phc_cd *coefs_target,
                                            phc_cd gamma, phc_homotopy **out)
-{
+try {
     if (!out) return fail(PHC_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_sys < 1) return fail(PHC_EINVAL, "n_systems = %d < 1", n_sys);
@@ -467,6 +469,8 @@ extern "C" int phc_make_parameter_homotopy(int n_eq, int n_var, const int32_t *t
     }
     *out = h;
     return PHC_OK;
+} catch (...) {
+    return fail(PHC_ENOMEM, "phc_make_parameter_homotopy: host allocation failed");
 }
 
 extern "C" void phc_destroy_homotopy(phc_homotopy *h)
@@ -1032,7 +1036,7 @@ static int helper_streams(cudaStream_t st, size_t count, std::vector<cudaStream_
 
 extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
                               int8_t *const *cls_out, phc_path_stats *const *stats_out, void *stream)
-{
+try {
     if (n_h < 0 || (n_h > 0 && (!hs || !x_out || !cls_out))) return fail(PHC_EINVAL, "NULL argument");
     if (n_h == 0) return PHC_OK;
     phc_opts o;
@@ -1087,6 +1091,8 @@ extern "C" int phc_track_many(phc_homotopy *const *hs, int n_h, const phc_opts *
     }
     cudaEventDestroy(fork_ev);
     return PHC_OK;
+} catch (...) {
+    return fail(PHC_ENOMEM, "phc_track_many: host allocation failed");
 }
 
 // ------------------------------------------------------------------ multi-system plans
@@ -1121,7 +1127,7 @@ extern "C" void phc_many_plan_destroy(phc_many_plan *p)
 extern "C" int phc_many_plan_create(phc_homotopy *const *hs, int n_h, const phc_opts *opts, phc_cd *const *x_out,
                                     int8_t *const *cls_out, phc_path_stats *const *stats_out, void *stream,
                                     phc_many_plan **out)
-{
+try {
     if (!out) return fail(PHC_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_h < 1 || !hs || !x_out || !cls_out) return fail(PHC_EINVAL, "NULL argument or n_h < 1");
@@ -1182,6 +1188,8 @@ extern "C" int phc_many_plan_create(phc_homotopy *const *hs, int n_h, const phc_
     }
     *out = p;
     return PHC_OK;
+} catch (...) {
+    return fail(PHC_ENOMEM, "phc_many_plan_create: host allocation failed");
 }
 
 extern "C" int phc_many_plan_run(phc_many_plan *p, void *stream)
@@ -1326,7 +1334,7 @@ extern "C" int phc_membership_test(int n_eq, int n_var, const int32_t *tpe, cons
                                    const phc_cd *coefs, int k, const phc_cd *witness, int64_t m,
                                    const phc_cd *points, int64_t p, double tol, const phc_opts *opts,
                                    uint8_t *on_out, phc_cd *x_out, int8_t *cls_out, void *stream)
-{
+try {
     if (k < 1 || k >= n_var) return fail(PHC_EINVAL, "k = %d outside 1..n_var-1", k);
     if (m < 1 || p < 0) return fail(PHC_EINVAL, "need m >= 1 witness points and p >= 0 test points");
     if (p == 0) return PHC_OK;
@@ -1423,6 +1431,8 @@ extern "C" int phc_membership_test(int n_eq, int n_var, const int32_t *tpe, cons
     if (!cls_out && co) cudaFree(co);
     phc_destroy_homotopy(h);
     return rc;
+} catch (...) {
+    return fail(PHC_ENOMEM, "phc_membership_test: host allocation failed");
 }
 
 extern "C" int phc_refine_endpoints(const phc_homotopy *hc, phc_cd *x_hi, phc_cd *x_lo, int64_t n,
@@ -1473,7 +1483,7 @@ struct Lcg {
 
 extern "C" int phc_embed(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs, int D,
                          const phc_cd *gammas, const phc_cd *hyper, uint64_t seed, phc_system_lists **out)
-{
+try {
     if (!out) return fail(PHC_EINVAL, "out is NULL");
     *out = nullptr;
     if (D < 0) return fail(PHC_EINVAL, "top_dim = %d < 0", D);
@@ -1533,6 +1543,8 @@ extern "C" int phc_embed(int n_eq, int n_var, const int32_t *tpe, const uint8_t 
     std::memcpy(L->coefs, ocoef.data(), ocoef.size() * sizeof(phc_cd));
     *out = L;
     return PHC_OK;
+} catch (...) {
+    return fail(PHC_ENOMEM, "phc_embed: host allocation failed");
 }
 
 // Output lists of a host-side transformation (phc_embed, phc_square).
@@ -1560,7 +1572,7 @@ static int make_lists(int n_eq, int n_var, const std::vector<int32_t> &tpe, cons
 
 extern "C" int phc_square(int n_eq, int n_var, const int32_t *tpe, const uint8_t *exps, const phc_cd *coefs,
                           const phc_cd *consts, uint64_t seed, phc_system_lists **out)
-{
+try {
     if (!out) return fail(PHC_EINVAL, "out is NULL");
     *out = nullptr;
     int rc = validate_lists(n_eq, n_var, tpe, exps, coefs, false, nullptr);
@@ -1611,6 +1623,8 @@ extern "C" int phc_square(int n_eq, int n_var, const int32_t *tpe, const uint8_t
         }
     }
     return make_lists(N, N, otpe, oexp, ocoef, out);
+} catch (...) {
+    return fail(PHC_ENOMEM, "phc_square: host allocation failed");
 }
 
 extern "C" void phc_free_lists(phc_system_lists *L)

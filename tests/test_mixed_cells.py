@@ -104,3 +104,36 @@ def test_a_support_of_one_point_has_no_cells():
                    np.array([1.0, 2.0, 3.0]))
     cells, vols, mv = P.phc_mixed_cells(s, np.array([5, 7, 9], dtype=np.int32))
     assert cells.shape[0] == 0 and mv == 0
+
+
+def test_host_allocation_failure_is_an_error_code():
+    """Two equations of 4096 terms each (every exponent pair below 64) ask for
+    16.8 M candidate edges; under an address-space limit the search runs out
+    of host memory, and the call returns PHC_ENOMEM instead of aborting the
+    process (run in a child process, whose limit does not outlive it)."""
+    import subprocess
+    import sys as _sys
+    if not os.path.exists("/proc/self/status"):
+        pytest.skip("needs /proc/self/status")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r'''
+import resource, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import paper_1804_03807_gb300 as P
+from workloads import PolySystem, random_lifting, rng_for
+grid = np.array([(a, b) for a in range(64) for b in range(64)], dtype=np.uint8)
+s = PolySystem(2, 2, np.array([4096, 4096]), np.vstack([grid, grid]), np.ones(8192, dtype=np.complex128))
+lift = random_lifting(rng_for(560), s.n_terms)
+P.load()
+vm = int(open("/proc/self/status").read().split("VmSize:")[1].split()[0]) * 1024
+resource.setrlimit(resource.RLIMIT_AS, (vm + (96 << 20), resource.RLIM_INFINITY))
+try:
+    P.phc_mixed_cells(s, lift)
+    print("no error")
+except P.PhcError as e:
+    print("code", e.code, str(e))
+'''
+    r = subprocess.run([_sys.executable, "-c", code, root], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "code -2" in r.stdout and "allocation" in r.stdout, r.stdout + r.stderr[-2000:]
