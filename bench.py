@@ -356,6 +356,8 @@ def run_gpu(args):
     if traffic is None and args.precision == 0 and tail_on and (opts.tail_threads or 32) == 32:
         traffic = (203_264 + 256 + 337_408) * units / 3_969_533
     secs = kern_ms / 1e3
+    # the same peak measured on this device (independent FMA chains, every SM)
+    probe = P.phc_fp64_probe(16, 200_000, stream=main)
     frac = (f64 / secs / 1e12) / FP64_PEAK_TFLOPS
     frac32 = (f32 / secs / 1e12) / FP32_PEAK_TFLOPS
     roofline = {"bound": "alu", "achieved": f64 / secs / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -369,6 +371,7 @@ def run_gpu(args):
                 "fp32_units_per_step": units32, "kernel_ms": kern_ms,
                 "flops_per_unit": uf,
                 "peak_source": "derived: 152 SMs x 2 FP64 (128 FP32) FMA/clk x 2 flops x 2.07 GHz",
+                "peak_probe": probe, "frac_of_probe": f64 / secs / 1e12 / probe if probe > 0 else None,
                 "frac_formula": "frac = fp64_flops/peak/T; fp32_frac = fp32_flops/fp32_peak/T; "
                                 "flops = units x flops_per_unit (FP64 flops the kernel executes per unit)"}
 

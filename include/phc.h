@@ -496,6 +496,18 @@ int phc_refine_endpoints(const phc_homotopy *h, phc_cd *x_hi_io, phc_cd *x_lo_ou
 int phc_track_paths_noalloc(phc_homotopy *h, int64_t first_path, int64_t n_paths, const phc_opts *opts,
                             phc_cd *x_out, int8_t *cls_out, phc_path_stats *stats_out, void *cuda_stream);
 
+/* ---------------------------------------------------------------- measurement */
+
+/* The FP64 rate of the current device, measured (the paper has no
+ * counterpart: the trackers are bound by double precision arithmetic, and
+ * this measures the peak their roofline divides by).  Launches 2 blocks per
+ * SM of warps_per_block warps (1..32) on the stream; every thread runs 8
+ * independent fused multiply-add chains for iters (1..1e8) iterations.
+ * Synchronizes on the stream, then writes 2 x 8 x iters x threads / seconds
+ * / 1e12 to *tflops_out (host).  Errors: PHC_EINVAL for NULL tflops_out or a
+ * count out of range; PHC_ECUDA. */
+int phc_fp64_probe(int warps_per_block, int64_t iters, double *tflops_out, void *cuda_stream);
+
 /* ---------------------------------------------------------------- polyhedral homotopies */
 
 /* Fine mixed cells of the Newton polytopes of a square system under an

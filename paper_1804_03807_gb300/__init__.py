@@ -34,7 +34,7 @@ from ._lib import (PHC_STOP_SKIPPED, phc_cascade_from, PHC_AT_INFINITY, PHC_FAIL
                    phc_make_parameter_homotopy, phc_track_from, phc_membership_test, phc_square,
                    phc_many_plan_create, phc_many_plan_run, ManyPlan, phc_track_paths_dd, phc_endgame,
                    phc_mixed_cells, phc_make_polyhedral_homotopy, phc_polyhedral_starts, phc_track_polyhedral,
-                   phc_solve_polyhedral, phc_track_paths_qd)
+                   phc_solve_polyhedral, phc_track_paths_qd, phc_fp64_probe)
 
 __all__ = [
     "PHC_AT_INFINITY", "PHC_FAILED", "PHC_MAX_VARS", "PHC_PREC_FP32_INTERIOR", "PHC_PREC_FP64", "PHC_REGULAR",
@@ -48,6 +48,7 @@ __all__ = [
     "track_from", "membership", "phc_square", "phc_many_plan_create", "phc_many_plan_run", "ManyPlan",
     "phc_track_paths_dd", "track_dd", "phc_endgame", "endgame",
     "phc_mixed_cells", "phc_make_polyhedral_homotopy", "phc_polyhedral_starts", "phc_track_polyhedral",
+    "phc_fp64_probe",
     "phc_solve_polyhedral", "polyhedral_starts", "track_polyhedral", "solve_polyhedral",
     "phc_track_paths_qd", "track_qd",
 ]

@@ -119,6 +119,7 @@ def load() -> ctypes.CDLL:
     L.phc_track_polyhedral.argtypes = [vp, i64, i64, ctypes.POINTER(phc_opts), vp, vp, vp, vp]
     L.phc_solve_polyhedral.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(phc_opts), i64, vp, vp, vp,
                                        ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
+    L.phc_fp64_probe.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp]
     L.phc_last_error.restype = ctypes.c_char_p
     L.phc_destroy_homotopy.argtypes = [vp]
     L.phc_destroy_homotopy.restype = None
@@ -132,7 +133,7 @@ def load() -> ctypes.CDLL:
                  "phc_tail_paths", "phc_make_parameter_homotopy", "phc_track_from", "phc_membership_test",
                  "phc_square", "phc_many_plan_create", "phc_many_plan_run", "phc_track_paths_dd", "phc_endgame",
                  "phc_mixed_cells", "phc_make_polyhedral_homotopy", "phc_polyhedral_starts",
-                 "phc_track_polyhedral", "phc_solve_polyhedral", "phc_track_paths_qd"):
+                 "phc_track_polyhedral", "phc_solve_polyhedral", "phc_track_paths_qd", "phc_fp64_probe"):
         getattr(L, name).restype = ctypes.c_int
     if L.phc_sizeof_opts() != ctypes.sizeof(phc_opts):
         raise ImportError("phc_opts layout mismatch between phc.h and the binding")
@@ -360,6 +361,13 @@ def phc_endgame(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cycle_o
     _check(load().phc_endgame(ctypes.c_void_p(h.ptr), int(first_path), int(n_paths),
                               ctypes.byref(opts) if opts is not None else None, _ptr(x_out), _ptr(cycle_out),
                               _ptr(stats_out), _stream_ptr(stream)))
+
+
+def phc_fp64_probe(warps_per_block: int = 16, iters: int = 200_000, stream=None) -> float:
+    """Measured FP64 rate of the current device in TFLOP/s (synchronizes)."""
+    out = ctypes.c_double(0.0)
+    _check(load().phc_fp64_probe(int(warps_per_block), int(iters), ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def phc_track_paths_noalloc(h: Homotopy, first_path: int, n_paths: int, opts, x_out, cls_out, stats_out=None,

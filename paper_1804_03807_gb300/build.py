@@ -22,7 +22,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["track.cu", "track_pipe.cu", "track_multi.cu", "track_tail.cu", "track_dd.cu", "track_qd.cu", "endgame.cu", "track_poly.cu", "refine.cu",
-           "noalloc.cu", "mixed_cells.cpp", "phc_api.cpp"]
+           "noalloc.cu", "probe.cu", "mixed_cells.cpp", "phc_api.cpp"]
 
 
 def nvcc() -> str:

@@ -109,3 +109,15 @@ def test_single_paths_at_the_ends_and_empty_calls():
     with pytest.raises(P.PhcError):
         P.phc_track_paths(hb, total, 1, None, e, c)  # beyond the last path
     torch.cuda.synchronize()
+
+
+def test_fp64_probe_measures_the_derived_peak():
+    """The measured FP64 rate lies near the peak derived from the units and
+    the clock (152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz = 1.259
+    TFLOP/s); bad counts are rejected."""
+    v = P.phc_fp64_probe(16, 200_000)
+    assert 0.6 * 1.259 <= v <= 1.2 * 1.259, v
+    with pytest.raises(P.PhcError):
+        P.phc_fp64_probe(0, 10)
+    with pytest.raises(P.PhcError):
+        P.phc_fp64_probe(4, 0)
