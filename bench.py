@@ -349,12 +349,12 @@ def run_gpu(args):
     f32 = units32 * uf
     kern_ms = float(np.mean([p0.elapsed_time(p1) for p0, p1 in pairs]))
     # DRAM bytes (read + write) per tracking call: ncu counters of track_kernel<7,0>
-    # (203,264 + 256 B) and tail_kernel<7,32> (337,408 B) tracking one system of this
-    # batch (5040 paths, 3,969,533 units), scaled by the units of this step.
+    # (985,344 + 82,688 B) and tail_kernel<7,32> (785,664 + 0 B) tracking one system
+    # of this batch (5040 paths, 3,969,533 units), scaled by the units of this step.
     # Only meaningful for the default FP64 configuration those kernels ran in.
     traffic = args.traffic
     if traffic is None and args.precision == 0 and tail_on and (opts.tail_threads or 32) == 32:
-        traffic = (203_264 + 256 + 337_408) * units / 3_969_533
+        traffic = (985_344 + 82_688 + 785_664) * units / 3_969_533
     secs = kern_ms / 1e3
     # the same peak measured on this device (independent FMA chains, every SM)
     probe = P.phc_fp64_probe(16, 200_000, stream=main)
