@@ -719,7 +719,8 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
                 joined = true;
             }
             if (compact && joined && (iter++ & (COMPACT_EVERY - 1)) == 0) {
-                // every thread of the block reaches these barriers at the same iteration
+                // every thread of the block reaches these barriers at the same count of
+                // iterations since its joining barrier
                 if (__syncthreads_and(q < 0 && done)) break;
                 const int live = __syncthreads_count(q >= 0);
                 const bool warp_live = __any_sync(FULL, q >= 0);
