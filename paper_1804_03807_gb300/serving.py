@@ -249,7 +249,10 @@ class Server:
         mem_used = 0
         active = []   # batches: (slot, reqs, bytes, admitted, handles, host, event, n_paths)
         results = {}
-        last_small = -1e9                              # last time a small request waited or ran
+        # last time a small request waited or ran; the session starts as if one
+        # just had, so a large request arriving first begins with capped chunks
+        # (small requests may follow it within idle_after seconds)
+        last_small = 0.0
         t0 = time.perf_counter()
         while pending or waiting or active or bigs:
             now = time.perf_counter() - t0
