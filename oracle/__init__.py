@@ -13,8 +13,9 @@ list manipulation.
 Parity pins (tests/test_oracle_*.py): Bezout counts, roots-of-unity starts,
 residuals, companion-matrix roots (n = 1), resultant roots (n = 2), gamma
 invariance, cyclic symmetry, Example 2.1 and Example 3.1 counts, double double
-against exact rationals.  Parity unpinned: per-path step counts and the map
-from start solutions to endpoints (reported only).
+against exact rationals, step counts of a linear path counted by hand.
+Parity unpinned: per-path step counts where floating point decides them, and
+the map from start solutions to endpoints (reported only).
 """
 from __future__ import annotations
 

@@ -32,8 +32,9 @@
  * Parity pins live in tests/ (Bezout counts, roots of unity, residuals,
  * companion-matrix and resultant roots, gamma invariance, cyclic symmetry,
  * Example 2.1 and Example 3.1 counts, double double against exact rationals).
- * The per-path step counts and the path-to-root map are "parity unpinned":
- * they are reported, never compared.
+ * The per-path step counts are pinned only where the step rules alone fix
+ * them (a linear path, every step accepted, counted by hand); elsewhere they
+ * and the path-to-root map are "parity unpinned": reported, never pinned.
  */
 #include <complex.h>
 #include <math.h>

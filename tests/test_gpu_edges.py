@@ -121,3 +121,24 @@ def test_fp64_probe_measures_the_derived_peak():
         P.phc_fp64_probe(0, 10)
     with pytest.raises(P.PhcError):
         P.phc_fp64_probe(4, 0)
+
+
+@pytest.mark.parametrize("rules,accepted", [((0.01, 0.1, 3), 18), ((0.05, 0.2, 2), 8)])
+def test_step_counts_on_a_linear_path_gpu(rules, accepted):
+    """The hand-counted steps of the path from x - 1 to x - a (every step
+    accepted; the step sizes follow from the expansion rule alone: 18 with
+    the default rules, 8 with h_init 0.05, h_max 0.2 and expansion after 2
+    accepts), in the one-thread tracker and with the tail hand-off forced."""
+    h_init, h_max, after = rules
+    for k, a in enumerate((0.5 + 0.25j, -2 + 1j, 3j)):
+        s = PolySystem(1, 1, np.array([2]), np.array([[1], [0]], dtype=np.uint8), np.array([1, -a]))
+        h = P.phc_make_homotopy(s, unit_gamma(rng_for(720 + k)))
+        for drain in (0.0, 1e-9):
+            o = P.phc_default_opts(tail_drain=drain)
+            o.h_init, o.h_max, o.expand_after = h_init, h_max, after
+            r = P.track(h, opts=o)
+            st = P.stats_numpy(r.stats)
+            assert r.cls.cpu().numpy()[0] == P.PHC_REGULAR
+            assert abs(r.x.cpu().numpy()[0, 0] - a) <= 1e-14 * abs(a)
+            assert st["n_accept"][0] == accepted and st["n_reject"][0] == 0 and st["t"][0] == 1.0
+            assert st["n_solve"][0] == 4 * accepted + st["n_newton"][0]

@@ -15,8 +15,8 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import (configs, cyclic, embedding_constants, multistep_example, random_dense, rng_for,
-                       univariate, unit_gamma)
+from workloads import (PolySystem, configs, cyclic, embedding_constants, multistep_example, random_dense,
+                       rng_for, univariate, unit_gamma)
 from tests._checks import eval_system, min_pair_distance, relative_residual, same_set
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_examples.json")))
@@ -318,3 +318,26 @@ def test_failure_and_singular_classes():
     assert sorted(cls2.tolist()) == [0, 1, 1]
     assert abs(xh[cls2 == 0][0, 0] + 2) < 1e-12
     assert np.all(np.abs(xh[cls2 == 1][:, 0] - 1) < 1e-5)
+
+
+@pytest.mark.parametrize("rules,accepted", [((0.01, 0.1, 3), 18), ((0.05, 0.2, 2), 8)])
+def test_step_counts_on_a_linear_path(rules, accepted):
+    """Step control (the predictor-corrector loop of Section 3; its step
+    rules): on the path from x - 1 to x - a every Newton correction
+    converges, so every step is accepted and the step sizes follow from the
+    expansion rule alone.  Counted by hand: with h_init 0.01, expansion by 2
+    after 3 accepts, h_max 0.1: three steps each of 0.01, 0.02, 0.04, 0.08
+    (t = 0.45), five of 0.1 (t = 0.95), and one clamped to land on t = 1: 18.
+    With h_init 0.05, expansion after 2 accepts, h_max 0.2: two each of 0.05
+    and 0.1 (t = 0.3), three of 0.2 (t = 0.9) and the clamped last: 8.  A unit
+    is one evaluate+solve, so the units are 4 per step plus the Newton
+    iterations."""
+    h_init, h_max, after = rules
+    o = oracle.default_opts()
+    o.h_init, o.h_max, o.expand_after = h_init, h_max, after
+    for k, a in enumerate((0.5 + 0.25j, -2 + 1j, 3j)):
+        s = PolySystem(1, 1, np.array([2]), np.array([[1], [0]], dtype=np.uint8), np.array([1, -a]))
+        x, cls, st = oracle.track(oracle.total_degree(s, unit_gamma(rng_for(720 + k))), opts=o, threads=1)
+        assert cls[0] == 0 and abs(x[0, 0] - a) <= 1e-14 * abs(a)
+        assert st["n_accept"][0] == accepted and st["n_reject"][0] == 0 and st["t"][0] == 1.0
+        assert st["n_solve"][0] == 4 * accepted + st["n_newton"][0]
