@@ -95,6 +95,13 @@ __host__ __device__ inline size_t thread_smem_bytes(int n, bool scale = false, b
 #define PHC_LOCALP_MASK ((1u << 7) | (1u << 8) | (1u << 11))
 #endif
 __host__ __device__ constexpr bool localp_of(int n) { return ((PHC_LOCALP_MASK) >> n) & 1u; }
+// The same for the pipelined tracker (top stage and cascade stage in one
+// launch), whose threads also keep the classification scales: N = 7, 8 and 9
+// gain a warp per block (160 -> 192, 128 -> 160, 96 -> 128 threads).
+#ifndef PHC_LOCALP_PIPE_MASK
+#define PHC_LOCALP_PIPE_MASK ((1u << 7) | (1u << 8) | (1u << 9))
+#endif
+__host__ __device__ constexpr bool localp_pipe_of(int n) { return ((PHC_LOCALP_PIPE_MASK) >> n) & 1u; }
 
 // One system of a multi-system launch (systems of different structure and
 // equal number of unknowns tracked in one kernel).

@@ -491,7 +491,7 @@ __device__ __forceinline__ ThreadArrays thread_arrays(char *smem, size_t table_b
 // readings in include/phc.h, identical to the oracle's).  s carries stop, t,
 // grew and system in; cond, relres and norm_x (and stop for a non-finite
 // endpoint) out.
-template <int N>
+template <int N, bool LP = false>
 __device__ __forceinline__ int8_t classify_one(const SmTab &tb, const ThreadArrays &A, phc_path_stats &s,
                                                const phc_opts &o, int bt)
 {
@@ -510,7 +510,7 @@ __device__ __forceinline__ int8_t classify_one(const SmTab &tb, const ThreadArra
     if (s.stop == PHC_STOP_SKIPPED) return -1;
     if (fin && s.stop != PHC_STOP_DIVERGED) {
         const double2 *C0 = tb.c0 + (size_t)s.system * tb.n_terms, *C1 = tb.c1 + (size_t)s.system * tb.n_terms;
-        evaluate<N, double2, true>(C0, C1, tb, 1.0, false, true, A.xe, A.R, A.J, A.P, A.S, bt);
+        evaluate<N, double2, true, LP>(C0, C1, tb, 1.0, false, true, A.xe, A.R, A.J, A.P, A.S, bt);
         double rr = 0.0;
 #pragma unroll
         for (int i = 0; i < N; i++) {
@@ -596,13 +596,21 @@ __host__ __device__ inline size_t compact_smem_bytes(int bt) { return 64 * sizeo
 // time.  Modes 1 and 2 classify inline.
 enum { MODE_SINGLE = 0, MODE_PIPE = 1, MODE_MULTI = 2 };
 
+// Whether the tracker of this mode and N keeps its prefix products in local memory.
+template <int N, int MODE>
+__host__ __device__ constexpr bool mode_localp()
+{
+    return (MODE == MODE_SINGLE && localp_of(N)) || (MODE == MODE_PIPE && localp_pipe_of(N));
+}
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t table_bytes, size_t table2_bytes)
 {
     constexpr bool PIPE = MODE == MODE_PIPE;
     constexpr bool MULTI = MODE == MODE_MULTI;
     // prefix products in local memory for the numbers of unknowns in PHC_LOCALP_MASK
-    constexpr bool LOCALP = MODE == MODE_SINGLE && localp_of(N);
+    // (PHC_LOCALP_PIPE_MASK for the pipeline)
+    constexpr bool LOCALP = mode_localp<N, MODE>();
     // compaction needs 3N + 11 free slots per thread between units (R, (P), J:
     // N^2 + 2N, with LOCALP N^2 + N)
     constexpr bool COMPACT = MODE == MODE_SINGLE && N >= (LOCALP ? 5 : 4);
@@ -1183,7 +1191,7 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackLaunch L, size_t 
         // modes 1 and 2 classify here
 #pragma unroll
         for (int j = 0; j < N; j++) SL(A.xe, j) = x0[j];
-        const int8_t c = classify_one<N>(*cur, A, rec, o, bt);
+        const int8_t c = classify_one<N, LOCALP>(*cur, A, rec, o, bt);
         if constexpr (MULTI) {
             const SysDesc &d = L.multi[ws];
             for (int j = 0; j < N; j++) d.x_out[(int64_t)j * d.n_paths + q] = x0[j];
@@ -1230,7 +1238,7 @@ static int64_t lanes_n(const TrackLaunch &L, int bt, int max_blocks)
     const size_t tb = MODE == MODE_MULTI  ? (size_t)(bt / 32) * (size_t)L.warp_table_bytes
                       : MODE == MODE_PIPE ? table_smem_bytes(L.tab) + table_smem_bytes(L.tab2)
                                           : table_smem_bytes(L.tab);
-    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32, MODE == MODE_SINGLE && localp_of(N)) +
+    const size_t smem = tb + (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, f32, mode_localp<N, MODE>()) +
                         (MODE == MODE_SINGLE ? compact_smem_bytes(bt) : 0);
     if (cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
@@ -1260,7 +1268,7 @@ static cudaError_t launch_track_n(const TrackLaunch &L_in, int bt, int max_block
     const size_t smem =
         tb + tb2 +
         (size_t)bt * thread_smem_bytes(N, MODE != MODE_SINGLE, L.o.precision == PHC_PREC_FP32_INTERIOR,
-                                       MODE == MODE_SINGLE && localp_of(N)) +
+                                       mode_localp<N, MODE>()) +
         (MODE == MODE_SINGLE ? compact_smem_bytes(bt) : 0);
     cudaError_t e =
         cudaFuncSetAttribute(track_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -10,7 +10,8 @@ cudaError_t launch_pipeline(const TrackLaunch &L, int block_threads, int max_blo
     device_limits();
     if (L.n_paths <= 0) return cudaSuccess;
     const size_t tb = table_smem_bytes(L.tab) + table_smem_bytes(L.tab2);
-    const int bt = track_block_threads(L.tab.n, tb, block_threads, true, L.o.precision == PHC_PREC_FP32_INTERIOR);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, true, L.o.precision == PHC_PREC_FP32_INTERIOR,
+                                       localp_pipe_of(L.tab.n));
     if (bt == 0) return cudaErrorInvalidConfiguration;
 #define PHC_CALL_PIPE(NN) launch_track_n<NN, MODE_PIPE>(L, bt, max_blocks, L.n_paths, s)
     PHC_DISPATCH_N(L.tab.n, PHC_CALL_PIPE)
@@ -21,7 +22,8 @@ int64_t pipe_lanes(const TrackLaunch &L, int block_threads, int max_blocks)
 {
     device_limits();
     const size_t tb = table_smem_bytes(L.tab) + table_smem_bytes(L.tab2);
-    const int bt = track_block_threads(L.tab.n, tb, block_threads, true, L.o.precision == PHC_PREC_FP32_INTERIOR);
+    const int bt = track_block_threads(L.tab.n, tb, block_threads, true, L.o.precision == PHC_PREC_FP32_INTERIOR,
+                                       localp_pipe_of(L.tab.n));
     if (bt == 0) return -1;
     switch (L.tab.n) {
     case 1: return lanes_n<1, MODE_PIPE>(L, bt, max_blocks);
