@@ -169,3 +169,28 @@ def exact_residual_parts(sys, parts: np.ndarray) -> float:
         worst = max(worst, val / (1.0 + scale))
         off += m
     return worst
+
+
+def min_pair_distance_large(A: np.ndarray, window: float = 1e-6, seed: int = 0) -> float:
+    """min_pair_distance for many rows: rows are sorted by a random real
+    projection, and only pairs whose projections lie within `window` of
+    each other are compared (two rows closer than `window` in the max-norm
+    have projections closer than window * ||w||_1, which the window covers
+    for the unit-modulus weights used).  Returns the smallest distance found
+    among those pairs, or inf when no pair has projections that close."""
+    A = np.atleast_2d(A)
+    if A.shape[0] < 2:
+        return float("inf")
+    rng = np.random.default_rng(seed)
+    w = np.exp(2j * np.pi * rng.random(A.shape[1])) / A.shape[1]
+    p = (A @ w).real
+    order = np.argsort(p)
+    ps, As = p[order], A[order]
+    best = float("inf")
+    for k in range(1, A.shape[0]):
+        close = np.nonzero(ps[k:] - ps[:-k] <= window)[0]
+        if close.size == 0:
+            break
+        d = np.max(np.abs(As[close + k] - As[close]), axis=1)
+        best = min(best, float(d.min()))
+    return best

@@ -267,3 +267,35 @@ def test_polyhedral_one_and_two_unknowns():
     assert np.all(c2 == P.PHC_REGULAR) and reg.shape[0] == mv
     _, _, d2 = match_sets(x2, reg)
     assert d2.max() <= 1e-9
+
+
+def test_random_cyclic11_all_184756_roots():
+    """Random-coefficient cyclic 11 by the pipelined polyhedral solve (cells on
+    the host threads while the GPU tracks the paths of the cells made so far,
+    Section 2.2, Figure 2): the mixed volume is the number of roots of cyclic
+    n for prime n, C(2n - 2, n - 1) = C(20, 10) = 184,756 (the roots of cyclic
+    7, 924 = C(12, 6), are pinned the same way), where the total-degree
+    homotopy would track 11! = 39,916,800 paths.  All but a few paths end at
+    regular roots, distinct and with small residuals; the few others fall
+    under the at-infinity readings -- on this system 10 end at t = 1 just
+    beyond the endpoint bound (norms 1.03e4 to 1.30e4) and 11 pass the
+    divergence bound within the first steps (t = 1.6e-4, norms ~5e6)."""
+    from math import comb
+    from tests._checks import min_pair_distance_large
+    g = with_random_coefficients(cyclic(11), rng_for(911))
+    lift = random_lifting(rng_for(961), g.n_terms)
+    r = P.solve_polyhedral(g, lift, comb(20, 10))
+    x, c = r.x.cpu().numpy().T, r.cls.cpu().numpy()
+    st = P.stats_numpy(r.stats)
+    assert x.shape[0] == comb(20, 10) == 184756
+    reg = c == P.PHC_REGULAR
+    assert reg.sum() >= 184756 - 64, np.bincount(c, minlength=4)
+    o = P.phc_default_opts()
+    # diverged (stop code 1), beyond the endpoint bound, or growing at the end: the
+    # at-infinity readings
+    far = (st["stop"] == 1) | (st["norm_x"] > o.endpoint_inf_norm) | (st["grew"] != 0)
+    assert np.all(c[~reg] == P.PHC_AT_INFINITY) and np.all(far[~reg])
+    xr = x[reg]
+    res = np.concatenate([relative_residual(g, xr[k:k + 8192]) for k in range(0, xr.shape[0], 8192)])
+    assert res.max() <= 1e-12, res.max()
+    assert min_pair_distance_large(xr, 1e-6) > 1e-6
