@@ -435,7 +435,8 @@ int orc_end_measures(const orc_homotopy *h, const double *x_ri, double *cond, do
  * Step control: the step is clamped to land on t = 1; after expand_after
  *   consecutive accepts it grows by `expand` (at most h_max), a rejection
  *   multiplies it by `shrink`.
- * Stop: t = 1; ||x|| > diverge_norm (at infinity); h < h_min, max_steps, or
+ * Stop: t = 1; ||x|| > diverge_norm (at infinity; for a polyhedral path
+ *   diverge_norm * max(1, ||x(0)||)); h < h_min, max_steps, or
  *   max_steps_decade steps without 1-t crossing a power of ten (stalled);
  *   non-finite values (failed).
  * End (only for paths that reached t = 1): Newton at t = 1 (<= end_iters),
@@ -451,6 +452,14 @@ static void track_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_sta
     const int n = h->n;
     cplx x0[NMAX], xs[NMAX], k1[NMAX], k2[NMAX], k3[NMAX], k4[NMAX];
     double t = 0.0, step = o->h_init;
+    /* divergence bound; a polyhedral path starts at a solution of its cell's
+       binomial system in the scaled coordinates, whose norm may already
+       exceed diverge_norm: its bound is diverge_norm * max(1, ||x(0)||) */
+    double div_bound = o->diverge_norm;
+    if (h->kind == 3) {
+        const double s0 = vnorm(n, x);
+        div_bound = o->diverge_norm * (s0 > 1.0 ? s0 : 1.0);
+    }
     int streak = 0, steps = 0;
     /* decade checkpoints: ||x|| at the first accepted t with 1-t <= 10^-k;
        the last five are kept (ring), nck counts all of them */
@@ -501,7 +510,7 @@ static void track_one(const orc_homotopy *h, const orc_opts *o, cplx *x, orc_sta
                 next_s *= 0.1;
                 if (nck >= 40) next_s = 0.0;
             }
-            if (vnorm(n, x) > o->diverge_norm) { st->stop = 1; break; }
+            if (vnorm(n, x) > div_bound) { st->stop = 1; break; }
             if (++streak >= o->expand_after) {
                 streak = 0;
                 step = step * o->expand;

@@ -163,6 +163,7 @@ static __device__ void plan_fill(const SmTab &tb, const TailPlan &p)
 // side c1 (H_t) or the same c0 + t c1 (H).
 struct LinearCoef {
     const double2 *C0, *C1;
+    __device__ __forceinline__ double diverge_bound(const phc_opts &o) const { return o.diverge_norm; }
     __device__ __forceinline__ void operator()(int q, double te, bool dt, double2 &ct, double2 &cr)
     {
         const double2 c0 = C0[q], c1 = C1[q];
@@ -173,7 +174,8 @@ struct LinearCoef {
 
 // Tracks one path to its end with the G lanes of a group (base: the group's
 // slots; coef(q, t, dt, ct, cr): term q's coefficient at t in H and H_x, and
-// in the right-hand side, H_t when dt, else H).  The path starts from the
+// in the right-hand side, H_t when dt, else H; coef.diverge_bound(o): the
+// norm beyond which the path counts as diverged).  The path starts from the
 // state in hd (a handed-off path, or a fresh one: t = 0, counters 0).  At the
 // end every lane calls finish(x0r, rec, units): lane r < N holds x_r, lane 0
 // the statistics record, units = the units run here.
@@ -411,7 +413,7 @@ __device__ __forceinline__ void tail_path(const Handoff &hd, const SmTab &tb, co
                 next_s *= 0.1;
                 if (nck >= 40) next_s = 0.0;
             }
-            if (nx > o.diverge_norm) {
+            if (nx > coef.diverge_bound(o)) {
                 stop = PHC_STOP_DIVERGED;
             } else {
                 if (++streak >= o.expand_after) {

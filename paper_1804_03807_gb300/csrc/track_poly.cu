@@ -118,12 +118,28 @@ __device__ __forceinline__ void poly_coef(double2 c, double p, double t, double 
     cr = dt ? make_double2(c.x * dtp, c.y * dtp) : ct;
 }
 
+// Divergence bound of a polyhedral path: diverge_norm x max(1, ||y(0)||).
+// The start solution of a cell's binomial system (the y coordinates at t = 0)
+// may itself lie beyond diverge_norm without the path diverging.
+template <int N>
+__device__ __forceinline__ double poly_diverge_bound(const double2 (&y)[N], double diverge_norm)
+{
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        const double a = absinf(y[j]);
+        if (!(a <= s)) s = a;
+    }
+    return diverge_norm * (s > 1.0 ? s : 1.0);
+}
+
 // The same coefficients for tail_path (the grouped tracker), log t taken
-// once per t.
+// once per t; div: the path's divergence bound.
 struct PolyCoef {
     const double2 *C;
     const double *pw;
-    double last_t, lt;
+    double last_t, lt, div;
+    __device__ __forceinline__ double diverge_bound(const phc_opts &) const { return div; }
     __device__ __forceinline__ void operator()(int q, double te, bool dt, double2 &ct, double2 &cr)
     {
         if (te != last_t) {
@@ -211,6 +227,7 @@ __global__ void __launch_bounds__(256) track_poly_kernel(const PolyLaunch L, siz
         const int64_t q = (int64_t)c;
         const int cell = poly_start<N>(L, L.first + q, x0);
         const double *pw = L.powers + (size_t)cell * tb.n_terms;
+        const double div = poly_diverge_bound<N>(x0, o.diverge_norm);
         double t = 0.0, h = o.h_init, next_s = 0.1;
         double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0;
         int streak = 0, steps = 0, nck = 0, since_ck = 0, n_acc = 0, n_rej = 0, n_newt = 0, n_solve = 0;
@@ -286,7 +303,7 @@ __global__ void __launch_bounds__(256) track_poly_kernel(const PolyLaunch L, siz
                     next_s *= 0.1;
                     if (nck >= 40) next_s = 0.0;
                 }
-                if (nx > o.diverge_norm) {
+                if (nx > div) {
                     stop = PHC_STOP_DIVERGED;
                     break;
                 }
@@ -392,7 +409,8 @@ __global__ void __launch_bounds__(128) poly_group_kernel(const PolyLaunch L, siz
         hd.q = q;
         hd.sys = hd.streak = hd.steps = hd.since_ck = hd.nck = 0;
         hd.n_acc = hd.n_rej = hd.n_newt = hd.n_solve = hd.n_f32 = hd.stage = 0;
-        const PolyCoef coef{tb.c1, L.powers + (size_t)cell * tb.n_terms, -1.0, 0.0};
+        const PolyCoef coef{tb.c1, L.powers + (size_t)cell * tb.n_terms, -1.0, 0.0,
+                            poly_diverge_bound<N>(y, L.o.diverge_norm)};
         tail_path<N, G>(hd, tb, plan, coef, base, L.o, r, gmask, [&](double2 x0r, const phc_path_stats &rec, int) {
             if (r < N) L.x_out[(int64_t)r * xld + q] = x0r;
             if (r == 0) L.stats[q] = rec;
