@@ -91,7 +91,9 @@ enum { PHC_PREC_FP64 = 0, PHC_PREC_FP32_INTERIOR = 1 };
  *   end         a path that reaches t = 1 gets <= end_iters Newton steps at
  *               t = 1 (stop at ||dx|| <= end_tol (1 + ||x||))
  *   classes     norms are max_j max(|Re x_j|, |Im x_j|).
- *               AT_INFINITY: ||x|| > diverge_norm after an accepted step; or
+ *               AT_INFINITY: ||x|| > diverge_norm after an accepted step
+ *                 (a polyhedral path: diverge_norm x max(1, ||x(0)||), as
+ *                 its binomial start solution may lie beyond it); or
  *                 an endpoint with ||x|| > endpoint_inf_norm; or stalled at
  *                 t >= end_zone with ||x|| grown by more than growth_inf per
  *                 decade of 1-t over its last (<= 4) decade checkpoints.
