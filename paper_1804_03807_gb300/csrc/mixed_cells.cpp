@@ -91,16 +91,27 @@ int simplex(int R, int C, const double *M, const double *b, const double *cost, 
         }
         basis[r] = e;
     };
-    // returns 0 optimal, 1 unbounded, 3 iteration limit
+    // returns 0 optimal, 1 unbounded, 3 iteration limit; the most negative
+    // reduced cost enters, after 4 (R + C) pivots the first negative one
+    // (Bland's rule, which cannot cycle)
     auto run = [&](int allow, double eps_cost) -> int {
-        const int limit = 64 * (R + C) + 256;
+        const int limit = 64 * (R + C) + 256, bland_after = 4 * (R + C);
         for (int it = 0; it < limit; it++) {
             int e = -1;
-            for (int j = 0; j < allow; j++)
-                if (obj[j] < -eps_cost) {
-                    e = j;
-                    break;
-                }
+            if (it < bland_after) {
+                double best = -eps_cost;
+                for (int j = 0; j < allow; j++)
+                    if (obj[j] < best) {
+                        best = obj[j];
+                        e = j;
+                    }
+            } else {
+                for (int j = 0; j < allow; j++)
+                    if (obj[j] < -eps_cost) {
+                        e = j;
+                        break;
+                    }
+            }
             if (e < 0) return 0;
             int r = -1;
             double best = 0.0;
@@ -231,16 +242,23 @@ struct DualLP {
     void pivot(int r, int e)
     {
         const double p = A[(size_t)e * R + r];
-        for (int j = 0; j < C; j++) A[(size_t)j * R + r] /= p;
+        // the entering column's multipliers, row r's taken out (0): the
+        // update below then runs down whole columns, the memory order of A
+        double fr[PHC_MAX_VARS + 1];
+        for (int i = 0; i < R; i++) fr[i] = i == r ? 0.0 : A[(size_t)e * R + i];
         for (int k = 0; k < R; k++) Binv[(size_t)r * R + k] /= p;
         rhs[r] /= p;
+        for (int j = 0; j < C; j++) {
+            double *col = &A[(size_t)j * R];
+            const double ar = col[r] / p;
+            col[r] = ar;
+            if (ar == 0.0) continue;
+            for (int i = 0; i < R; i++) col[i] -= fr[i] * ar;
+        }
         for (int i = 0; i < R; i++) {
-            if (i == r) continue;
-            const double f = A[(size_t)e * R + i];
-            if (f == 0.0) continue;
-            for (int j = 0; j < C; j++) A[(size_t)j * R + i] -= f * A[(size_t)j * R + r];
-            for (int k = 0; k < R; k++) Binv[(size_t)i * R + k] -= f * Binv[(size_t)r * R + k];
-            rhs[i] -= f * rhs[r];
+            if (fr[i] == 0.0) continue;
+            for (int k = 0; k < R; k++) Binv[(size_t)i * R + k] -= fr[i] * Binv[(size_t)r * R + k];
+            rhs[i] -= fr[i] * rhs[r];
         }
         const double f = d[e];
         if (f != 0.0) {
@@ -250,18 +268,29 @@ struct DualLP {
         }
         basis[r] = e;
     }
-    // Primal simplex on the reduced costs d (Bland's rule; artificial
-    // columns never enter).  0 optimal, 1 unbounded, 3 iteration limit.
+    // Primal simplex on the reduced costs d (artificial columns never
+    // enter): the most negative reduced cost enters (Dantzig), and after
+    // 4 (R + C) pivots the first negative one (Bland's rule, which cannot
+    // cycle).  0 optimal, 1 unbounded, 3 iteration limit.
     int run(double eps)
     {
-        const int limit = 64 * (R + C) + 256;
+        const int limit = 64 * (R + C) + 256, bland_after = 4 * (R + C);
         for (int it = 0; it < limit; it++) {
             int e = -1;
-            for (int j = 0; j < C; j++)
-                if (d[j] < -eps) {
-                    e = j;
-                    break;
-                }
+            if (it < bland_after) {
+                double best = -eps;
+                for (int j = 0; j < C; j++)
+                    if (d[j] < best) {
+                        best = d[j];
+                        e = j;
+                    }
+            } else {
+                for (int j = 0; j < C; j++)
+                    if (d[j] < -eps) {
+                        e = j;
+                        break;
+                    }
+            }
             if (e < 0) return 0;
             int r = -1;
             double best = 0.0;
@@ -389,9 +418,14 @@ void lp_start(const Lifted &L, const Pair &P, DualLP &lp)
 void lp_extend(const Lifted &L, const DualLP &parent, const Pair &P, DualLP &lp)
 {
     lp = parent;
-    std::vector<double> cols, costs;
+    thread_local std::vector<double> cols, costs;
+    cols.clear();
+    costs.clear();
     pair_columns(L, P, cols, costs);
     const int R = lp.R;
+    lp.A.reserve((size_t)(lp.C + costs.size()) * R);
+    lp.d.reserve(lp.C + costs.size());
+    lp.cost.reserve(lp.C + costs.size());
     for (size_t c = 0; c < costs.size(); c++) lp.add_column(&cols[c * R], costs[c]);
     // an artificial left in the basis (at 0) holds a row no parent column
     // touched; a new column that touches it replaces it (a degenerate pivot:
