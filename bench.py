@@ -781,31 +781,38 @@ def run_configs(args):
         return {"config": "pipelined polyhedral vs host threads", "system": "cyclic 10, random coefficients",
                 "rows": rows}
 
-    def config14():
-        """Random-coefficient cyclic 11 by the pipelined polyhedral solve
+    def polyhedral_large(n: int, max_paths: int):
+        """Random-coefficient cyclic n by the pipelined polyhedral solve
         (Section 2.2, Figure 2: the host threads make the mixed cells while
-        the GPU tracks the paths of the cells made so far): 184,756 paths, the
-        number of roots of cyclic 11, against 11! = 39,916,800 total-degree
-        paths."""
+        the GPU tracks the paths of the cells made so far)."""
         from workloads import cyclic, random_lifting, rng_for, with_random_coefficients
-        from math import comb
-        g = with_random_coefficients(cyclic(11), rng_for(911))
-        lift = random_lifting(rng_for(961), g.n_terms)
+        g = with_random_coefficients(cyclic(n), rng_for(900 + n))
+        lift = random_lifting(rng_for(950 + n), g.n_terms)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = P.solve_polyhedral(g, lift, comb(20, 10))
+        r = P.solve_polyhedral(g, lift, max_paths)
         torch.cuda.synchronize()
         t_pipe = time.perf_counter() - t0
         st = P.stats_numpy(r.stats)
         c = r.cls.cpu().numpy()
         far = c != 0
-        return {"config": "polyhedral-11", "workload": "random cyclic 11, pipelined polyhedral solve",
+        return {"config": f"polyhedral-{n}", "workload": f"random cyclic {n}, pipelined polyhedral solve",
                 "not_regular": {"norm_x": sorted(float(v) for v in st["norm_x"][far]),
                                 "stop": np.bincount(st["stop"][far], minlength=6).tolist(),
                                 "t": sorted(float(v) for v in st["t"][far])},
                 "paths": int(c.shape[0]), "pipeline_s": t_pipe, "paths_per_s": c.shape[0] / t_pipe,
                 "units": int(st["n_solve"].sum()), "classes": np.bincount(c, minlength=4).tolist(),
                 "host_threads": os.cpu_count()}
+
+    def config14():
+        """Random cyclic 11: 184,756 paths (the number of roots of cyclic 11,
+        C(20, 10)) against 11! = 39,916,800 total-degree paths."""
+        return polyhedral_large(11, 184756)
+
+    def config15():
+        """Random cyclic 12: 500,352 paths (the mixed volume of cyclic 12)
+        against 12! = 479,001,600 total-degree paths."""
+        return polyhedral_large(12, 500352)
 
     def config11():
         """Polyhedral homotopies (Section 2.2) on random-coefficient cyclic
@@ -923,7 +930,7 @@ def run_configs(args):
 
     want = [int(c) for c in args.configs.split(",")] if args.configs else [1, 2, 3, 4, 5]
     table = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5, 9: config9, 10: config10, 11: config11,
-             12: config12, 13: config13, 14: config14}
+             12: config12, 13: config13, 14: config14, 15: config15}
     for c in want:
         print(json.dumps(table[c]()), flush=True)
     return 0
@@ -992,8 +999,8 @@ def main(argv=None):
     ap.add_argument("--configs", default="", help="--workload configs: which (e.g. 3,5; default 1-5; 9 = the "
                     "cyclic 9 D=2 request of the serving workload alone; 10 = double double tracking; "
                     "11 = polyhedral homotopies; 12 = double, double double and quad double tracking; "
-                    "13 = the pipelined polyhedral solve against the host threads; 14 = random cyclic 11 by "
-                    "the pipelined polyhedral solve)")
+                    "13 = the pipelined polyhedral solve against the host threads; 14 / 15 = random cyclic 11 / 12 "
+                    "by the pipelined polyhedral solve)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the served-latency measurement added to the line (0 = none)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",
