@@ -271,8 +271,9 @@ struct DualLP {
     // Primal simplex on the reduced costs d (artificial columns never
     // enter): the most negative reduced cost enters (Dantzig), and after
     // 4 (R + C) pivots the first negative one (Bland's rule, which cannot
-    // cycle).  0 optimal, 1 unbounded, 3 iteration limit.
-    int run(double eps)
+    // cycle).  0 optimal, 1 unbounded, 3 iteration limit, 4 the objective
+    // of the (feasible) basis fell below z_stop: the minimum lies below it.
+    int run(double eps, double z_stop = -INFINITY)
     {
         const int limit = 64 * (R + C) + 256, bland_after = 4 * (R + C);
         for (int it = 0; it < limit; it++) {
@@ -307,6 +308,7 @@ struct DualLP {
             }
             if (r < 0) return 1;
             pivot(r, e);
+            if (z < z_stop) return 4;
         }
         return 3;
     }
@@ -438,13 +440,16 @@ void lp_extend(const Lifted &L, const DualLP &parent, const Pair &P, DualLP &lp)
                 break;
             }
     }
-    lp.status = lp.run(1e-10 * (1.0 + lp.cmax));
+    // the node is pruned once its objective is below the threshold of
+    // lp_feasible: the simplex keeps the basis feasible and the objective
+    // only falls, so the minimum lies below it too
+    lp.status = lp.run(1e-10 * (1.0 + lp.cmax), -1e-7 * (1.0 + L.wmax));
 }
 
 // Feasibility from a solved problem (as feasible()).
 bool lp_feasible(const Lifted &L, const DualLP &lp)
 {
-    if (lp.status == 1 || lp.status == 2) return false;
+    if (lp.status == 1 || lp.status == 2 || lp.status == 4) return false;
     if (lp.status != 0) return true;
     return lp.z > -1e-7 * (1.0 + L.wmax);
 }
