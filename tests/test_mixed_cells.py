@@ -137,3 +137,25 @@ except P.PhcError as e:
     r = subprocess.run([_sys.executable, "-c", code, root], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert "code -2" in r.stdout and "allocation" in r.stdout, r.stdout + r.stderr[-2000:]
+
+
+def test_cells_do_not_depend_on_the_host_threads():
+    """The search's subtrees run on the host threads and their cells are
+    emitted in task order, so the cells, their order and the volumes are the
+    same for any number of threads (PHC_HOST_THREADS, read at each call)."""
+    g = with_random_coefficients(cyclic(7), rng_for(470))
+    lift = random_lifting(rng_for(471), g.n_terms)
+    old = os.environ.get("PHC_HOST_THREADS")
+    runs = []
+    try:
+        for t in ("1", "3", "8"):
+            os.environ["PHC_HOST_THREADS"] = t
+            cells, vols, mv = P.phc_mixed_cells(g, lift)
+            runs.append((np.asarray(cells).tobytes(), np.asarray(vols).tobytes(), mv))
+    finally:
+        if old is None:
+            os.environ.pop("PHC_HOST_THREADS", None)
+        else:
+            os.environ["PHC_HOST_THREADS"] = old
+    assert runs[0][2] == 924
+    assert all(r == runs[0] for r in runs[1:])
