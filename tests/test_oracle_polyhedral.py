@@ -137,3 +137,23 @@ def test_polyhedral_paths_end_at_the_roots_of_the_total_degree_homotopy(n):
     assert reg.shape[0] == x.shape[0]
     _, _, r = match_sets(x, reg)
     assert r.max() < 1e-9
+
+
+def test_polyhedral_divergence_bound_is_relative_to_the_start():
+    """Section 2.2 fixes no divergence bound.  A polyhedral path starts at a
+    binomial solution in its cell's scaled coordinates, which may lie beyond
+    diverge_norm (1e6) without the path diverging, so its bound is diverge_norm
+    x max(1, ||y(0)||); the other homotopies keep diverge_norm.  y - 1e7 with
+    both terms on the cell (no power of t) is a path that stays at its start
+    1e7: it reaches t = 1 in the 18 steps of a path whose steps are all
+    accepted and ends beyond the endpoint bound (at infinity).  The
+    total-degree path of the same equation from x - 1 grows from 1 to 1e7 and
+    stops when it passes 1e6."""
+    s = PolySystem(1, 1, np.array([2]), np.array([[1], [0]], dtype=np.uint8), np.array([1.0, -1e7]))
+    x, cls, st = oracle.track(oracle.polyhedral_homotopy(s, np.array([0.0, 0.0])), starts=np.array([[1e7]]),
+                              threads=1)
+    assert st["stop"][0] == 0 and st["t"][0] == 1.0 and st["n_accept"][0] == 18
+    assert cls[0] == 2 and x[0, 0] == 1e7
+    x, cls, st = oracle.track(oracle.total_degree(s, unit_gamma(rng_for(480))), threads=1)
+    assert st["stop"][0] == 1 and st["t"][0] < 1.0 and cls[0] == 2
+    assert 1e6 < abs(x[0, 0]) < 1e7
